@@ -1,0 +1,407 @@
+/*
+ * kura_oracle.c -- plain, slow, single-threaded FP64 CPU oracle for the
+ * Kuramoto model on graphs (Boehle, Kuehn, Thalhammer, arXiv 2102.07167).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or helper
+ * with the CUDA library.
+ *
+ * Every function follows a passage of the paper, cited beside it:
+ *   - eq:Kuramoto            (Sec. 2)  classical all-to-all model
+ *   - eq:KuramotoReformulation / eq:EulerCost (Sec. 2) precomputed S_M, C_M
+ *   - eq:OrderParameter      (Sec. 2)  r e^{i psi} = mean of e^{i theta}
+ *   - eq:Potential           (Sec. 2)  classical potential
+ *   - eq:Means / eq:5c       (Sec. 2)  mean deviation / conserved quantity
+ *   - eq:KuramotoGraph       (Sec. 3)  model on a graph, uniform or degree scaling
+ *   - eq:KuramotoGraphApproach (Sec. 3) block rule: sparse sum over non-zeros,
+ *                            dense: precomputed block sums minus the zeros
+ *   - eq:ExtendedPotentialConservation (Sec. 3) graph potential
+ * The time integrator is the classical fixed-step fourth-order Runge-Kutta
+ * method (the paper's Euler example, Sec. 2, generalised as the paper says is
+ * straightforward; the tableau is the textbook one).
+ *
+ * Conventions (readings of the paper, stated once here):
+ *   - Graphs arrive as CSR: row_ptr[n+1] (int64), col[nnz] (int32); row m
+ *     lists the l with A_{m l} = 1.  Diagonal entries are ignored: they add
+ *     sin(0) = 0 to the sum (Sec. 2, remark on coinciding indices) and are
+ *     not counted in the degree used by the non-uniform scaling.
+ *   - scaling 0: uniform, calM_m = n.  scaling 1: calM_m = sum_l A_{m l};
+ *     a zero row gives theta'_m = omega_m (eq:KuramotoGraph, zero-row case).
+ *   - Sums use Neumaier's compensated summation so that the oracle's own
+ *     rounding error stays far below every tolerance it is used for.
+ *
+ * Return codes: 0 ok, -1 bad argument, -2 out of memory.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Trig-evaluation counter (sin and cos calls), for the cost counts of
+ * Table 1 and eq:EulerCost. */
+static int64_t g_trig_count = 0;
+int64_t orc_trig_count(void) { return g_trig_count; }
+void orc_trig_count_reset(void) { g_trig_count = 0; }
+static double counted_sin(double x) { g_trig_count++; return sin(x); }
+static double counted_cos(double x) { g_trig_count++; return cos(x); }
+
+/* Neumaier compensated accumulator. */
+typedef struct { double s, c; } acc_t;
+static void acc_add(acc_t* a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else                       a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double acc_val(const acc_t* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------ */
+/* eq:KuramotoGraph by brute force over a dense 0/1 matrix A (row-major,
+ * A[m*n + l] = A_{m l}).  Intended for n <= a few hundred. */
+int orc_rhs_dense(int64_t n, const uint8_t* A, const double* omega,
+                  const double* theta, double K, int scaling, double* out)
+{
+    if (n <= 0 || !A || !omega || !theta || !out) return -1;
+    for (int64_t m = 0; m < n; m++) {
+        acc_t sum = {0, 0};
+        int64_t deg = 0;
+        for (int64_t l = 0; l < n; l++) {
+            if (l == m || !A[m * n + l]) continue;
+            acc_add(&sum, counted_sin(theta[l] - theta[m]));
+            deg++;
+        }
+        double calM = scaling ? (double)deg : (double)n;
+        out[m] = omega[m];
+        if (deg > 0) out[m] += (K / calM) * acc_val(&sum);
+    }
+    return 0;
+}
+
+/* eq:KuramotoGraph over CSR edges, for the rows listed in `rows` (all rows
+ * when rows == NULL; then nrows must be n).  out[k] is the value of row
+ * rows[k]. */
+int orc_rhs_csr_rows(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                     const double* omega, const double* theta, double K,
+                     int scaling, const int64_t* rows, int64_t nrows,
+                     double* out)
+{
+    if (n <= 0 || !row_ptr || !omega || !theta || !out) return -1;
+    if (!rows && nrows != n) return -1;
+    for (int64_t k = 0; k < nrows; k++) {
+        int64_t m = rows ? rows[k] : k;
+        if (m < 0 || m >= n) return -1;
+        acc_t sum = {0, 0};
+        int64_t deg = 0;
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            int64_t l = col[e];
+            if (l < 0 || l >= n) return -1;
+            if (l == m) continue;
+            acc_add(&sum, counted_sin(theta[l] - theta[m]));
+            deg++;
+        }
+        double calM = scaling ? (double)deg : (double)n;
+        out[k] = omega[m];
+        if (deg > 0) out[k] += (K / calM) * acc_val(&sum);
+    }
+    return 0;
+}
+
+int orc_rhs_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                const double* omega, const double* theta, double K,
+                int scaling, double* out)
+{
+    return orc_rhs_csr_rows(n, row_ptr, col, omega, theta, K, scaling,
+                            NULL, n, out);
+}
+
+/* Classical model through the order-parameter sums, eq:KuramotoReformulation
+ * and eq:EulerCost: S_M = mean sin, C_M = mean cos are computed first (2n
+ * evaluations), then F = omega + K (S_M cos theta - C_M sin theta) (another
+ * 2n evaluations): 4n in total, as counted in Table 1. */
+int orc_rhs_complete_op(int64_t n, const double* omega, const double* theta,
+                        double K, double* out)
+{
+    if (n <= 0 || !omega || !theta || !out) return -1;
+    acc_t S = {0, 0}, C = {0, 0};
+    for (int64_t m = 0; m < n; m++) {
+        acc_add(&S, counted_sin(theta[m]));
+        acc_add(&C, counted_cos(theta[m]));
+    }
+    double SM = acc_val(&S) / (double)n, CM = acc_val(&C) / (double)n;
+    for (int64_t m = 0; m < n; m++)
+        out[m] = omega[m] + K * (SM * counted_cos(theta[m]) - CM * counted_sin(theta[m]));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block rule, eq:KuramotoGraphApproach.  The submatrices are the blocks
+ * (I, J) = {rows with label I} x {columns with label J}; relabelling the
+ * nodes community by community (P A P^T) only reorders rows and columns and
+ * does not change any sum, so blocks are addressed through the labels
+ * directly.  A block is evaluated by the "dense" rule (precomputed
+ * S_J = sum_{l in J} sin theta_l and C_J, minus the sums over the zeros of
+ * the block row) when its zero fraction is below tau, and by the "sparse"
+ * rule (sum of sin(theta_l - theta_m) over the non-zeros) otherwise.  The
+ * zero set of a diagonal block contains l = m itself, literally as in the
+ * paper's formula (A_{m m} = 0).
+ *
+ * stats (nullable, 6 entries): [0] dense blocks with at least one row and
+ * column, [1] sparse blocks, [2] zeros summed over by the dense rule,
+ * [3] non-zeros summed over by the sparse rule, [4] blocks considered,
+ * [5] sin/cos evaluations of this call.
+ */
+int orc_rhs_block(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                  const int32_t* label, int32_t n_comm, const double* omega,
+                  const double* theta, double K, int scaling, double tau,
+                  double* out, int64_t* stats)
+{
+    if (n <= 0 || n_comm <= 0 || !row_ptr || !col || !label || !omega ||
+        !theta || !out) return -1;
+    for (int64_t m = 0; m < n; m++)
+        if (label[m] < 0 || label[m] >= n_comm) return -1;
+    int64_t trig0 = g_trig_count;
+    int64_t nc = n_comm;
+    int64_t* size = calloc((size_t)nc, sizeof(int64_t));
+    int64_t* nnzb = calloc((size_t)(nc * nc), sizeof(int64_t));
+    uint8_t* dense = calloc((size_t)(nc * nc), 1);
+    int64_t* member_ptr = calloc((size_t)nc + 1, sizeof(int64_t));
+    int64_t* members = malloc((size_t)n * sizeof(int64_t));
+    double* S = calloc((size_t)nc, sizeof(double));
+    double* C = calloc((size_t)nc, sizeof(double));
+    double* sn = malloc((size_t)n * sizeof(double));
+    double* cs = malloc((size_t)n * sizeof(double));
+    uint8_t* mark = calloc((size_t)n, 1);
+    int rc = 0;
+    if (!size || !nnzb || !dense || !member_ptr || !members || !S || !C ||
+        !sn || !cs || !mark) { rc = -2; goto done; }
+
+    /* community sizes and member lists */
+    for (int64_t m = 0; m < n; m++) size[label[m]]++;
+    for (int64_t I = 0; I < nc; I++) member_ptr[I + 1] = member_ptr[I] + size[I];
+    {
+        int64_t* fill = calloc((size_t)nc, sizeof(int64_t));
+        if (!fill) { rc = -2; goto done; }
+        for (int64_t m = 0; m < n; m++) {
+            int64_t I = label[m];
+            members[member_ptr[I] + fill[I]++] = m;
+        }
+        free(fill);
+    }
+    /* non-zeros per block, diagonal entries ignored */
+    for (int64_t m = 0; m < n; m++)
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n) { rc = -1; goto done; }
+            if (col[e] == m) continue;
+            nnzb[(int64_t)label[m] * nc + label[col[e]]]++;
+        }
+    /* classification: zero fraction of the block below tau => dense */
+    int64_t n_dense = 0, n_sparse = 0, n_zero_terms = 0, n_nz_terms = 0;
+    for (int64_t I = 0; I < nc; I++)
+        for (int64_t J = 0; J < nc; J++) {
+            double entries = (double)size[I] * (double)size[J];
+            if (entries == 0) continue;
+            double zeros = entries - (double)nnzb[I * nc + J];
+            int d = (zeros / entries) < tau;
+            dense[I * nc + J] = (uint8_t)d;
+            if (d) n_dense++; else n_sparse++;
+        }
+    /* sin, cos of every phase (2n evaluations) and the block sums S_J, C_J */
+    for (int64_t l = 0; l < n; l++) { sn[l] = counted_sin(theta[l]); cs[l] = counted_cos(theta[l]); }
+    for (int64_t J = 0; J < nc; J++) {
+        acc_t sj = {0, 0}, cj = {0, 0};
+        for (int64_t k = member_ptr[J]; k < member_ptr[J + 1]; k++) {
+            acc_add(&sj, sn[members[k]]);
+            acc_add(&cj, cs[members[k]]);
+        }
+        S[J] = acc_val(&sj);
+        C[J] = acc_val(&cj);
+    }
+    /* rows */
+    for (int64_t m = 0; m < n; m++) {
+        int64_t I = label[m];
+        int64_t deg = 0;
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++)
+            if (col[e] != m) { mark[col[e]] = 1; deg++; }
+        acc_t total = {0, 0};
+        for (int64_t J = 0; J < nc; J++) {
+            if (size[J] == 0) continue;
+            if (dense[I * nc + J]) {
+                /* (S_J - sum_{zeros} sin) cos theta_m - (C_J - sum_{zeros} cos) sin theta_m */
+                acc_t zs = {0, 0}, zc = {0, 0};
+                for (int64_t k = member_ptr[J]; k < member_ptr[J + 1]; k++) {
+                    int64_t l = members[k];
+                    if (mark[l]) continue;          /* A_{m l} = 1: not a zero */
+                    acc_add(&zs, sn[l]);
+                    acc_add(&zc, cs[l]);
+                    n_zero_terms++;
+                }
+                acc_add(&total, (S[J] - acc_val(&zs)) * cs[m]);
+                acc_add(&total, -(C[J] - acc_val(&zc)) * sn[m]);
+            } else {
+                /* straightforward sum over the non-zeros of the block row */
+                for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+                    int64_t l = col[e];
+                    if (l == m || label[l] != J) continue;
+                    acc_add(&total, counted_sin(theta[l] - theta[m]));
+                    n_nz_terms++;
+                }
+            }
+        }
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) mark[col[e]] = 0;
+        double calM = scaling ? (double)deg : (double)n;
+        out[m] = omega[m];
+        if (deg > 0) out[m] += (K / calM) * acc_val(&total);
+    }
+    if (stats) {
+        stats[0] = n_dense; stats[1] = n_sparse; stats[2] = n_zero_terms;
+        stats[3] = n_nz_terms; stats[4] = n_dense + n_sparse;
+        stats[5] = g_trig_count - trig0;
+    }
+done:
+    free(size); free(nnzb); free(dense); free(member_ptr); free(members);
+    free(S); free(C); free(sn); free(cs); free(mark);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Classical fixed-step RK4 on the graph model, right-hand side by the CSR
+ * definition (orc_rhs_csr).  theta is advanced in place, n_steps steps of
+ * size h:
+ *   k1 = f(y), k2 = f(y + h/2 k1), k3 = f(y + h/2 k2), k4 = f(y + h k3),
+ *   y <- y + h/6 (k1 + 2 k2 + 2 k3 + k4).
+ * The phases are kept unwrapped (the conserved quantity, eq:5c, is stated
+ * for unwrapped phases). */
+int orc_rk4_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                const double* omega, double K, int scaling, double* theta,
+                double h, int64_t n_steps)
+{
+    if (n <= 0 || !theta || n_steps < 0) return -1;
+    double* k1 = malloc((size_t)n * sizeof(double));
+    double* k2 = malloc((size_t)n * sizeof(double));
+    double* k3 = malloc((size_t)n * sizeof(double));
+    double* k4 = malloc((size_t)n * sizeof(double));
+    double* Y = malloc((size_t)n * sizeof(double));
+    int rc = 0;
+    if (!k1 || !k2 || !k3 || !k4 || !Y) { rc = -2; goto done; }
+    for (int64_t s = 0; s < n_steps; s++) {
+        if ((rc = orc_rhs_csr(n, row_ptr, col, omega, theta, K, scaling, k1))) goto done;
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + 0.5 * h * k1[i];
+        if ((rc = orc_rhs_csr(n, row_ptr, col, omega, Y, K, scaling, k2))) goto done;
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + 0.5 * h * k2[i];
+        if ((rc = orc_rhs_csr(n, row_ptr, col, omega, Y, K, scaling, k3))) goto done;
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + h * k3[i];
+        if ((rc = orc_rhs_csr(n, row_ptr, col, omega, Y, K, scaling, k4))) goto done;
+        for (int64_t i = 0; i < n; i++)
+            theta[i] += (h / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+done:
+    free(k1); free(k2); free(k3); free(k4); free(Y);
+    return rc;
+}
+
+/* Classical all-to-all model (eq:Kuramoto) integrated with the same RK4,
+ * right-hand side by the order-parameter sums (eq:KuramotoReformulation). */
+int orc_rk4_complete(int64_t n, const double* omega, double K, double* theta,
+                     double h, int64_t n_steps)
+{
+    if (n <= 0 || !theta || n_steps < 0) return -1;
+    double* k1 = malloc((size_t)n * sizeof(double));
+    double* k2 = malloc((size_t)n * sizeof(double));
+    double* k3 = malloc((size_t)n * sizeof(double));
+    double* k4 = malloc((size_t)n * sizeof(double));
+    double* Y = malloc((size_t)n * sizeof(double));
+    int rc = 0;
+    if (!k1 || !k2 || !k3 || !k4 || !Y) { rc = -2; goto done; }
+    for (int64_t s = 0; s < n_steps; s++) {
+        orc_rhs_complete_op(n, omega, theta, K, k1);
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + 0.5 * h * k1[i];
+        orc_rhs_complete_op(n, omega, Y, K, k2);
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + 0.5 * h * k2[i];
+        orc_rhs_complete_op(n, omega, Y, K, k3);
+        for (int64_t i = 0; i < n; i++) Y[i] = theta[i] + h * k3[i];
+        orc_rhs_complete_op(n, omega, Y, K, k4);
+        for (int64_t i = 0; i < n; i++)
+            theta[i] += (h / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+done:
+    free(k1); free(k2); free(k3); free(k4); free(Y);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* eq:OrderParameter: r e^{i psi} = (1/n) sum_m e^{i theta_m} = C + i S;
+ * r = sqrt(C^2 + S^2), psi = atan2(S, C) (psi = 0 when r = 0).  When label is
+ * given, the same quantity restricted to each community ("localised order
+ * parameters") is written to r_comm[n_comm], psi_comm[n_comm] (nullable). */
+int orc_order_params(int64_t n, const double* theta, double* r, double* psi,
+                     const int32_t* label, int32_t n_comm, double* r_comm,
+                     double* psi_comm)
+{
+    if (n <= 0 || !theta || !r || !psi) return -1;
+    acc_t S = {0, 0}, C = {0, 0};
+    for (int64_t m = 0; m < n; m++) {
+        acc_add(&S, sin(theta[m]));
+        acc_add(&C, cos(theta[m]));
+    }
+    double s = acc_val(&S) / (double)n, c = acc_val(&C) / (double)n;
+    *r = sqrt(c * c + s * s);
+    *psi = (*r == 0.0) ? 0.0 : atan2(s, c);
+    if (label && n_comm > 0 && r_comm) {
+        for (int32_t I = 0; I < n_comm; I++) {
+            acc_t SI = {0, 0}, CI = {0, 0};
+            int64_t cnt = 0;
+            for (int64_t m = 0; m < n; m++) {
+                if (label[m] != I) continue;
+                acc_add(&SI, sin(theta[m]));
+                acc_add(&CI, cos(theta[m]));
+                cnt++;
+            }
+            double si = cnt ? acc_val(&SI) / (double)cnt : 0.0;
+            double ci = cnt ? acc_val(&CI) / (double)cnt : 0.0;
+            r_comm[I] = sqrt(ci * ci + si * si);
+            if (psi_comm) psi_comm[I] = (r_comm[I] == 0.0) ? 0.0 : atan2(si, ci);
+        }
+    }
+    return 0;
+}
+
+/* Potential on a graph, eq:ExtendedPotentialConservation (with the classical
+ * eq:Potential as the complete-graph case):
+ *   V = -omega^T theta + (K/2) sum_{m,l} calA_{m l} (1 - cos(theta_l - theta_m)),
+ * calA_{m l} = A_{m l} / calM_m. */
+int orc_potential_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                      const double* omega, const double* theta, double K,
+                      int scaling, double* V)
+{
+    if (n <= 0 || !row_ptr || !col || !omega || !theta || !V) return -1;
+    acc_t lin = {0, 0}, quad = {0, 0};
+    for (int64_t m = 0; m < n; m++) acc_add(&lin, -omega[m] * theta[m]);
+    for (int64_t m = 0; m < n; m++) {
+        int64_t deg = 0;
+        acc_t row = {0, 0};
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            int64_t l = col[e];
+            if (l == m) continue;
+            acc_add(&row, 1.0 - cos(theta[l] - theta[m]));
+            deg++;
+        }
+        if (deg == 0) continue;
+        double calM = scaling ? (double)deg : (double)n;
+        acc_add(&quad, acc_val(&row) / calM);
+    }
+    *V = acc_val(&lin) + 0.5 * K * acc_val(&quad);
+    return 0;
+}
+
+/* eq:Means: (1/n) sum_m (theta_m(t) - theta_m(0) - t omega_m). */
+int orc_mean_deviation(int64_t n, const double* theta_t, const double* theta_0,
+                       const double* omega, double t, double* out)
+{
+    if (n <= 0 || !theta_t || !theta_0 || !omega || !out) return -1;
+    acc_t a = {0, 0};
+    for (int64_t m = 0; m < n; m++) acc_add(&a, theta_t[m] - theta_0[m] - t * omega[m]);
+    *out = acc_val(&a) / (double)n;
+    return 0;
+}
