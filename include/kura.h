@@ -1,0 +1,217 @@
+/*
+ * kura.h -- C ABI of libkura: the Kuramoto model on graphs with localised
+ * order parameters, integrated by classical RK4 on one NVIDIA GB300 GPU.
+ *
+ * Method: Boehle, Kuehn, Thalhammer, "On the reliable and efficient
+ * numerical integration of the Kuramoto model and related dynamical systems
+ * on graphs", arXiv 2102.07167.
+ *
+ *   theta'_m = omega_m + (K / calM_m) sum_l A_{m l} sin(theta_l - theta_m)
+ *                                               (eq:KuramotoGraph, Sec. 3)
+ *
+ * The adjacency matrix is permuted so that communities are contiguous
+ * (P A P^T, Sec. 3), every block (I, J) is classified by its zero fraction,
+ * dense blocks are evaluated through the precomputed block sums
+ * S_J = sum_{l in J} sin theta_l, C_J = sum_{l in J} cos theta_l minus the
+ * sums over the block row's zeros, sparse blocks by direct summation over
+ * their non-zeros (eq:KuramotoGraphApproach and the remark after it).
+ *
+ * Conventions for every entry point:
+ *   - All vectors are in the caller's ("user") node order; the library
+ *     applies and undoes its permutation at the boundary.
+ *   - Phase/frequency vectors may be device pointers or host pointers
+ *     (pinned or pageable); the library detects which.  With host pointers
+ *     the call copies in and out and returns after the result is on the
+ *     host.  With device pointers the call is asynchronous on the handle's
+ *     stream.
+ *   - Arrays passed to kura_create are copied; the caller keeps ownership of
+ *     every pointer it passes.  The handle owns its internal buffers.
+ *   - Every call returns a kura_status; nothing aborts or exits.  A failed
+ *     call leaves a message in kura_last_error(handle).  Device-side
+ *     conditions (non-finite phases, a bounded wait that gave up) latch in
+ *     the handle and are reported by kura_sync and by any call that
+ *     synchronises.
+ *   - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef KURA_H
+#define KURA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kura_ctx* kura_t;
+typedef struct kura_plan_s* kura_plan_t;
+
+typedef enum {
+    KURA_OK = 0,
+    KURA_EINVAL = 1,     /* invalid argument (bad CSR, label, size, pointer, h, ...) */
+    KURA_ENOMEM = 2,     /* host or device allocation failed */
+    KURA_ECUDA = 3,      /* CUDA runtime error (no device, launch failure, ...) */
+    KURA_ESTATE = 4,     /* call not valid in the handle's state */
+    KURA_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    KURA_ENUMERIC = 6    /* a non-finite value appeared in the state */
+} kura_status;
+
+enum { KURA_PREC_FP64 = 0, KURA_PREC_MIXED = 1 };
+enum { KURA_SCALING_UNIFORM = 0, KURA_SCALING_DEGREE = 1 };
+
+typedef struct {
+    /* KURA_PREC_FP64: FP64 sin/cos, per-edge sums exact in 64-bit fixed
+     *   point, FP64 epilogue and state.
+     * KURA_PREC_MIXED: FP32 sin/cos of the phase reduced mod 2 pi in FP64,
+     *   FP32 per-edge corrections, block sums exact in fixed point and
+     *   rounded once to FP64, FP64 epilogue and state. */
+    int32_t precision;
+    /* calM_m of eq:KuramotoGraph: KURA_SCALING_UNIFORM (calM_m = N) or
+     * KURA_SCALING_DEGREE (calM_m = sum_l A_{m l}; zero rows get theta' = omega). */
+    int32_t scaling;
+    /* block threshold: dense iff zero fraction < tau (Sec. 1, 3: precompute
+     * when ones outnumber zeros); in [0, 1], default 0.5 */
+    double tau;
+    /* keep a host copy of the CSR (needed by kura_classify_blocks with a new
+     * tau and by the direct-summation baseline); default 1 */
+    int32_t keep_host_csr;
+    int32_t reserved[7];
+} kura_opts;
+
+typedef struct {
+    int64_t n, nnz, self_loops;      /* nodes; edges as given; diagonal entries dropped */
+    int32_t n_comm, q_bits;          /* communities; fixed-point fraction bits */
+    double tau;
+    int64_t dense_blocks, sparse_blocks, nonempty_blocks;
+    int64_t missing_entries;         /* zeros of dense blocks stored (subtracted) */
+    int64_t sparse_entries;          /* non-zeros of sparse blocks stored (added) */
+    int64_t max_row_entries;
+    int64_t tiles, max_window;
+    /* Algorithmic bytes of one right-hand-side evaluation, split by kernel:
+     * stream_bytes = correction streams + per-row metadata read by the row
+     * kernel; node_bytes_row = per-node traffic of the row kernel in an RK4
+     * stage; node_bytes_trig = per-node traffic of the trig/block-sum kernel. */
+    int64_t stream_bytes, node_bytes_row, node_bytes_trig;
+    int64_t direct_edges;            /* edges summed by the direct baseline */
+} kura_block_stats;
+
+/* Fills *opts with the defaults (FP64, uniform scaling, tau 0.5, host CSR kept). */
+void kura_default_opts(kura_opts* opts);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t kura_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* kura_status_string(kura_status s);
+
+/* Creates a handle for the graph given in CSR (eq:KuramotoGraph).
+ *   n               number of oscillators (M in the paper), >= 1
+ *   row_ptr[n+1]    host, int64, row_ptr[0] = 0, non-decreasing
+ *   col[nnz]        host, int32, row m lists the l with A_{m l} = 1,
+ *                   strictly increasing within a row; diagonal entries are
+ *                   dropped (they add sin 0 = 0, Sec. 2 remark)
+ *   label[n]        host, community of each node in [0, n_comm) (the
+ *                   partition of Sec. 3; communities may be empty)
+ *   omega[n]        host, natural frequencies
+ *   K               coupling constant (finite)
+ *   opts            nullable (defaults)
+ *   stream          cudaStream_t for all work of the handle (NULL: legacy
+ *                   default stream)
+ *   out             receives the handle
+ * Permutes, classifies blocks with opts->tau and uploads.  Returns
+ * KURA_EINVAL for malformed input, KURA_ECUDA if no usable GPU. */
+kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                        const int32_t* label, int32_t n_comm, const double* omega,
+                        double K, const kura_opts* opts, void* stream, kura_t* out);
+
+/* Re-classifies the blocks with a new threshold tau in [0, 1] (pass a
+ * negative tau to keep the current one) and rebuilds the streams (Sec. 3,
+ * dense/sparse decision).  Needs the host CSR copy.  stats is nullable. */
+kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats);
+
+/* Current classification statistics (host struct). */
+kura_status kura_get_stats(kura_t h, kura_block_stats* stats);
+
+/* One right-hand-side evaluation, dtheta = F(theta) (eq:KuramotoGraph by
+ * eq:KuramotoGraphApproach).  theta[n], dtheta[n]: user order, device or
+ * host, may not alias. */
+kura_status kura_rhs(kura_t h, const double* theta, double* dtheta);
+
+/* n_steps classical RK4 steps of size step on theta[n] in place (user
+ * order, device or host).  step > 0 and finite; n_steps >= 0.  The step
+ * loop runs as a CUDA graph (cached per (step, chunk)).  The phases are kept
+ * unwrapped (eq:5c). */
+kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps);
+
+/* Order parameters (eq:OrderParameter): r e^{i psi} = (1/n) sum_m e^{i theta_m}
+ * of theta[n] (user order, device or host); r, psi: host scalars.  When
+ * r_comm / psi_comm (host, n_comm entries each, nullable) are given, the
+ * same quantity per community ("localised order parameters"); empty
+ * communities give 0.  psi = 0 when r = 0.  Synchronises the stream. */
+kura_status kura_order_params(kura_t h, const double* theta, double* r, double* psi,
+                              double* r_comm, double* psi_comm);
+
+/* Replaces omega (nullable; n entries, user order, device or host) and/or
+ * K (nullable). */
+kura_status kura_set_param(kura_t h, const double* omega, const double* K);
+
+/* Direct-summation baseline: dtheta_m = omega_m + (K/calM_m) sum over the
+ * CSR edges of sin(theta_l - theta_m), one sine per edge (eq:KuramotoGraph,
+ * original formulation; the paper's straightforward summation).
+ * precision: KURA_PREC_FP64 (FP64 sine per edge) or KURA_PREC_MIXED (FP32
+ * sine of FP32 phases reduced mod 2 pi, FP32 row sums, FP64 epilogue). */
+kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32_t precision);
+
+/* n_steps RK4 steps with the direct-summation right-hand side. */
+kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps,
+                                  int32_t precision);
+
+/* Enables (1) or disables (0) CUDA-event timing of every row-kernel launch
+ * inside the captured RK4 graphs; kura_kernel_times then returns the
+ * per-launch durations (ms) of the last replay, up to cap entries, and the
+ * number available in *count. */
+kura_status kura_set_timing(kura_t h, int32_t on);
+kura_status kura_kernel_times(kura_t h, float* ms, int32_t cap, int32_t* count);
+
+/* Switches the handle to another stream (cached graphs stay valid). */
+kura_status kura_set_stream(kura_t h, void* stream);
+
+/* Waits for the handle's stream and reports latched device conditions
+ * (KURA_ENUMERIC, KURA_ETIMEOUT), clearing them. */
+kura_status kura_sync(kura_t h);
+
+/* Last error message of the handle (or of the last failed kura_create when
+ * h is NULL).  Static storage owned by the library. */
+const char* kura_last_error(kura_t h);
+
+/* Frees the handle and all its device and host memory.  NULL is a no-op. */
+void kura_destroy(kura_t h);
+
+/* ---------------------------------------------------------------------
+ * Host-only block plan (no GPU needed): the permutation, classification and
+ * correction streams that kura_create uploads, exposed for inspection.
+ * Arguments as for kura_create; tau in [0, 1].
+ */
+kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* label, int32_t n_comm, double tau,
+                            kura_plan_t* out);
+/* stats of the plan (the byte counts assume KURA_PREC_FP64) */
+kura_status kura_plan_stats(kura_plan_t p, kura_block_stats* stats);
+/* perm[n]: perm[new] = old; comm_off[n_comm + 1]: community boundaries in
+ * the permuted order.  Either pointer may be NULL. */
+kura_status kura_plan_perm(kura_plan_t p, int32_t* perm, int64_t* comm_off);
+/* Correction streams of permuted row `row`: missing entries (zeros of its
+ * dense blocks) and present entries (non-zeros of its sparse blocks), as
+ * permuted column indices.  Writes up to cap entries to each array
+ * (nullable) and the true counts to *n_missing, *n_present. */
+kura_status kura_plan_row(kura_plan_t p, int64_t row, int32_t* missing, int64_t* n_missing,
+                          int32_t* present, int64_t* n_present, int64_t cap);
+/* Dense column blocks D(I) of row block I: up to cap entries, count in *count. */
+kura_status kura_plan_dense_blocks(kura_plan_t p, int32_t I, int32_t* J, int32_t cap,
+                                   int32_t* count);
+void kura_plan_destroy(kura_plan_t p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KURA_H */

@@ -1,0 +1,842 @@
+// C ABI of libkura (declared in include/kura.h): handle, device buffers,
+// CUDA-graph step loop and the host-only plan inspection entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kura.h"
+#include "kura_kernels.cuh"
+#include "plan.hpp"
+
+using namespace kura;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------- device memory
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t b)
+    {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) bytes = b;
+        else p = nullptr;
+        return e;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> events;   // begin/end pairs around every row-kernel launch
+    ~GraphEntry()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto e : events) cudaEventDestroy(e);
+    }
+};
+
+int ceil_log2(int64_t v)
+{
+    int k = 0;
+    while ((int64_t(1) << k) < v) k++;
+    return k;
+}
+
+}  // namespace
+
+struct kura_ctx {
+    std::string err;
+    int device = 0;
+    kura_opts opts{};
+    int64_t n = 0;
+    int32_t n_comm = 0;
+    double K = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;        // capture stream (graphs are replayed on `stream`)
+    // host copies
+    std::vector<int64_t> h_row_ptr;
+    std::vector<int32_t> h_col, h_label;
+    std::vector<double> h_omega;        // user order
+    Plan plan;                          // host plan (streams released after upload)
+    int64_t miss_total = 0, pres_total = 0, nnz = 0;
+    // device buffers
+    DevMem perm, node_comm, miss_off, pres_off, miss_cnt, pres_cnt, miss, pres, tiles, dptr, dcol, comm_off;
+    DevMem omega, rscale, table, bsum, bsum_out, tot, T, counter, err_flags;
+    DevMem y, Y, krk, fbuf, user, red, order_out;
+    DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
+    int q_bits = 0;
+    int32_t n_tiles = 0, max_wlen = 0;
+    size_t row_smem = 0;
+    // graphs
+    std::map<std::pair<double, int64_t>, std::unique_ptr<GraphEntry>> graphs;
+    GraphEntry* last_graph = nullptr;
+    bool timing = false;
+
+    kura_status fail(kura_status s, const char* fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return s;
+    }
+    kura_status cuda_fail(cudaError_t e, const char* what)
+    {
+        return fail(e == cudaErrorMemoryAllocation ? KURA_ENOMEM : KURA_ECUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    }
+    ~kura_ctx()
+    {
+        if (device >= 0) cudaSetDevice(device);
+        graphs.clear();
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+#define KCHECK(h, call, what)                                  \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return (h)->cuda_fail(e_, what); \
+    } while (0)
+
+namespace {
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t upload(DevMem& d, const std::vector<T>& v, cudaStream_t s)
+{
+    cudaError_t e = d.alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaMemsetAsync(d.p, 0, d.bytes, s);
+    return cudaMemcpyAsync(d.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+DevGraph dev_graph(kura_ctx* h)
+{
+    DevGraph g{};
+    g.n = h->n;
+    g.n_comm = h->n_comm;
+    g.q_bits = h->q_bits;
+    g.scale_q = std::ldexp(1.0, h->q_bits);
+    g.inv_scale_q = std::ldexp(1.0, -h->q_bits);
+    g.scale = h->K / double(h->n);
+    g.rscale = h->opts.scaling == KURA_SCALING_DEGREE ? h->rscale.as<double>() : nullptr;
+    g.node_comm = h->node_comm.as<int32_t>();
+    g.miss_off = h->miss_off.as<int64_t>();
+    g.pres_off = h->pres_off.as<int64_t>();
+    g.miss_cnt = h->miss_cnt.as<int32_t>();
+    g.pres_cnt = h->pres_cnt.as<int32_t>();
+    g.miss = h->miss.as<int32_t>();
+    g.pres = h->pres.as<int32_t>();
+    g.tiles = h->tiles.as<Tile>();
+    g.dptr = h->dptr.as<int64_t>();
+    g.dcol = h->dcol.as<int32_t>();
+    g.comm_off = h->comm_off.as<int64_t>();
+    g.omega = h->omega.as<double>();
+    g.table = h->table.p;
+    g.bsum = h->bsum.as<unsigned long long>();
+    g.bsum_out = h->bsum_out.as<long long>();
+    g.tot = h->tot.as<long long>();
+    g.T = h->T.p;
+    g.counter = h->counter.as<unsigned int>();
+    g.err = h->err_flags.as<int>();
+    return g;
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
+
+// ---- launches of one right-hand-side evaluation on stream s
+template <int MODE>
+void launch_trig(kura_ctx* h, const DevGraph& g, const double* theta_perm, int what, cudaStream_t s)
+{
+    const unsigned nb = blocks_for(h->n, TRIG_THREADS);
+    if (what == (TB_TABLE | TB_T)) k_trig_blocksum<MODE, TB_TABLE | TB_T><<<nb, TRIG_THREADS, 0, s>>>(g, theta_perm);
+    else k_trig_blocksum<MODE, 0><<<nb, TRIG_THREADS, 0, s>>>(g, theta_perm);
+}
+
+template <int MODE, int STAGE>
+void launch_row(kura_ctx* h, const DevGraph& g, const RkArgs& rk, cudaStream_t s)
+{
+    k_row_stage<MODE, STAGE><<<unsigned(h->n_tiles), ROW_THREADS, h->row_smem, s>>>(g, rk);
+}
+
+template <int MODE>
+void launch_row_stage(kura_ctx* h, const DevGraph& g, const RkArgs& rk, int stage, cudaStream_t s)
+{
+    switch (stage) {
+    case ST_RHS: launch_row<MODE, ST_RHS>(h, g, rk, s); break;
+    case ST_1: launch_row<MODE, ST_1>(h, g, rk, s); break;
+    case ST_2: launch_row<MODE, ST_2>(h, g, rk, s); break;
+    case ST_3: launch_row<MODE, ST_3>(h, g, rk, s); break;
+    default: launch_row<MODE, ST_4>(h, g, rk, s); break;
+    }
+}
+
+template <int MODE>
+cudaError_t set_row_attrs(size_t smem)
+{
+    cudaError_t e = cudaSuccess;
+    const void* fns[] = {(const void*)k_row_stage<MODE, ST_RHS>, (const void*)k_row_stage<MODE, ST_1>,
+                         (const void*)k_row_stage<MODE, ST_2>, (const void*)k_row_stage<MODE, ST_3>,
+                         (const void*)k_row_stage<MODE, ST_4>};
+    for (const void* f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+RkArgs rk_args(kura_ctx* h, double step)
+{
+    RkArgs rk{};
+    rk.y = h->y.as<double>();
+    rk.y_out = h->y.as<double>();
+    rk.Y = h->Y.as<double>();
+    rk.krk = h->krk.as<double>();
+    rk.out = h->fbuf.as<double>();
+    rk.h = step;
+    return rk;
+}
+
+// One RK4 step (4 stages) enqueued on s; events (if any) bracket the row kernels.
+void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
+{
+    const DevGraph g = dev_graph(h);
+    const RkArgs rk = rk_args(h, step);
+    for (int st = ST_1; st <= ST_4; st++) {
+        const double* in = (st == ST_1) ? h->y.as<double>() : h->Y.as<double>();
+        if (h->opts.precision == KURA_PREC_MIXED) launch_trig<MODE_MIXED>(h, g, in, TB_TABLE | TB_T, s);
+        else launch_trig<MODE_FP64>(h, g, in, TB_TABLE | TB_T, s);
+        if (ev) cudaEventRecordWithFlags(ev[2 * (st - 1)], s, cudaEventRecordExternal);
+        if (h->opts.precision == KURA_PREC_MIXED) launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
+        else launch_row_stage<MODE_FP64>(h, g, rk, st, s);
+        if (ev) cudaEventRecordWithFlags(ev[2 * (st - 1) + 1], s, cudaEventRecordExternal);
+    }
+}
+
+kura_status build_device(kura_ctx* h, Plan&& plan)
+{
+    cudaStream_t s = h->stream;
+    h->plan = std::move(plan);
+    Plan& p = h->plan;
+    h->n_tiles = int32_t(p.tiles.size());
+    h->max_wlen = p.max_wlen;
+    h->miss_total = p.miss_total;
+    h->pres_total = p.pres_total;
+    h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2));
+    const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
+    h->row_smem = size_t(std::max(p.max_wlen, 2)) * esize;
+    KCHECK(h, (h->opts.precision == KURA_PREC_MIXED ? set_row_attrs<MODE_MIXED>(h->row_smem)
+                                                    : set_row_attrs<MODE_FP64>(h->row_smem)),
+           "setting the row kernel's shared-memory size");
+
+    KCHECK(h, upload(h->perm, p.perm, s), "upload perm");
+    KCHECK(h, upload(h->node_comm, p.node_comm, s), "upload node_comm");
+    KCHECK(h, upload(h->miss_off, p.miss_off, s), "upload miss_off");
+    KCHECK(h, upload(h->pres_off, p.pres_off, s), "upload pres_off");
+    KCHECK(h, upload(h->miss_cnt, p.miss_cnt, s), "upload miss_cnt");
+    KCHECK(h, upload(h->pres_cnt, p.pres_cnt, s), "upload pres_cnt");
+    KCHECK(h, upload(h->miss, p.miss, s), "upload missing-entry stream");
+    KCHECK(h, upload(h->pres, p.pres, s), "upload sparse-entry stream");
+    KCHECK(h, upload(h->tiles, p.tiles, s), "upload tiles");
+    KCHECK(h, upload(h->dptr, p.dptr, s), "upload dptr");
+    KCHECK(h, upload(h->dcol, p.dcol, s), "upload dcol");
+    KCHECK(h, upload(h->comm_off, p.comm_off, s), "upload comm_off");
+    {
+        std::vector<double> om(size_t(h->n));
+        for (int64_t v = 0; v < h->n; v++) om[size_t(v)] = h->h_omega[size_t(p.perm[size_t(v)])];
+        KCHECK(h, upload(h->omega, om, s), "upload omega");
+        std::vector<double> rs;
+        if (h->opts.scaling == KURA_SCALING_DEGREE) {
+            rs.resize(size_t(h->n));
+            for (int64_t v = 0; v < h->n; v++) rs[size_t(v)] = p.deg[size_t(v)] > 0 ? h->K / p.deg[size_t(v)] : 0.0;
+        }
+        KCHECK(h, upload(h->rscale, rs, s), "upload rscale");
+    }
+    const size_t n = size_t(h->n), nc = size_t(h->n_comm);
+    KCHECK(h, h->table.alloc(esize * (n + 2)), "alloc table");
+    KCHECK(h, cudaMemsetAsync(h->table.p, 0, h->table.bytes, s), "memset table");
+    KCHECK(h, h->bsum.alloc(16 * nc), "alloc bsum");
+    KCHECK(h, cudaMemsetAsync(h->bsum.p, 0, h->bsum.bytes, s), "memset bsum");
+    KCHECK(h, h->bsum_out.alloc(16 * nc), "alloc bsum_out");
+    KCHECK(h, h->tot.alloc(16), "alloc tot");
+    KCHECK(h, h->T.alloc(16 * nc), "alloc T");
+    KCHECK(h, h->counter.alloc(16), "alloc counter");
+    KCHECK(h, cudaMemsetAsync(h->counter.p, 0, 16, s), "memset counter");
+    if (!h->err_flags.p) {
+        KCHECK(h, h->err_flags.alloc(16), "alloc error flags");
+        KCHECK(h, cudaMemsetAsync(h->err_flags.p, 0, 16, s), "memset error flags");
+    }
+    for (DevMem* d : {&h->y, &h->Y, &h->krk, &h->fbuf, &h->user}) KCHECK(h, d->alloc(8 * n), "alloc state");
+    KCHECK(h, h->order_out.alloc(8 * (2 + 2 * nc)), "alloc order_out");
+    KCHECK(h, cudaStreamSynchronize(s), "upload");
+    // the per-row streams now live on the device
+    std::vector<int32_t>().swap(p.miss);
+    std::vector<int32_t>().swap(p.pres);
+    h->graphs.clear();
+    h->last_graph = nullptr;
+    return KURA_OK;
+}
+
+kura_status check_handle(kura_t h)
+{
+    if (!h) return KURA_EINVAL;
+    cudaSetDevice(h->device);
+    return KURA_OK;
+}
+
+// Latched device conditions -> status (clears them).
+kura_status read_flags(kura_t h)
+{
+    int flags = 0;
+    KCHECK(h, cudaMemcpyAsync(&flags, h->err_flags.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
+    KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    if (flags) {
+        KCHECK(h, cudaMemsetAsync(h->err_flags.p, 0, sizeof(int), h->stream), "clear flags");
+        if (flags & ERR_TIMEOUT) return h->fail(KURA_ETIMEOUT, "a bounded device-side wait gave up");
+        if (flags & ERR_NONFINITE) return h->fail(KURA_ENUMERIC, "non-finite phase or right-hand side");
+    }
+    return KURA_OK;
+}
+
+// Resolves a user vector: device pointer used as is, host pointer staged
+// through the handle's `user` buffer.
+kura_status stage_in(kura_t h, const double* src, const double** dev, bool* host)
+{
+    *host = !is_device_ptr(src);
+    if (*host) {
+        KCHECK(h, cudaMemcpyAsync(h->user.p, src, size_t(h->n) * 8, cudaMemcpyHostToDevice, h->stream), "copy in");
+        *dev = h->user.as<double>();
+    } else {
+        *dev = src;
+    }
+    return KURA_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+void kura_default_opts(kura_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = KURA_PREC_FP64;
+    o->scaling = KURA_SCALING_UNIFORM;
+    o->tau = 0.5;
+    o->keep_host_csr = 1;
+}
+
+int32_t kura_version(void) { return 100; }
+
+const char* kura_status_string(kura_status s)
+{
+    switch (s) {
+    case KURA_OK: return "ok";
+    case KURA_EINVAL: return "invalid argument";
+    case KURA_ENOMEM: return "out of memory";
+    case KURA_ECUDA: return "CUDA error";
+    case KURA_ESTATE: return "invalid state";
+    case KURA_ETIMEOUT: return "device wait timed out";
+    case KURA_ENUMERIC: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char* kura_last_error(kura_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
+                        int32_t n_comm, const double* omega, double K, const kura_opts* opts, void* stream,
+                        kura_t* out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
+    *out = nullptr;
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != KURA_PREC_FP64 && o.precision != KURA_PREC_MIXED) { g_create_error = "bad precision"; return KURA_EINVAL; }
+    if (o.scaling != KURA_SCALING_UNIFORM && o.scaling != KURA_SCALING_DEGREE) { g_create_error = "bad scaling"; return KURA_EINVAL; }
+    if (!omega || !std::isfinite(K)) { g_create_error = "omega is NULL or K is not finite"; return KURA_EINVAL; }
+    if (n > 0) {
+        for (int64_t i = 0; i < n; i++)
+            if (!std::isfinite(omega[i])) { g_create_error = "omega has a non-finite entry"; return KURA_EINVAL; }
+    }
+    PlanInput in;
+    in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
+    in.tile_max_rows = TILE_MAX_ROWS;
+    Plan plan;
+    std::string err;
+    int rc = build_plan(in, plan, err);
+    if (rc) { g_create_error = err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+        return KURA_ECUDA;
+    }
+    std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
+    if (!h) { g_create_error = "out of host memory"; return KURA_ENOMEM; }
+    cudaGetDevice(&h->device);
+    h->opts = o;
+    h->n = n;
+    h->n_comm = n_comm;
+    h->K = K;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->nnz = row_ptr[n];
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+        g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+        return KURA_ECUDA;
+    }
+    h->h_omega.assign(omega, omega + n);
+    if (o.keep_host_csr) {
+        h->h_row_ptr.assign(row_ptr, row_ptr + n + 1);
+        h->h_col.assign(col, col + row_ptr[n]);
+        h->h_label.assign(label, label + n);
+    }
+    kura_status st = build_device(h.get(), std::move(plan));
+    if (st != KURA_OK) { g_create_error = h->err; return st; }
+    *out = h.release();
+    return KURA_OK;
+}
+
+kura_status kura_get_stats(kura_t h, kura_block_stats* s)
+{
+    if (check_handle(h) || !s) return KURA_EINVAL;
+    std::memset(s, 0, sizeof *s);
+    const Plan& p = h->plan;
+    s->n = h->n;
+    s->nnz = h->nnz;
+    s->self_loops = p.self_loops;
+    s->n_comm = h->n_comm;
+    s->q_bits = h->q_bits;
+    s->tau = p.tau;
+    s->dense_blocks = p.dense_blocks;
+    s->sparse_blocks = p.sparse_blocks;
+    s->nonempty_blocks = p.nonempty_blocks;
+    s->missing_entries = h->miss_total;
+    s->sparse_entries = h->pres_total;
+    s->max_row_entries = p.max_row_entries;
+    s->tiles = h->n_tiles;
+    s->max_window = h->max_wlen;
+    const int64_t esize = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
+    // algorithmic bytes: 4 B per stored index + 24 B of row metadata per row
+    s->stream_bytes = 4 * (h->miss_total + h->pres_total) + 24 * h->n;
+    // row kernel per node: omega, y, krk (read+write), Y (write) or y (write), own entry
+    s->node_bytes_row = (8 + 8 + 16 + 8 + esize) * h->n;
+    // trig kernel per node: theta read, table write, community id
+    s->node_bytes_trig = (8 + esize + 4) * h->n;
+    s->direct_edges = h->nnz - p.self_loops;
+    return KURA_OK;
+}
+
+kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (tau >= 0) {
+        if (tau > 1.0) return h->fail(KURA_EINVAL, "tau must be in [0, 1]");
+        if (h->h_col.empty() && h->nnz > 0)
+            return h->fail(KURA_ESTATE, "re-classification needs the host CSR copy (keep_host_csr = 1)");
+        PlanInput in;
+        in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
+        in.n_comm = h->n_comm; in.tau = tau;
+        in.tile_max_rows = TILE_MAX_ROWS;
+        Plan plan;
+        std::string err;
+        int rc = build_plan(in, plan, err);
+        if (rc) return h->fail(rc == 2 ? KURA_ENOMEM : KURA_EINVAL, "%s", err.c_str());
+        KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise before re-classification");
+        kura_status st = build_device(h, std::move(plan));
+        if (st) return st;
+    }
+    return stats ? kura_get_stats(h, stats) : KURA_OK;
+}
+
+kura_status kura_set_stream(kura_t h, void* stream)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return KURA_OK;
+}
+
+kura_status kura_sync(kura_t h)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    return read_flags(h);
+}
+
+kura_status kura_rhs(kura_t h, const double* theta, double* dtheta)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
+    const double* th_dev;
+    bool host_in;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host_in)) return st;
+    const bool host_out = !is_device_ptr(dtheta);
+    cudaStream_t s = h->stream;
+    const DevGraph g = dev_graph(h);
+    RkArgs rk = rk_args(h, 0.0);
+    const unsigned nb = blocks_for(h->n, 256);
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), th_dev, h->Y.as<double>());
+    if (h->opts.precision == KURA_PREC_MIXED) {
+        launch_trig<MODE_MIXED>(h, g, h->Y.as<double>(), TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_MIXED>(h, g, rk, ST_RHS, s);
+    } else {
+        launch_trig<MODE_FP64>(h, g, h->Y.as<double>(), TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_FP64>(h, g, rk, ST_RHS, s);
+    }
+    double* out_dev = host_out ? h->user.as<double>() : dtheta;
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->fbuf.as<double>(), out_dev);
+    KCHECK(h, cudaGetLastError(), "launching the right-hand side");
+    if (host_out) {
+        KCHECK(h, cudaMemcpyAsync(dtheta, out_dev, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
+    }
+    return KURA_OK;
+}
+
+kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
+    if (!(step > 0) || !std::isfinite(step)) return h->fail(KURA_EINVAL, "step must be positive and finite");
+    if (n_steps < 0) return h->fail(KURA_EINVAL, "n_steps must be >= 0");
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    double* io = host ? h->user.as<double>() : theta;
+    cudaStream_t s = h->stream;
+    const unsigned nb = blocks_for(h->n, 256);
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), io, h->y.as<double>());
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    const int64_t chunk_max = 8;
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int64_t c = std::min(left, chunk_max);
+        auto key = std::make_pair(step, c * (h->timing ? -1 : 1));
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            std::unique_ptr<GraphEntry> ge(new GraphEntry());
+            if (h->timing) {
+                ge->events.resize(size_t(8 * c));
+                for (auto& e : ge->events) KCHECK(h, cudaEventCreate(&e), "cudaEventCreate");
+            }
+            cudaGraph_t graph = nullptr;
+            KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int64_t k = 0; k < c; k++)
+                enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
+            ec = cudaGraphInstantiate(&ge->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate graph");
+            it = h->graphs.emplace(key, std::move(ge)).first;
+        }
+        KCHECK(h, cudaGraphLaunch(it->second->exec, s), "graph launch");
+        h->last_graph = it->second.get();
+        left -= c;
+    }
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->y.as<double>(), io);
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    if (host) {
+        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
+    }
+    return KURA_OK;
+}
+
+kura_status kura_order_params(kura_t h, const double* theta, double* r, double* psi, double* r_comm,
+                              double* psi_comm)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta || !r || !psi) return h->fail(KURA_EINVAL, "NULL argument");
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    cudaStream_t s = h->stream;
+    const unsigned nb = blocks_for(h->n, 256);
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), th_dev, h->Y.as<double>());
+    const DevGraph g = dev_graph(h);
+    // order parameters always in FP64 (FP64 sin/cos, exact fixed-point sums)
+    launch_trig<MODE_FP64>(h, g, h->Y.as<double>(), 0, s);
+    k_order_finalize<<<blocks_for(std::max(h->n_comm, 1), 256), 256, 0, s>>>(
+        h->n_comm, h->n, h->bsum_out.as<long long>(), h->tot.as<long long>(), h->comm_off.as<int64_t>(),
+        std::ldexp(1.0, -h->q_bits), h->order_out.as<double>());
+    KCHECK(h, cudaGetLastError(), "launching the order parameters");
+    std::vector<double> res(size_t(2 + 2 * h->n_comm));
+    KCHECK(h, cudaMemcpyAsync(res.data(), h->order_out.p, res.size() * 8, cudaMemcpyDeviceToHost, s), "copy out");
+    kura_status st = read_flags(h);
+    if (st) return st;
+    *r = res[0];
+    *psi = res[1];
+    for (int32_t I = 0; I < h->n_comm; I++) {
+        if (r_comm) r_comm[I] = res[size_t(2 + 2 * I)];
+        if (psi_comm) psi_comm[I] = res[size_t(3 + 2 * I)];
+    }
+    return KURA_OK;
+}
+
+kura_status kura_set_param(kura_t h, const double* omega, const double* K)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (K) {
+        if (!std::isfinite(*K)) return h->fail(KURA_EINVAL, "K is not finite");
+        h->K = *K;
+        if (h->opts.scaling == KURA_SCALING_DEGREE) {
+            std::vector<double> rs(size_t(h->n));
+            for (int64_t v = 0; v < h->n; v++)
+                rs[size_t(v)] = h->plan.deg[size_t(v)] > 0 ? h->K / h->plan.deg[size_t(v)] : 0.0;
+            KCHECK(h, cudaMemcpyAsync(h->rscale.p, rs.data(), rs.size() * 8, cudaMemcpyHostToDevice, h->stream),
+                   "upload rscale");
+            KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+        }
+        h->graphs.clear();   // K / N is a kernel argument baked into the graphs
+        h->last_graph = nullptr;
+    }
+    if (omega) {
+        const double* om_dev;
+        bool host;
+        if (kura_status st = stage_in(h, omega, &om_dev, &host)) return st;
+        if (host) {
+            for (int64_t i = 0; i < h->n; i++)
+                if (!std::isfinite(omega[i])) return h->fail(KURA_EINVAL, "omega has a non-finite entry");
+            h->h_omega.assign(omega, omega + h->n);
+        }
+        k_gather_perm<<<blocks_for(h->n, 256), 256, 0, h->stream>>>(h->n, h->perm.as<int32_t>(), om_dev,
+                                                                       h->omega.as<double>());
+        KCHECK(h, cudaGetLastError(), "launching the permutation");
+        if (h->d_omega_user.p)
+            KCHECK(h, cudaMemcpyAsync(h->d_omega_user.p, om_dev, size_t(h->n) * 8, cudaMemcpyDeviceToDevice,
+                                      h->stream), "update omega");
+        if (host) KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    }
+    return KURA_OK;
+}
+
+static kura_status ensure_direct(kura_t h)
+{
+    if (h->d_col.p) return KURA_OK;
+    if (h->h_col.empty() && h->nnz > 0)
+        return h->fail(KURA_ESTATE, "the direct baseline needs the host CSR copy (keep_host_csr = 1)");
+    KCHECK(h, upload(h->d_row_ptr, h->h_row_ptr, h->stream), "upload row_ptr");
+    KCHECK(h, upload(h->d_col, h->h_col, h->stream), "upload col");
+    KCHECK(h, upload(h->d_omega_user, h->h_omega, h->stream), "upload omega");
+    KCHECK(h, h->red.alloc(4 * size_t(h->n)), "alloc reduced phases");
+    KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    return KURA_OK;
+}
+
+static void launch_direct(kura_t h, const double* th_user, double* out_user, int32_t precision, cudaStream_t s)
+{
+    const int deg = h->opts.scaling == KURA_SCALING_DEGREE;
+    const unsigned nbw = unsigned((h->n * 32 + 255) / 256);
+    if (precision == KURA_PREC_MIXED) {
+        k_reduce_phase<<<blocks_for(h->n, 256), 256, 0, s>>>(h->n, th_user, h->red.as<float>());
+        k_direct_fp32<<<nbw, 256, 0, s>>>(h->n, h->d_row_ptr.as<int64_t>(), h->d_col.as<int32_t>(),
+                                           h->d_omega_user.as<double>(), h->red.as<float>(), h->K, deg, out_user);
+    } else {
+        k_direct_fp64<<<nbw, 256, 0, s>>>(h->n, h->d_row_ptr.as<int64_t>(), h->d_col.as<int32_t>(),
+                                           h->d_omega_user.as<double>(), th_user, h->K, deg, out_user);
+    }
+}
+
+kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32_t precision)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
+    if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
+    if (kura_status st = ensure_direct(h)) return st;
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    const bool host_out = !is_device_ptr(dtheta);
+    double* out = host_out ? h->fbuf.as<double>() : dtheta;
+    launch_direct(h, th_dev, out, precision, h->stream);
+    KCHECK(h, cudaGetLastError(), "launching the direct baseline");
+    if (host_out) {
+        KCHECK(h, cudaMemcpyAsync(dtheta, out, size_t(h->n) * 8, cudaMemcpyDeviceToHost, h->stream), "copy out");
+        KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    }
+    return KURA_OK;
+}
+
+kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps, int32_t precision)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
+    if (!(step > 0) || !std::isfinite(step) || n_steps < 0) return h->fail(KURA_EINVAL, "bad step or n_steps");
+    if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
+    if (kura_status st = ensure_direct(h)) return st;
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    double* io = host ? h->user.as<double>() : theta;
+    cudaStream_t s = h->stream;
+    const unsigned nb = blocks_for(h->n, 256);
+    // the direct path works in user order: y = io
+    RkArgs rk{};
+    rk.y = io;
+    rk.y_out = io;
+    rk.Y = h->Y.as<double>();
+    rk.krk = h->krk.as<double>();
+    rk.h = step;
+    double* f = h->fbuf.as<double>();
+    for (int64_t k = 0; k < n_steps; k++) {
+        launch_direct(h, io, f, precision, s);
+        k_rk4_update<ST_1><<<nb, 256, 0, s>>>(h->n, f, rk);
+        launch_direct(h, h->Y.as<double>(), f, precision, s);
+        k_rk4_update<ST_2><<<nb, 256, 0, s>>>(h->n, f, rk);
+        launch_direct(h, h->Y.as<double>(), f, precision, s);
+        k_rk4_update<ST_3><<<nb, 256, 0, s>>>(h->n, f, rk);
+        launch_direct(h, h->Y.as<double>(), f, precision, s);
+        k_rk4_update<ST_4><<<nb, 256, 0, s>>>(h->n, f, rk);
+    }
+    KCHECK(h, cudaGetLastError(), "launching the direct baseline");
+    if (host) {
+        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        KCHECK(h, cudaStreamSynchronize(s), "synchronise");
+    }
+    return KURA_OK;
+}
+
+kura_status kura_set_timing(kura_t h, int32_t on)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    h->timing = on != 0;
+    return KURA_OK;
+}
+
+kura_status kura_kernel_times(kura_t h, float* ms, int32_t cap, int32_t* count)
+{
+    if (check_handle(h) || !count) return KURA_EINVAL;
+    *count = 0;
+    if (!h->last_graph || h->last_graph->events.empty()) return KURA_OK;
+    KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise");
+    const auto& ev = h->last_graph->events;
+    const int32_t avail = int32_t(ev.size() / 2);
+    for (int32_t k = 0; k < avail && k < cap && ms; k++)
+        KCHECK(h, cudaEventElapsedTime(&ms[k], ev[size_t(2 * k)], ev[size_t(2 * k + 1)]), "event time");
+    *count = avail;
+    return KURA_OK;
+}
+
+void kura_destroy(kura_t h) { delete h; }
+
+// ---------------------------------------------------------------- host-only plan
+struct kura_plan_s {
+    Plan p;
+};
+
+kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
+                            int32_t n_comm, double tau, kura_plan_t* out)
+{
+    g_create_error.clear();
+    if (!out) return KURA_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<kura_plan_s> p(new (std::nothrow) kura_plan_s());
+    if (!p) return KURA_ENOMEM;
+    PlanInput in;
+    in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = tau;
+    std::string err;
+    int rc = build_plan(in, p->p, err);
+    if (rc) { g_create_error = err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+    *out = p.release();
+    return KURA_OK;
+}
+
+kura_status kura_plan_stats(kura_plan_t pl, kura_block_stats* s)
+{
+    if (!pl || !s) return KURA_EINVAL;
+    const Plan& p = pl->p;
+    std::memset(s, 0, sizeof *s);
+    s->n = p.n;
+    s->nnz = p.nnz_in;
+    s->self_loops = p.self_loops;
+    s->n_comm = p.n_comm;
+    s->q_bits = 61 - ceil_log2(std::max<int64_t>(p.n, 2));
+    s->tau = p.tau;
+    s->dense_blocks = p.dense_blocks;
+    s->sparse_blocks = p.sparse_blocks;
+    s->nonempty_blocks = p.nonempty_blocks;
+    s->missing_entries = p.miss_total;
+    s->sparse_entries = p.pres_total;
+    s->max_row_entries = p.max_row_entries;
+    s->tiles = int64_t(p.tiles.size());
+    s->max_window = p.max_wlen;
+    s->stream_bytes = 4 * (p.miss_total + p.pres_total) + 24 * p.n;
+    s->node_bytes_row = (8 + 8 + 16 + 8 + 16) * p.n;
+    s->node_bytes_trig = (8 + 16 + 4) * p.n;
+    s->direct_edges = p.nnz_in - p.self_loops;
+    return KURA_OK;
+}
+
+kura_status kura_plan_perm(kura_plan_t pl, int32_t* perm, int64_t* comm_off)
+{
+    if (!pl) return KURA_EINVAL;
+    if (perm) std::copy(pl->p.perm.begin(), pl->p.perm.end(), perm);
+    if (comm_off) std::copy(pl->p.comm_off.begin(), pl->p.comm_off.end(), comm_off);
+    return KURA_OK;
+}
+
+kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t* n_missing, int32_t* present,
+                          int64_t* n_present, int64_t cap)
+{
+    if (!pl || !n_missing || !n_present) return KURA_EINVAL;
+    const Plan& p = pl->p;
+    if (row < 0 || row >= p.n) return KURA_EINVAL;
+    *n_missing = p.miss_cnt[size_t(row)];
+    *n_present = p.pres_cnt[size_t(row)];
+    for (int64_t k = 0; k < *n_missing && k < cap && missing; k++) missing[k] = p.miss[size_t(p.miss_off[size_t(row)] + k)];
+    for (int64_t k = 0; k < *n_present && k < cap && present; k++) present[k] = p.pres[size_t(p.pres_off[size_t(row)] + k)];
+    return KURA_OK;
+}
+
+kura_status kura_plan_dense_blocks(kura_plan_t pl, int32_t I, int32_t* J, int32_t cap, int32_t* count)
+{
+    if (!pl || !count || I < 0 || I >= pl->p.n_comm) return KURA_EINVAL;
+    const Plan& p = pl->p;
+    *count = int32_t(p.dptr[size_t(I) + 1] - p.dptr[size_t(I)]);
+    for (int32_t k = 0; k < *count && k < cap && J; k++) J[k] = p.dcol[size_t(p.dptr[size_t(I)] + k)];
+    return KURA_OK;
+}
+
+void kura_plan_destroy(kura_plan_t p) { delete p; }
+
+}  // extern "C"

@@ -1,0 +1,503 @@
+// CUDA kernels (sm_103a) of the localised-order-parameter right-hand side
+// and the fused RK4 stage (arXiv 2102.07167, eq:KuramotoGraphApproach).
+//
+// Per right-hand-side evaluation:
+//   k_trig_blocksum  sin/cos of every phase -> table, block sums S_J, C_J
+//                    (exact 64-bit fixed point, order independent), then in
+//                    the last CTA: T_I = sum_{J in D(I)} (S_J, C_J)
+//   k_row_stage      per row: T_I - sum over missing entries + sum over
+//                    sparse entries, then f = omega + scale (c acc_s - s acc_c)
+//                    and the RK4 stage update, fused
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace kura {
+
+constexpr int ROW_THREADS = 512;
+constexpr int ROW_WARPS = ROW_THREADS / 32;
+constexpr int TILE_MAX_ROWS = 1024;     // stash capacity of the row kernel (matches the planner)
+constexpr int TRIG_THREADS = 256;
+
+enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
+enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4 };
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+enum : int { TB_TABLE = 1, TB_T = 2 };   // what k_trig_blocksum writes
+
+// 2 pi split in two doubles (Cody-Waite style): hi = nearest double, lo = remainder
+#define KURA_TWO_PI_HI 6.283185307179586232
+#define KURA_TWO_PI_LO 2.4492935982947064e-16
+#define KURA_INV_TWO_PI 0.15915494309189533577
+
+template <int MODE> struct EntryT;
+template <> struct EntryT<MODE_FP64> { using T = longlong2; using A = long long; };   // fixed-point (sin, cos)
+template <> struct EntryT<MODE_MIXED> { using T = float2; using A = float; };        // FP32 (sin, cos)
+
+// All device pointers of a handle; passed by value.
+struct DevGraph {
+    int64_t n;
+    int32_t n_comm;
+    int32_t q_bits;
+    double scale_q, inv_scale_q;            // 2^q, 2^-q
+    double scale;                           // K / N (uniform scaling)
+    const double* rscale;                   // per permuted row K / calM_m (degree scaling) or null
+    const int32_t* node_comm;               // [n]
+    const int64_t* miss_off;                // [n+1]
+    const int64_t* pres_off;                // [n+1]
+    const int32_t* miss_cnt;                // [n]
+    const int32_t* pres_cnt;                // [n]
+    const int32_t* miss;                    // missing entries of dense blocks (permuted columns)
+    const int32_t* pres;                    // present entries of sparse blocks
+    const Tile* tiles;
+    const int64_t* dptr;                    // [n_comm+1]
+    const int32_t* dcol;
+    const int64_t* comm_off;                // [n_comm+1]
+    const double* omega;                    // [n] permuted
+    void* table;                            // EntryT<MODE>::T [n + 2]
+    unsigned long long* bsum;               // [2 n_comm] accumulators, zero between launches
+    long long* bsum_out;                    // [2 n_comm] last block sums (S_J, C_J)
+    long long* tot;                         // [2] last totals
+    void* T;                                // FP64: longlong2[n_comm]; MIXED: double2[n_comm]
+    unsigned int* counter;                  // last-CTA ticket, zero between launches
+    int* err;                               // latched error bits
+};
+
+struct RkArgs {
+    const double* y;      // state at the start of the step (permuted)
+    double* y_out;        // stage 4 writes the new state here (== y)
+    double* Y;            // next stage input
+    double* krk;          // k1 + 2 k2 + 2 k3 accumulator
+    double* out;          // ST_RHS: f
+    double h;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// TMA bulk copy global -> shared, completion signalled on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the barrier phase with a time limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 31u && globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- trig + block sums
+// One node per thread.  Writes the (sin, cos) table (TB_TABLE), accumulates
+// the fixed-point block sums with warp-aggregated 64-bit integer atomics
+// (integer addition is associative, so the sums do not depend on the order
+// of the atomics), and the last CTA to finish forms T_I (TB_T), copies the
+// block sums and totals out and re-zeroes the accumulators for the next use.
+template <int MODE, int WHAT>
+__global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, const double* __restrict__ theta)
+{
+    const int64_t i = int64_t(blockIdx.x) * TRIG_THREADS + threadIdx.x;
+    long long sf = 0, cf = 0;
+    int J = -1;
+    if (i < g.n) {
+        const double th = theta[i];
+        if (!isfinite(th)) atomicOr(g.err, ERR_NONFINITE);
+        if (MODE == MODE_FP64) {
+            double s, c;
+            sincos(th, &s, &c);
+            sf = __double2ll_rn(s * g.scale_q);
+            cf = __double2ll_rn(c * g.scale_q);
+            if (WHAT & TB_TABLE) reinterpret_cast<longlong2*>(g.table)[i] = make_longlong2(sf, cf);
+        } else {
+            // reduce mod 2 pi in FP64, then FP32 sin/cos of |r| <= pi
+            const double k = rint(th * KURA_INV_TWO_PI);
+            double r = fma(-k, KURA_TWO_PI_HI, th);
+            r = fma(-k, KURA_TWO_PI_LO, r);
+            float s, c;
+            sincosf(static_cast<float>(r), &s, &c);
+            const float sq = static_cast<float>(g.scale_q);
+            sf = __float2ll_rn(s * sq);
+            cf = __float2ll_rn(c * sq);
+            if (WHAT & TB_TABLE) reinterpret_cast<float2*>(g.table)[i] = make_float2(s, c);
+        }
+        J = g.node_comm[i];
+    }
+    const unsigned full = 0xffffffffu;
+    const int J0 = __shfl_sync(full, J, 0);
+    if (__all_sync(full, J == J0) && J0 >= 0) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sf += __shfl_xor_sync(full, sf, o);
+            cf += __shfl_xor_sync(full, cf, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&g.bsum[2 * J0], static_cast<unsigned long long>(sf));
+            atomicAdd(&g.bsum[2 * J0 + 1], static_cast<unsigned long long>(cf));
+        }
+    } else if (J >= 0) {
+        atomicAdd(&g.bsum[2 * J], static_cast<unsigned long long>(sf));
+        atomicAdd(&g.bsum[2 * J + 1], static_cast<unsigned long long>(cf));
+    }
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(g.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const long long* bs = reinterpret_cast<const long long*>(g.bsum);
+    if (WHAT & TB_T) {
+        for (int I = threadIdx.x; I < g.n_comm; I += TRIG_THREADS) {
+            long long ts = 0, tc = 0;
+            for (int64_t k = g.dptr[I]; k < g.dptr[I + 1]; k++) {
+                const int Jd = g.dcol[k];
+                ts += __ldcg(bs + 2 * Jd);
+                tc += __ldcg(bs + 2 * Jd + 1);
+            }
+            if (MODE == MODE_FP64)
+                reinterpret_cast<longlong2*>(g.T)[I] = make_longlong2(ts, tc);
+            else
+                reinterpret_cast<double2*>(g.T)[I] =
+                    make_double2(static_cast<double>(ts) * g.inv_scale_q, static_cast<double>(tc) * g.inv_scale_q);
+        }
+    }
+    __syncthreads();
+    long long s_loc = 0, c_loc = 0;
+    for (int Jj = threadIdx.x; Jj < g.n_comm; Jj += TRIG_THREADS) {
+        const long long s = __ldcg(bs + 2 * Jj), c = __ldcg(bs + 2 * Jj + 1);
+        g.bsum_out[2 * Jj] = s;
+        g.bsum_out[2 * Jj + 1] = c;
+        s_loc += s;
+        c_loc += c;
+        g.bsum[2 * Jj] = 0ull;
+        g.bsum[2 * Jj + 1] = 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s_loc += __shfl_xor_sync(full, s_loc, o);
+        c_loc += __shfl_xor_sync(full, c_loc, o);
+    }
+    __shared__ long long red[2][TRIG_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s_loc;
+        red[1][threadIdx.x >> 5] = c_loc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0;
+        for (int w = 0; w < TRIG_THREADS / 32; w++) { a += red[0][w]; b += red[1][w]; }
+        g.tot[0] = a;
+        g.tot[1] = b;
+        __threadfence();
+        *g.counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- fused row kernel
+template <int MODE>
+__device__ __forceinline__ typename EntryT<MODE>::T gather_entry(const typename EntryT<MODE>::T* win, int wbeg,
+                                                                 int wlen, const typename EntryT<MODE>::T* table,
+                                                                 int j)
+{
+    const unsigned u = static_cast<unsigned>(j - wbeg);
+    if (u < static_cast<unsigned>(wlen)) return win[u];
+    return __ldg(table + j);
+}
+
+template <int MODE>
+struct Acc2 {
+    typename EntryT<MODE>::A s, c;
+};
+
+// Sums the entries of one stream segment into (as, ac) with sign SIGN.
+template <int MODE, int SIGN>
+__device__ __forceinline__ void sum_segment(const int32_t* __restrict__ seg, int cnt, int lane,
+                                            const typename EntryT<MODE>::T* win, int wbeg, int wlen,
+                                            const typename EntryT<MODE>::T* table,
+                                            typename EntryT<MODE>::A& as, typename EntryT<MODE>::A& ac)
+{
+    const int4* v4 = reinterpret_cast<const int4*>(seg);
+#pragma unroll 2
+    for (int q = lane; q * 4 < cnt; q += 32) {
+        const int4 v = __ldcs(v4 + q);
+        const int b = q * 4;
+        const int idx[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            if (b + t < cnt) {
+                const auto e = gather_entry<MODE>(win, wbeg, wlen, table, idx[t]);
+                if (SIGN > 0) { as += e.x; ac += e.y; }
+                else          { as -= e.x; ac -= e.y; }
+            }
+        }
+    }
+}
+
+template <int MODE, int STAGE>
+__global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk)
+{
+    using E = typename EntryT<MODE>::T;
+    using A = typename EntryT<MODE>::A;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ Acc2<MODE> stash[TILE_MAX_ROWS];
+    __shared__ int abort_flag;
+
+    const Tile t = g.tiles[blockIdx.x];
+    const E* table = reinterpret_cast<const E*>(g.table);
+    E* win = reinterpret_cast<E*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- stage the community's (sin, cos) window with one TMA bulk copy
+    if (tid == 0) abort_flag = 0;
+    if (t.wlen > 0) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            const uint32_t bytes = static_cast<uint32_t>(t.wlen) * static_cast<uint32_t>(sizeof(E));
+            mbar_arrive_expect_tx(&bar, bytes);
+            bulk_g2s(win, table + t.wbeg, bytes, &bar);
+        }
+        __syncthreads();
+        if (!mbar_wait_bounded(&bar, 0, 1000000000ull)) {
+            atomicOr(g.err, ERR_TIMEOUT);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) {
+            // give the copy in flight one more bounded chance to land before leaving
+            if (tid == 0) mbar_wait_bounded(&bar, 0, 1000000000ull);
+            __syncthreads();
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
+
+    // ---- one warp per row: gathers of the correction streams
+    const int nrows = t.r1 - t.r0;
+    for (int k = warp; k < nrows; k += ROW_WARPS) {
+        const int64_t row = int64_t(t.r0) + k;
+        A as = 0, ac = 0;
+        sum_segment<MODE, -1>(g.miss + g.miss_off[row], g.miss_cnt[row], lane, win, t.wbeg, t.wlen, table, as, ac);
+        sum_segment<MODE, +1>(g.pres + g.pres_off[row], g.pres_cnt[row], lane, win, t.wbeg, t.wlen, table, as, ac);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            as += __shfl_xor_sync(0xffffffffu, as, o);
+            ac += __shfl_xor_sync(0xffffffffu, ac, o);
+        }
+        if (lane == 0) stash[k] = Acc2<MODE>{as, ac};
+    }
+    __syncthreads();
+
+    // ---- one thread per row: the right-hand side and the RK4 stage, FP64
+    for (int k = tid; k < nrows; k += ROW_THREADS) {
+        const int64_t row = int64_t(t.r0) + k;
+        const Acc2<MODE> a = stash[k];
+        const E own = gather_entry<MODE>(win, t.wbeg, t.wlen, table, static_cast<int>(row));
+        double acc_s, acc_c, si, ci;
+        if (MODE == MODE_FP64) {
+            const longlong2 T = reinterpret_cast<const longlong2*>(g.T)[t.comm];
+            acc_s = static_cast<double>(T.x + static_cast<long long>(a.s)) * g.inv_scale_q;
+            acc_c = static_cast<double>(T.y + static_cast<long long>(a.c)) * g.inv_scale_q;
+            si = static_cast<double>(own.x) * g.inv_scale_q;
+            ci = static_cast<double>(own.y) * g.inv_scale_q;
+        } else {
+            const double2 T = reinterpret_cast<const double2*>(g.T)[t.comm];
+            acc_s = T.x + static_cast<double>(a.s);
+            acc_c = T.y + static_cast<double>(a.c);
+            si = static_cast<double>(own.x);
+            ci = static_cast<double>(own.y);
+        }
+        const double sc = g.rscale ? g.rscale[row] : g.scale;
+        const double f = g.omega[row] + sc * (ci * acc_s - si * acc_c);
+        if (!isfinite(f)) atomicOr(g.err, ERR_NONFINITE);
+        if (STAGE == ST_RHS) {
+            rk.out[row] = f;
+        } else if (STAGE == ST_1) {
+            rk.krk[row] = f;
+            rk.Y[row] = rk.y[row] + (0.5 * rk.h) * f;
+        } else if (STAGE == ST_2) {
+            rk.krk[row] = rk.krk[row] + 2.0 * f;
+            rk.Y[row] = rk.y[row] + (0.5 * rk.h) * f;
+        } else if (STAGE == ST_3) {
+            rk.krk[row] = rk.krk[row] + 2.0 * f;
+            rk.Y[row] = rk.y[row] + rk.h * f;
+        } else {
+            rk.y_out[row] = rk.y[row] + (rk.h / 6.0) * (rk.krk[row] + f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- order parameters
+// out[0] = r, out[1] = psi, out[2 + 2I] = r_I, out[3 + 2I] = psi_I (eq:OrderParameter)
+__global__ void k_order_finalize(int32_t n_comm, int64_t n, const long long* bsum_out, const long long* tot,
+                                 const int64_t* comm_off, double inv_scale_q, double* out)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I == 0) {
+        const double s = static_cast<double>(tot[0]) * inv_scale_q / static_cast<double>(n);
+        const double c = static_cast<double>(tot[1]) * inv_scale_q / static_cast<double>(n);
+        const double r = sqrt(s * s + c * c);
+        out[0] = r;
+        out[1] = (r == 0.0) ? 0.0 : atan2(s, c);
+    }
+    if (I < n_comm) {
+        const int64_t m = comm_off[I + 1] - comm_off[I];
+        double r = 0, psi = 0;
+        if (m > 0) {
+            const double s = static_cast<double>(bsum_out[2 * I]) * inv_scale_q / static_cast<double>(m);
+            const double c = static_cast<double>(bsum_out[2 * I + 1]) * inv_scale_q / static_cast<double>(m);
+            r = sqrt(s * s + c * c);
+            psi = (r == 0.0) ? 0.0 : atan2(s, c);
+        }
+        out[2 + 2 * I] = r;
+        out[3 + 2 * I] = psi;
+    }
+}
+
+// ---------------------------------------------------------------- permutation at the boundary
+__global__ void k_gather_perm(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src_user,
+                              double* __restrict__ dst_perm)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) dst_perm[i] = src_user[perm[i]];
+}
+__global__ void k_scatter_perm(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src_perm,
+                               double* __restrict__ dst_user)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) dst_user[perm[i]] = src_perm[i];
+}
+
+// ---------------------------------------------------------------- direct-summation baseline
+// One warp per row of the user-order CSR; one sine per edge (eq:KuramotoGraph
+// in its original form).  FP64: FP64 sine of the FP64 difference.
+__global__ void __launch_bounds__(256) k_direct_fp64(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const double* __restrict__ omega,
+                                                     const double* __restrict__ theta, double K, int degree_scaling,
+                                                     double* __restrict__ out)
+{
+    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const double th = theta[row];
+    double acc = 0.0;
+    int deg = 0;
+    for (int64_t e = row_ptr[row] + lane; e < row_ptr[row + 1]; e += 32) {
+        const int c = __ldcs(col + e);
+        if (c == row) continue;
+        acc += sin(__ldg(theta + c) - th);
+        deg++;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        deg += __shfl_xor_sync(0xffffffffu, deg, o);
+    }
+    if (lane == 0) {
+        double sc = degree_scaling ? (deg > 0 ? K / deg : 0.0) : K / static_cast<double>(n);
+        out[row] = omega[row] + sc * acc;
+    }
+}
+
+// FP32 variant: phases reduced mod 2 pi once per evaluation (k_reduce_phase),
+// FP32 sine per edge, FP32 row sums, FP64 epilogue.
+__global__ void k_reduce_phase(int64_t n, const double* __restrict__ theta, float* __restrict__ red)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double th = theta[i];
+    const double k = rint(th * KURA_INV_TWO_PI);
+    double r = fma(-k, KURA_TWO_PI_HI, th);
+    r = fma(-k, KURA_TWO_PI_LO, r);
+    red[i] = static_cast<float>(r);
+}
+__global__ void __launch_bounds__(256) k_direct_fp32(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const double* __restrict__ omega,
+                                                     const float* __restrict__ red, double K, int degree_scaling,
+                                                     double* __restrict__ out)
+{
+    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float th = red[row];
+    float acc = 0.f;
+    int deg = 0;
+    for (int64_t e = row_ptr[row] + lane; e < row_ptr[row + 1]; e += 32) {
+        const int c = __ldcs(col + e);
+        if (c == row) continue;
+        acc += sinf(__ldg(red + c) - th);
+        deg++;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        deg += __shfl_xor_sync(0xffffffffu, deg, o);
+    }
+    if (lane == 0) {
+        double sc = degree_scaling ? (deg > 0 ? K / deg : 0.0) : K / static_cast<double>(n);
+        out[row] = omega[row] + sc * static_cast<double>(acc);
+    }
+}
+
+// RK4 stage update for a precomputed right-hand side f (direct baseline).
+template <int STAGE>
+__global__ void k_rk4_update(int64_t n, const double* __restrict__ f, RkArgs rk)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double fi = f[i];
+    if (STAGE == ST_1) {
+        rk.krk[i] = fi;
+        rk.Y[i] = rk.y[i] + (0.5 * rk.h) * fi;
+    } else if (STAGE == ST_2) {
+        rk.krk[i] = rk.krk[i] + 2.0 * fi;
+        rk.Y[i] = rk.y[i] + (0.5 * rk.h) * fi;
+    } else if (STAGE == ST_3) {
+        rk.krk[i] = rk.krk[i] + 2.0 * fi;
+        rk.Y[i] = rk.y[i] + rk.h * fi;
+    } else {
+        rk.y_out[i] = rk.y[i] + (rk.h / 6.0) * (rk.krk[i] + fi);
+    }
+}
+
+}  // namespace kura

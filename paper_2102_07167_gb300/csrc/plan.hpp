@@ -1,0 +1,66 @@
+// Host-side block plan for the localised-order-parameter right-hand side
+// (eq:KuramotoGraphApproach, Sec. 3 of arXiv 2102.07167).
+//
+// The plan permutes the nodes so that communities are contiguous (P A P^T,
+// Sec. 3 "Community detection in graphs"), classifies every block (I, J) as
+// dense or sparse by its zero fraction, and writes two correction streams per
+// row: the missing entries of the row's dense blocks ("zeros", subtracted from
+// the precomputed block sums) and the present entries of its sparse blocks
+// (summed directly).  It also cuts the rows into tiles for the row kernel.
+// Pure host code: no CUDA here, so the planner is testable without a GPU.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace kura {
+
+struct Tile {              // 32 bytes, read by the row kernel
+    int32_t r0, r1;        // rows [r0, r1) in permuted order, all in one community
+    int32_t comm;          // community of the rows
+    int32_t wbeg, wlen;    // staged table window [wbeg, wbeg + wlen) (wlen = 0: none)
+    int32_t pad[3];
+};
+
+struct PlanInput {
+    int64_t n = 0;
+    const int64_t* row_ptr = nullptr;   // [n+1]
+    const int32_t* col = nullptr;       // [nnz], strictly increasing per row
+    const int32_t* label = nullptr;     // [n] in [0, n_comm)
+    int32_t n_comm = 0;
+    double tau = 0.5;                   // dense iff zero fraction < tau
+    int32_t window_cap = 4096;          // max staged window entries per tile
+    int64_t tile_work = 0;              // target entries per tile (0: automatic)
+    int32_t tile_max_rows = 1024;
+};
+
+struct Plan {
+    int64_t n = 0;
+    int32_t n_comm = 0;
+    double tau = 0.5;
+    int64_t nnz_in = 0, self_loops = 0;
+    std::vector<int32_t> perm;          // perm[new] = old (stable sort by label)
+    std::vector<int32_t> inv_perm;      // inv_perm[old] = new
+    std::vector<int64_t> comm_off;      // [n_comm+1] community boundaries (permuted order)
+    std::vector<int32_t> node_comm;     // [n] community of each permuted node
+    std::vector<int32_t> deg;           // [n] degree without self-loops (permuted order)
+    std::vector<int64_t> dptr;          // [n_comm+1] dense column blocks of each row block
+    std::vector<int32_t> dcol;
+    // per-row streams; offsets in elements, each segment starts on a 16-byte
+    // boundary (multiple of 4 int32) and is zero-padded to one
+    std::vector<int64_t> miss_off, pres_off;
+    std::vector<int32_t> miss_cnt, pres_cnt;
+    std::vector<int32_t> miss, pres;    // permuted global column indices
+    std::vector<Tile> tiles;
+    int32_t max_wlen = 0;
+    // statistics
+    int64_t dense_blocks = 0, sparse_blocks = 0, nonempty_blocks = 0;
+    int64_t miss_total = 0, pres_total = 0;
+    int64_t max_row_entries = 0;
+};
+
+// Validates the CSR and labels and builds the plan.  Returns 0, or 1 with a
+// message for invalid input, 2 for allocation failure.
+int build_plan(const PlanInput& in, Plan& out, std::string& err);
+
+}  // namespace kura

@@ -1,0 +1,353 @@
+"""Thin ctypes binding of libkura (include/kura.h).
+
+Every function named ``kura_*`` here has the name, arguments and meaning of
+the C entry point of the same name; it only marshals arguments (torch tensors
+or numpy arrays to pointers, Python numbers to C scalars) and raises
+``KuraError`` for a non-zero status.  All computation happens in the
+library's CUDA kernels; if ``libkura.so`` is missing, loading raises instead
+of falling back to anything else.  ``Kuramoto`` bundles a handle with these
+calls for convenience.
+
+The method: Kuramoto model on graphs with localised order parameters
+(arXiv 2102.07167, eq:KuramotoGraph and eq:KuramotoGraphApproach, Sec. 3),
+integrated by classical RK4.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkura.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "kura.h")
+
+KURA_OK, KURA_EINVAL, KURA_ENOMEM, KURA_ECUDA, KURA_ESTATE, KURA_ETIMEOUT, KURA_ENUMERIC = range(7)
+PREC_FP64, PREC_MIXED = 0, 1
+SCALING_UNIFORM, SCALING_DEGREE = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KuraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libkura status {status}: {msg}")
+        self.status = status
+
+
+class KuraOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("scaling", C.c_int32), ("tau", C.c_double),
+                ("keep_host_csr", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class KuraBlockStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("self_loops", C.c_int64),
+                ("n_comm", C.c_int32), ("q_bits", C.c_int32), ("tau", C.c_double),
+                ("dense_blocks", C.c_int64), ("sparse_blocks", C.c_int64), ("nonempty_blocks", C.c_int64),
+                ("missing_entries", C.c_int64), ("sparse_entries", C.c_int64), ("max_row_entries", C.c_int64),
+                ("tiles", C.c_int64), ("max_window", C.c_int64),
+                ("stream_bytes", C.c_int64), ("node_bytes_row", C.c_int64), ("node_bytes_trig", C.c_int64),
+                ("direct_edges", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/kura.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(kura_[a-z_0-9]+)\s*\(", txt)))
+
+
+def load() -> C.CDLL:
+    """Loads libkura.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first "
+                               "(there is no fallback path)")
+        L = C.CDLL(LIB_PATH)
+        P, I64, I32, D, S = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_int
+        sig = {
+            "kura_default_opts": (None, [C.POINTER(KuraOpts)]),
+            "kura_version": (I32, []),
+            "kura_status_string": (C.c_char_p, [S]),
+            "kura_create": (S, [I64, P, P, P, I32, P, D, C.POINTER(KuraOpts), P, C.POINTER(P)]),
+            "kura_classify_blocks": (S, [P, D, C.POINTER(KuraBlockStats)]),
+            "kura_get_stats": (S, [P, C.POINTER(KuraBlockStats)]),
+            "kura_rhs": (S, [P, P, P]),
+            "kura_rk4_steps": (S, [P, P, D, I64]),
+            "kura_order_params": (S, [P, P, C.POINTER(D), C.POINTER(D), P, P]),
+            "kura_set_param": (S, [P, P, P]),
+            "kura_direct_rhs": (S, [P, P, P, I32]),
+            "kura_direct_rk4_steps": (S, [P, P, D, I64, I32]),
+            "kura_set_timing": (S, [P, I32]),
+            "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
+            "kura_set_stream": (S, [P, P]),
+            "kura_sync": (S, [P]),
+            "kura_last_error": (C.c_char_p, [P]),
+            "kura_destroy": (None, [P]),
+            "kura_plan_build": (S, [I64, P, P, P, I32, D, C.POINTER(P)]),
+            "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
+            "kura_plan_perm": (S, [P, P, P]),
+            "kura_plan_row": (S, [P, I64, P, C.POINTER(I64), P, C.POINTER(I64), I64]),
+            "kura_plan_dense_blocks": (S, [P, I32, P, I32, C.POINTER(I32)]),
+            "kura_plan_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+# ----------------------------------------------------------------------------- marshalling
+def _ptr(x, dtype=np.float64, n: Optional[int] = None):
+    """Pointer to a contiguous torch tensor (any device) or numpy array; None -> NULL."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):                     # torch tensor
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64,
+                np.float32: torch.float32}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        if n is not None and x.numel() < n:
+            raise ValueError(f"tensor has {x.numel()} elements, need {n}")
+        return x.data_ptr()
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    if n is not None and x.size < n:
+        raise ValueError(f"array has {x.size} elements, need {n}")
+    return x.ctypes.data
+
+
+def _check(rc: int, h=None):
+    if rc != KURA_OK:
+        L = load()
+        msg = L.kura_last_error(h)
+        raise KuraError(rc, (msg or b"").decode() or L.kura_status_string(rc).decode())
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+# ----------------------------------------------------------------------------- C-ABI mirrors
+def kura_default_opts() -> KuraOpts:
+    o = KuraOpts()
+    load().kura_default_opts(C.byref(o))
+    return o
+
+
+def kura_version() -> int:
+    return int(load().kura_version())
+
+
+def kura_create(n, row_ptr, col, label, n_comm, omega, K, opts: Optional[KuraOpts] = None, stream=None):
+    h = C.c_void_p()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    if row_ptr.size != n + 1 or label.size != n or omega.size != n:
+        raise ValueError("row_ptr must have n+1 entries, label and omega n")
+    if col.size < int(row_ptr[-1]):
+        raise ValueError("col shorter than row_ptr[n]")
+    s = _current_stream() if stream is None else int(stream)
+    rc = load().kura_create(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                            label.ctypes.data, int(n_comm), omega.ctypes.data, float(K),
+                            C.byref(opts) if opts is not None else None, s or None, C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def kura_classify_blocks(h, tau: float = -1.0) -> dict:
+    st = KuraBlockStats()
+    _check(load().kura_classify_blocks(h, float(tau), C.byref(st)), h)
+    return st.as_dict()
+
+
+def kura_get_stats(h) -> dict:
+    st = KuraBlockStats()
+    _check(load().kura_get_stats(h, C.byref(st)), h)
+    return st.as_dict()
+
+
+def kura_rhs(h, theta, dtheta, n):
+    _check(load().kura_rhs(h, _ptr(theta, n=n), _ptr(dtheta, n=n)), h)
+
+
+def kura_rk4_steps(h, theta, step, n_steps, n):
+    _check(load().kura_rk4_steps(h, _ptr(theta, n=n), float(step), int(n_steps)), h)
+
+
+def kura_order_params(h, theta, n, n_comm, per_community: bool = False):
+    r, psi = C.c_double(), C.c_double()
+    rc_ = np.zeros(n_comm) if per_community else None
+    pc_ = np.zeros(n_comm) if per_community else None
+    _check(load().kura_order_params(h, _ptr(theta, n=n), C.byref(r), C.byref(psi),
+                                    _ptr(rc_) if per_community else None,
+                                    _ptr(pc_) if per_community else None), h)
+    return (r.value, psi.value, rc_, pc_) if per_community else (r.value, psi.value)
+
+
+def kura_set_param(h, omega=None, K=None, n=None):
+    k = C.c_double(float(K)) if K is not None else None
+    _check(load().kura_set_param(h, _ptr(omega, n=n), C.byref(k) if k is not None else None), h)
+
+
+def kura_direct_rhs(h, theta, dtheta, precision, n):
+    _check(load().kura_direct_rhs(h, _ptr(theta, n=n), _ptr(dtheta, n=n), int(precision)), h)
+
+
+def kura_direct_rk4_steps(h, theta, step, n_steps, precision, n):
+    _check(load().kura_direct_rk4_steps(h, _ptr(theta, n=n), float(step), int(n_steps), int(precision)), h)
+
+
+def kura_set_timing(h, on: bool):
+    _check(load().kura_set_timing(h, 1 if on else 0), h)
+
+
+def kura_kernel_times(h, cap: int = 4096) -> np.ndarray:
+    buf = np.zeros(cap, dtype=np.float32)
+    cnt = C.c_int32()
+    _check(load().kura_kernel_times(h, buf.ctypes.data, cap, C.byref(cnt)), h)
+    return buf[:min(cnt.value, cap)].copy()
+
+
+def kura_set_stream(h, stream):
+    _check(load().kura_set_stream(h, int(stream) or None), h)
+
+
+def kura_sync(h):
+    _check(load().kura_sync(h), h)
+
+
+def kura_last_error(h=None) -> str:
+    return (load().kura_last_error(h) or b"").decode()
+
+
+def kura_destroy(h):
+    load().kura_destroy(h)
+
+
+def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5):
+    p = C.c_void_p()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    rc = load().kura_plan_build(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                label.ctypes.data, int(n_comm), float(tau), C.byref(p))
+    _check(rc, None)
+    return p
+
+
+def kura_plan_stats(p) -> dict:
+    st = KuraBlockStats()
+    _check(load().kura_plan_stats(p, C.byref(st)))
+    return st.as_dict()
+
+
+def kura_plan_perm(p, n, n_comm):
+    perm = np.empty(n, dtype=np.int32)
+    off = np.empty(n_comm + 1, dtype=np.int64)
+    _check(load().kura_plan_perm(p, perm.ctypes.data, off.ctypes.data))
+    return perm, off
+
+
+def kura_plan_row(p, row, cap):
+    miss = np.empty(max(cap, 1), dtype=np.int32)
+    pres = np.empty(max(cap, 1), dtype=np.int32)
+    nm, np_ = C.c_int64(), C.c_int64()
+    _check(load().kura_plan_row(p, int(row), miss.ctypes.data, C.byref(nm), pres.ctypes.data, C.byref(np_),
+                                int(cap)))
+    return miss[:nm.value].copy(), pres[:np_.value].copy()
+
+
+def kura_plan_dense_blocks(p, I, cap=1 << 16):
+    buf = np.empty(cap, dtype=np.int32)
+    cnt = C.c_int32()
+    _check(load().kura_plan_dense_blocks(p, int(I), buf.ctypes.data, int(cap), C.byref(cnt)))
+    return buf[:cnt.value].copy()
+
+
+def kura_plan_destroy(p):
+    load().kura_plan_destroy(p)
+
+
+# ----------------------------------------------------------------------------- convenience wrapper
+class Kuramoto:
+    """A libkura handle: the graph, omega and K resident on the GPU."""
+
+    def __init__(self, row_ptr, col, label, n_comm, omega, K, precision=PREC_FP64,
+                 scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None):
+        self.n = int(np.asarray(row_ptr).shape[0] - 1)
+        self.n_comm = int(n_comm)
+        o = kura_default_opts()
+        o.precision, o.scaling, o.tau, o.keep_host_csr = int(precision), int(scaling), float(tau), int(keep_host_csr)
+        self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
+
+    def rhs(self, theta, out):
+        kura_rhs(self.h, theta, out, self.n)
+
+    def rk4_steps(self, theta, step, n_steps):
+        kura_rk4_steps(self.h, theta, step, n_steps, self.n)
+
+    def order_params(self, theta, per_community=False):
+        return kura_order_params(self.h, theta, self.n, self.n_comm, per_community)
+
+    def set_param(self, omega=None, K=None):
+        kura_set_param(self.h, omega, K, self.n)
+
+    def classify_blocks(self, tau=-1.0):
+        return kura_classify_blocks(self.h, tau)
+
+    def stats(self):
+        return kura_get_stats(self.h)
+
+    def direct_rhs(self, theta, out, precision=PREC_FP64):
+        kura_direct_rhs(self.h, theta, out, precision, self.n)
+
+    def direct_rk4_steps(self, theta, step, n_steps, precision=PREC_FP64):
+        kura_direct_rk4_steps(self.h, theta, step, n_steps, precision, self.n)
+
+    def set_timing(self, on=True):
+        kura_set_timing(self.h, on)
+
+    def kernel_times(self, cap=4096):
+        return kura_kernel_times(self.h, cap)
+
+    def sync(self):
+        kura_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kura_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

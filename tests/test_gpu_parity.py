@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances (spec readings):
+  FP64 right-hand side:   |df_i| <= 1e-11 (1 + deg_i)
+  mixed right-hand side:  |df_i| <= 2e-4 (1 + deg_i) max(1, |f_i|)
+  FP64 RK4 trajectories:  |dtheta_i| <= 1e-8
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_07167_gb300 import gen as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2102_07167_gb300 import kura
+
+
+def _dev(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda:0")
+
+
+def _tol_fp64(g):
+    return 1e-11 * (1 + np.diff(g.row_ptr))
+
+
+def _tol_mixed(g, ref):
+    return 2e-4 * (1 + np.diff(g.row_ptr)) * np.maximum(1.0, np.abs(ref))
+
+
+def _rhs_gpu(sysk, theta):
+    th = _dev(theta)
+    out = torch.empty_like(th)
+    sysk.rhs(th, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def sbm_small():
+    return G.workload_sbm_small(n=12000, n_comm=12, min_size=128, seed=3)
+
+
+@pytest.fixture(scope="module")
+def sbm_mid():
+    return G.workload_sbm_small()            # N = 65536, 64 communities, p_in 0.95, p_out 0.001
+
+
+@pytest.fixture(scope="module")
+def sbm_large():
+    return G.workload_sbm_large()            # N = 2^20, 1024 communities
+
+
+# ----------------------------------------------------------------------------- right-hand side
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_complete_graph(prec):
+    w = G.workload_complete(512)
+    g = w.graph
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K, precision=prec) as k:
+        st = k.stats()
+        assert st["dense_blocks"] == 1 and st["missing_entries"] == 0 and st["sparse_entries"] == 0
+        f = _rhs_gpu(k, w.theta0)
+    tol = _tol_fp64(g) if prec == 0 else _tol_mixed(g, ref)
+    assert np.all(np.abs(f - ref) <= tol), np.abs(f - ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("tau", [0.0, 0.5, 1.0])
+def test_rhs_sbm_small_all_tau(sbm_small, prec, tau):
+    w = sbm_small
+    g = w.graph
+    th = w.theta0 + 40.0 * G.uniform(9, 3, g.n, -1, 1)       # unwrapped phases up to ~50 rad
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, th, w.K)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec, tau=tau) as k:
+        f = _rhs_gpu(k, th)
+    tol = _tol_fp64(g) if prec == 0 else _tol_mixed(g, ref)
+    assert np.all(np.abs(f - ref) <= tol), np.abs(f - ref).max()
+
+
+def test_rhs_degree_scaling(sbm_small):
+    w = sbm_small
+    g = w.graph
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, scaling=1)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, scaling=1) as k:
+        f = _rhs_gpu(k, w.theta0)
+    assert np.all(np.abs(f - ref) <= _tol_fp64(g))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_full_size_65536_sampled_rows(sbm_mid, prec):
+    w = sbm_mid
+    g = w.graph
+    rows = np.unique(G.permutation(5, g.n)[:3000].astype(np.int64))
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, rows=rows)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec) as k:
+        f = _rhs_gpu(k, w.theta0)[rows]
+    deg = np.diff(g.row_ptr)[rows]
+    tol = 1e-11 * (1 + deg) if prec == 0 else 2e-4 * (1 + deg) * np.maximum(1, np.abs(ref))
+    assert np.all(np.abs(f - ref) <= tol), np.abs(f - ref).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_full_size_2p20_sampled_rows_and_invariant(sbm_large, prec):
+    w = sbm_large
+    g = w.graph
+    rows = np.unique(G.permutation(6, g.n)[:600].astype(np.int64))
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, rows=rows)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec) as k:
+        f_all = _rhs_gpu(k, w.theta0)
+    f = f_all[rows]
+    deg = np.diff(g.row_ptr)[rows]
+    tol = 1e-11 * (1 + deg) if prec == 0 else 2e-4 * (1 + deg) * np.maximum(1, np.abs(ref))
+    assert np.all(np.abs(f - ref) <= tol), np.abs(f - ref).max()
+    # symmetric A, uniform scaling: the coupling terms sum to zero at any size (Sec. 3)
+    coupling_sum = np.sum(f_all - w.omega) / (w.K / g.n)
+    assert abs(coupling_sum) < (1e-6 if prec == 0 else 5.0), coupling_sum
+
+
+def test_rhs_window_cap_exceeded_and_ragged():
+    """A community larger than the staged window (global-gather path), tiny and empty communities,
+    an isolated node, self-loops (dropped) and ragged row lengths."""
+    sizes = [5000, 3, 1, 777, 250]
+    g = G.sbm(21, sizes, [0.9, 1.0, 0.5, 0.7, 0.2], 0.01)
+    lab = g.label.copy()
+    n_comm = 6                                  # community 5 is empty
+    A_rp, A_col = g.row_ptr.copy(), g.col.copy()
+    # add self-loops to a few rows
+    rows = [0, 17, 4000]
+    rp, cols = [0], []
+    for u in range(g.n):
+        c = list(A_col[A_rp[u]:A_rp[u + 1]])
+        if u in rows:
+            c = sorted(c + [u])
+        cols += c
+        rp.append(len(cols))
+    rp, cols = np.array(rp, np.int64), np.array(cols, np.int32)
+    omega, theta = G.normal(2, 0, g.n), G.uniform(2, 1, g.n, 0, 6.3)
+    ref = oracle.rhs_csr(rp, cols, omega, theta, 2.5)
+    with kura.Kuramoto(rp, cols, lab, n_comm, omega, 2.5) as k:
+        st = k.stats()
+        assert st["self_loops"] == 3
+        f = _rhs_gpu(k, theta)
+    deg = np.diff(rp)
+    assert np.all(np.abs(f - ref) <= 1e-11 * (1 + deg)), np.abs(f - ref).max()
+
+
+def test_single_node_and_edgeless_graph():
+    with kura.Kuramoto(np.array([0, 0]), np.zeros(0, np.int32), np.zeros(1, np.int32), 1, np.array([0.7]), 3.0) as k:
+        assert np.array_equal(_rhs_gpu(k, np.array([1.0])), [0.7])
+    n = 100
+    with kura.Kuramoto(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(n, np.int32), 1,
+                       np.arange(n, dtype=float), 1.0) as k:
+        assert np.array_equal(_rhs_gpu(k, np.ones(n)), np.arange(n, dtype=float))
+
+
+def test_host_pointers_match_device(sbm_small):
+    w = sbm_small
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        f_dev = _rhs_gpu(k, w.theta0)
+        f_host = np.empty(g.n)
+        k.rhs(np.ascontiguousarray(w.theta0), f_host)
+        assert np.array_equal(f_dev, f_host)
+        th_h = w.theta0.copy()
+        k.rk4_steps(th_h, w.h, 3)
+        th_d = _dev(w.theta0)
+        k.rk4_steps(th_d, w.h, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(th_h, th_d.cpu().numpy())
+
+
+def test_bitwise_deterministic(sbm_mid):
+    w = sbm_mid
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=1) as k:
+        a = _dev(w.theta0)
+        b = _dev(w.theta0)
+        k.rk4_steps(a, w.h, 5)
+        k.rk4_steps(b, w.h, 5)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+# ----------------------------------------------------------------------------- trajectories
+def test_rk4_trajectory_complete_512_full_horizon():
+    w = G.workload_complete(512)
+    g = w.graph
+    ref = oracle.rk4_complete(w.omega, w.K, w.theta0, w.h, w.n_steps)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K) as k:
+        th = _dev(w.theta0)
+        k.rk4_steps(th, w.h, w.n_steps)
+        k.sync()
+        err = np.abs(th.cpu().numpy() - ref).max()
+    assert err <= 1e-8, err
+
+
+def test_rk4_trajectory_sbm_and_conservation(sbm_small):
+    w = sbm_small
+    g = w.graph
+    steps = 40
+    ref = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        th = _dev(w.theta0)
+        k.rk4_steps(th, w.h, 17)          # two calls: chunked graphs of different lengths
+        k.rk4_steps(th, w.h, steps - 17)
+        k.sync()
+        got = th.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8
+    assert abs(oracle.mean_deviation(got, w.theta0, w.omega, steps * w.h)) < 1e-12   # eq:KuramotoGraphConservation
+
+
+def test_rk4_mixed_trajectory_error_vs_fp64(sbm_small):
+    w = sbm_small
+    g = w.graph
+    steps = 40
+    ref = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=1) as k:
+        th = _dev(w.theta0)
+        k.rk4_steps(th, w.h, steps)
+        k.sync()
+        err = np.abs(th.cpu().numpy() - ref).max()
+    assert err < 1e-5, err
+
+
+def test_rk4_synchronised_state_stays_synchronised():
+    g = G.sbm(8, [300, 500, 200], 0.8, 0.02)
+    omega = np.full(g.n, 0.37)
+    th0 = np.full(g.n, 2.0)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, omega, 3.0) as k:
+        th = _dev(th0)
+        k.rk4_steps(th, 0.01, 50)
+        k.sync()
+    np.testing.assert_allclose(th.cpu().numpy(), 2.0 + 0.37 * 0.5, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- order parameters, baseline
+def test_order_params(sbm_small):
+    w = sbm_small
+    g = w.graph
+    r_o, psi_o, rc_o, pc_o = oracle.order_params(w.theta0, g.label, g.n_comm)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        r, psi, rc, pc = k.order_params(_dev(w.theta0), per_community=True)
+    assert abs(r - r_o) < 1e-12 and abs(psi - psi_o) < 1e-10
+    np.testing.assert_allclose(rc, rc_o, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(pc, pc_o, atol=1e-9, rtol=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_direct_baseline(sbm_small, prec):
+    w = sbm_small
+    g = w.graph
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        th = _dev(w.theta0)
+        out = torch.empty_like(th)
+        k.direct_rhs(th, out, prec)
+        torch.cuda.synchronize()
+        f = out.cpu().numpy()
+        tol = _tol_fp64(g) if prec == 0 else _tol_mixed(g, ref)
+        assert np.all(np.abs(f - ref) <= tol)
+        if prec == 0:
+            steps = 10
+            ref_t = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps)
+            k.direct_rk4_steps(th, w.h, steps, 0)
+            torch.cuda.synchronize()
+            assert np.abs(th.cpu().numpy() - ref_t).max() <= 1e-8
+
+
+def test_set_param_and_timing(sbm_small):
+    w = sbm_small
+    g = w.graph
+    om2 = G.normal(77, 0, g.n)
+    ref = oracle.rhs_csr(g.row_ptr, g.col, om2, w.theta0, 1.25)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        k.set_param(omega=om2, K=1.25)
+        assert np.all(np.abs(_rhs_gpu(k, w.theta0) - ref) <= _tol_fp64(g))
+        k.set_timing(True)
+        th = _dev(w.theta0)
+        k.rk4_steps(th, w.h, 3)
+        t = k.kernel_times()
+        assert t.size == 12 and np.all(t > 0)
+
+
+def test_nonfinite_state_is_reported(sbm_small):
+    w = sbm_small
+    g = w.graph
+    th0 = w.theta0.copy()
+    th0[5] = np.nan
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:
+        th = _dev(th0)
+        k.rk4_steps(th, w.h, 1)
+        with pytest.raises(kura.KuraError) as e:
+            k.sync()
+        assert e.value.status == kura.KURA_ENUMERIC
+        k.sync()      # latched condition was cleared
