@@ -1,0 +1,352 @@
+"""Benchmark: RK4 oscillator-steps/s of the localised-order-parameter block path.
+
+Default workload: the 2^20-node SBM (1024 communities, Dirichlet sizes in
+[256, 4096], p_in ~ U[0.5, 0.99], p_out = 1e-4, omega ~ Cauchy(0, 0.5)
+clipped at +-10, K = 3, h = 0.01), mixed precision (FP32 sin/cos and
+per-edge corrections, exact fixed-point block sums, FP64 epilogue and state).
+One "step" is one classical RK4 step over the whole graph (4 right-hand-side
+evaluations).  Inputs are resident in HBM; the 1.85 GB correction stream of
+every stage is larger than the 126 MiB L2, so no L2 flush is needed.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the reference implementation of the method for this build) on the host
+cores on a bounded sample of the same workload.
+
+Multi-GPU: a single graph does not shard on this path (no exchange step is
+cheaper than the stage itself), so N > 1 runs N independent replicas
+("weak" scaling); value = total oscillator-steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RK4 oscillator-steps/s (N*steps/s) vs GPU direct sum at stated FP64/FP32 error"
+UNIT = "oscillator-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name: str):
+    from paper_2102_07167_gb300 import gen as G
+    if name == "sbm-2p20":
+        return G.workload_sbm_large()
+    if name == "sbm-2p18":     # same recipe at a quarter of the nodes and communities (profiling size)
+        return G.workload_sbm_large(n=1 << 18, n_comm=256)
+    if name == "sbm-65536":
+        return G.workload_sbm_small()
+    if name == "complete-512":
+        return G.workload_complete(512)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _workload_desc(w, st):
+    g = w.graph
+    return {"workload": f"{w.name}: SBM N={g.n}, {g.n_comm} communities" if g.n_comm > 1 else
+            f"{w.name}: complete graph N={g.n}",
+            "n": g.n, "edges": g.nnz, "communities": g.n_comm, "K": w.K, "h": w.h,
+            "dense_blocks": st["dense_blocks"], "missing_entries": st["missing_entries"],
+            "sparse_entries": st["sparse_entries"],
+            "l2": "inputs larger than L2 (correction stream %.2f GB per stage vs 126 MiB L2)" %
+                  (st["stream_bytes"] / 1e9)}
+
+
+def cpu_baseline_oracle(w, seconds: float = 12.0):
+    """The FP64 oracle as it stands (CSR definition, one sine per edge, one core) on a bounded sample of
+    rows of the same graph; 4 right-hand-side evaluations per RK4 step."""
+    import oracle
+    from paper_2102_07167_gb300 import gen as G
+    g = w.graph
+    order = G.permutation(123, g.n).astype(np.int64)
+    done, t0, pos, batch = 0, time.perf_counter(), 0, 2048
+    while time.perf_counter() - t0 < seconds and pos < g.n:
+        rows = order[pos:pos + batch]
+        oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, rows=rows)
+        pos += rows.size
+        done += rows.size
+    el = time.perf_counter() - t0
+    rows_per_s = done / el
+    return {"value": rows_per_s / 4.0, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle right-hand side (CSR definition) on {done} random rows of the "
+                      f"{g.n}-node graph in {el:.1f} s; RK4 step = 4 evaluations, extrapolated to N rows"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = _workload(args.workload)
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline_oracle(w, seconds=0.5)
+    for _ in range(args.steps):
+        per_step.append(cpu_baseline_oracle(w, seconds=max(1.0, 60.0 / max(args.steps, 1))))
+    vals = [p["value"] for p in per_step]
+    v = float(np.mean(vals))
+    ms = w.graph.n / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.graph.n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": per_step[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2102_07167_gb300 import kura
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    prec = kura.PREC_MIXED if args.precision == "mixed" else kura.PREC_FP64
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = _workload(args.workload)
+    g = w.graph
+    n = g.n
+    k = kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec)
+    st = k.stats()
+    theta = torch.tensor(w.theta0, device=dev)
+
+    # ---- warm-up, then the timed region: K RK4 steps through one library call
+    k.set_timing(True)
+    k.rk4_steps(theta, w.h, max(args.warmup, 3))
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record()
+        k.rk4_steps(theta, w.h, args.steps)
+        ev1.record()
+        barrier()
+    el_ms = ev0.elapsed_time(ev1)
+    launch_ms = k.kernel_times()
+    if dist is not None:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    ms_step = el_ms / args.steps
+    value = world * n * args.steps / (el_ms / 1e3)
+    gpu_launches = 8 * args.steps + 2
+
+    # ---- roofline of the dominant kernel (row kernel): algorithmic bytes / mean launch time
+    peak, peak_kind = _peaks()
+    alg_bytes = st["stream_bytes"] + st["node_bytes_row"]
+    row_ms = float(np.mean(launch_ms)) if launch_ms.size else None
+    achieved = alg_bytes / (row_ms * 1e-3) / 1e9 if row_ms else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "row_kernel_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            from paper_2102_07167_gb300 import _build
+            rec = json.load(open(tpath))
+            if rec.get("source_hash") == _build.kernel_source_hash() and rec.get("workload") == w.name \
+                    and rec.get("precision") == args.precision:
+                traffic = rec.get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "kernel": "k_row_stage",
+                "algorithmic_bytes_per_launch": alg_bytes, "row_kernel_ms": row_ms,
+                "launches_timed": int(launch_ms.size)}
+
+    # ---- e2e: the public call with pinned HOST phases, copies inside every step
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        host[:] = w.theta0
+        k.rk4_steps(host, w.h, 1)
+        ke = max(5, min(args.steps, 50))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            k.rk4_steps(host, w.h, 1)
+        el = time.perf_counter() - t0
+        e2e = {"value": n * ke / el, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+               "steps": ke, "note": "kura_rk4_steps(host pointer, n_steps=1) per step: H2D, permute, 1 RK4 "
+                                    "step, un-permute, D2H, synchronise"}
+
+    extra = {}
+    if not args.quick and rank == 0:
+        # mixed vs FP64 path error on one right-hand side (both through the library)
+        th0 = torch.tensor(w.theta0, device=dev)
+        f_a = torch.empty_like(th0)
+        k.rhs(th0, f_a)
+        other = kura.PREC_FP64 if prec == kura.PREC_MIXED else kura.PREC_MIXED
+        k.close()
+        k = None
+        k2 = kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=other)
+        f_b = torch.empty_like(th0)
+        k2.rhs(th0, f_b)
+        deg = torch.tensor(np.diff(g.row_ptr), device=dev, dtype=torch.float64)
+        err = (f_a - f_b).abs()
+        extra["rhs_error_vs_other_precision"] = {
+            "max_abs": float(err.max()), "max_scaled": float((err / (1 + deg)).max()),
+            "note": "|f_mixed - f_fp64|, and divided by (1 + deg_i); both through the library"}
+        # the other precision's throughput
+        th = th0.clone()
+        k2.rk4_steps(th, w.h, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(10, args.steps // 4)
+        e0.record()
+        k2.rk4_steps(th, w.h, ks)
+        e1.record()
+        torch.cuda.synchronize()
+        mso = e0.elapsed_time(e1) / ks
+        extra["fp64_mode" if other == kura.PREC_FP64 else "mixed_mode"] = {
+            "value": n / mso * 1e3, "ms_per_step": mso, "steps": ks}
+        # GPU direct-summation baselines (one sine per edge)
+        direct = {}
+        for dp, name in ((kura.PREC_MIXED, "fp32"), (kura.PREC_FP64, "fp64")):
+            th = th0.clone()
+            k2.direct_rk4_steps(th, w.h, 1, dp)
+            torch.cuda.synchronize()
+            nd = 2 if dp == kura.PREC_FP64 else 5
+            e0.record()
+            k2.direct_rk4_steps(th, w.h, nd, dp)
+            e1.record()
+            torch.cuda.synchronize()
+            msd = e0.elapsed_time(e1) / nd
+            direct[name] = {"value": n / msd * 1e3, "ms_per_step": msd, "steps": nd}
+        direct["speedup_vs_fp64_direct"] = value / world / direct["fp64"]["value"]
+        direct["speedup_vs_fp32_direct"] = value / world / direct["fp32"]["value"]
+        extra["direct_baseline"] = direct
+        k2.close()
+    if k is not None:
+        k.close()
+
+    cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds) if (rank == 0 and world == 1 and not args.quick) \
+        else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == kura.PREC_MIXED else "f64", "data": "synthetic",
+                "config": dict(_workload_desc(w, st), precision=args.precision,
+                               parallelism="replicas" if world > 1 else "single-gpu"),
+                "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clk.summary()}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sbm-2p20", choices=["sbm-2p20", "sbm-2p18", "sbm-65536", "complete-512"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--quick", action="store_true", help="skip the extra comparisons and the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

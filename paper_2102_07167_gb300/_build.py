@@ -58,3 +58,13 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     run([nvcc, ARCH, "-shared", "-o", tmp, cu_obj, cpp_obj, "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
+
+
+def kernel_source_hash() -> str:
+    """Hash of the CUDA kernel sources: profile records made from other sources are stale."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kura_kernels.cuh", "kura_capi.cu"):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]

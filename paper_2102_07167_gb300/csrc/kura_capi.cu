@@ -83,7 +83,7 @@ struct kura_ctx {
     Plan plan;                          // host plan (streams released after upload)
     int64_t miss_total = 0, pres_total = 0, nnz = 0;
     // device buffers
-    DevMem perm, node_comm, miss_off, pres_off, miss_cnt, pres_cnt, miss, pres, tiles, dptr, dcol, comm_off;
+    DevMem perm, node_comm, gstream, groups, tiles, dptr, dcol, comm_off;
     DevMem omega, rscale, table, bsum, bsum_out, tot, T, counter, err_flags;
     DevMem y, Y, krk, fbuf, user, red, order_out;
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
@@ -156,12 +156,8 @@ DevGraph dev_graph(kura_ctx* h)
     g.scale = h->K / double(h->n);
     g.rscale = h->opts.scaling == KURA_SCALING_DEGREE ? h->rscale.as<double>() : nullptr;
     g.node_comm = h->node_comm.as<int32_t>();
-    g.miss_off = h->miss_off.as<int64_t>();
-    g.pres_off = h->pres_off.as<int64_t>();
-    g.miss_cnt = h->miss_cnt.as<int32_t>();
-    g.pres_cnt = h->pres_cnt.as<int32_t>();
-    g.miss = h->miss.as<int32_t>();
-    g.pres = h->pres.as<int32_t>();
+    g.gstream = h->gstream.as<int32_t>();
+    g.groups = h->groups.as<Group>();
     g.tiles = h->tiles.as<Tile>();
     g.dptr = h->dptr.as<int64_t>();
     g.dcol = h->dcol.as<int32_t>();
@@ -259,19 +255,16 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     h->pres_total = p.pres_total;
     h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2));
     const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
-    h->row_smem = size_t(std::max(p.max_wlen, 2)) * esize;
+    const int slot = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
+    h->row_smem = size_t(ROW_SLOTS) * size_t(slot) * 4 + size_t(std::max(p.max_wlen, 2)) * esize;
     KCHECK(h, (h->opts.precision == KURA_PREC_MIXED ? set_row_attrs<MODE_MIXED>(h->row_smem)
                                                     : set_row_attrs<MODE_FP64>(h->row_smem)),
            "setting the row kernel's shared-memory size");
 
     KCHECK(h, upload(h->perm, p.perm, s), "upload perm");
     KCHECK(h, upload(h->node_comm, p.node_comm, s), "upload node_comm");
-    KCHECK(h, upload(h->miss_off, p.miss_off, s), "upload miss_off");
-    KCHECK(h, upload(h->pres_off, p.pres_off, s), "upload pres_off");
-    KCHECK(h, upload(h->miss_cnt, p.miss_cnt, s), "upload miss_cnt");
-    KCHECK(h, upload(h->pres_cnt, p.pres_cnt, s), "upload pres_cnt");
-    KCHECK(h, upload(h->miss, p.miss, s), "upload missing-entry stream");
-    KCHECK(h, upload(h->pres, p.pres, s), "upload sparse-entry stream");
+    KCHECK(h, upload(h->gstream, p.gstream, s), "upload the correction stream");
+    KCHECK(h, upload(h->groups, p.groups, s), "upload row groups");
     KCHECK(h, upload(h->tiles, p.tiles, s), "upload tiles");
     KCHECK(h, upload(h->dptr, p.dptr, s), "upload dptr");
     KCHECK(h, upload(h->dcol, p.dcol, s), "upload dcol");
@@ -304,9 +297,8 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     for (DevMem* d : {&h->y, &h->Y, &h->krk, &h->fbuf, &h->user}) KCHECK(h, d->alloc(8 * n), "alloc state");
     KCHECK(h, h->order_out.alloc(8 * (2 + 2 * nc)), "alloc order_out");
     KCHECK(h, cudaStreamSynchronize(s), "upload");
-    // the per-row streams now live on the device
-    std::vector<int32_t>().swap(p.miss);
-    std::vector<int32_t>().swap(p.pres);
+    // the correction stream now lives on the device
+    std::vector<int32_t>().swap(p.gstream);
     h->graphs.clear();
     h->last_graph = nullptr;
     return KURA_OK;
@@ -400,6 +392,7 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
     PlanInput in;
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.tile_max_rows = TILE_MAX_ROWS;
+    in.slot_ints = slot_ints_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     Plan plan;
     std::string err;
     int rc = build_plan(in, plan, err);
@@ -457,8 +450,8 @@ kura_status kura_get_stats(kura_t h, kura_block_stats* s)
     s->tiles = h->n_tiles;
     s->max_window = h->max_wlen;
     const int64_t esize = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
-    // algorithmic bytes: 4 B per stored index + 24 B of row metadata per row
-    s->stream_bytes = 4 * (h->miss_total + h->pres_total) + 24 * h->n;
+    // algorithmic bytes: 4 B per stored index + a 16 B header per row
+    s->stream_bytes = 4 * (h->miss_total + h->pres_total) + 16 * h->n;
     // row kernel per node: omega, y, krk (read+write), Y (write) or y (write), own entry
     s->node_bytes_row = (8 + 8 + 16 + 8 + esize) * h->n;
     // trig kernel per node: theta read, table write, community id
@@ -478,6 +471,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
         in.n_comm = h->n_comm; in.tau = tau;
         in.tile_max_rows = TILE_MAX_ROWS;
+        in.slot_ints = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
         Plan plan;
         std::string err;
         int rc = build_plan(in, plan, err);
@@ -800,7 +794,7 @@ kura_status kura_plan_stats(kura_plan_t pl, kura_block_stats* s)
     s->max_row_entries = p.max_row_entries;
     s->tiles = int64_t(p.tiles.size());
     s->max_window = p.max_wlen;
-    s->stream_bytes = 4 * (p.miss_total + p.pres_total) + 24 * p.n;
+    s->stream_bytes = 4 * (p.miss_total + p.pres_total) + 16 * p.n;
     s->node_bytes_row = (8 + 8 + 16 + 8 + 16) * p.n;
     s->node_bytes_trig = (8 + 16 + 4) * p.n;
     s->direct_edges = p.nnz_in - p.self_loops;
@@ -821,10 +815,12 @@ kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t
     if (!pl || !n_missing || !n_present) return KURA_EINVAL;
     const Plan& p = pl->p;
     if (row < 0 || row >= p.n) return KURA_EINVAL;
-    *n_missing = p.miss_cnt[size_t(row)];
-    *n_present = p.pres_cnt[size_t(row)];
-    for (int64_t k = 0; k < *n_missing && k < cap && missing; k++) missing[k] = p.miss[size_t(p.miss_off[size_t(row)] + k)];
-    for (int64_t k = 0; k < *n_present && k < cap && present; k++) present[k] = p.pres[size_t(p.pres_off[size_t(row)] + k)];
+    const Group& G = p.groups[size_t(p.row_group[size_t(row)])];
+    const int32_t* hdr = p.gstream.data() + G.off + 4 * (row - G.r0);
+    *n_missing = hdr[1];
+    *n_present = hdr[3];
+    for (int64_t k = 0; k < *n_missing && k < cap && missing; k++) missing[k] = p.gstream[size_t(G.off + hdr[0] + k)];
+    for (int64_t k = 0; k < *n_present && k < cap && present; k++) present[k] = p.gstream[size_t(G.off + hdr[2] + k)];
     return KURA_OK;
 }
 

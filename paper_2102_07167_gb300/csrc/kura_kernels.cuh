@@ -16,10 +16,13 @@
 
 namespace kura {
 
-constexpr int ROW_THREADS = 512;
-constexpr int ROW_WARPS = ROW_THREADS / 32;
-constexpr int TILE_MAX_ROWS = 1024;     // stash capacity of the row kernel (matches the planner)
+constexpr int ROW_CONSUMERS = 16;                       // consumer warps of the row kernel
+constexpr int ROW_THREADS = (ROW_CONSUMERS + 1) * 32;   // + one producer warp
+constexpr int ROW_SLOTS = 4;                            // shared-memory ring of row-group slots
+constexpr int TILE_MAX_ROWS = 512;      // stash capacity of the row kernel (the planner's tile bound)
 constexpr int TRIG_THREADS = 256;
+// slot capacity (int32 units) per precision mode: keeps two CTAs resident per SM
+__host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 4096; }
 
 enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
 enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4 };
@@ -44,12 +47,8 @@ struct DevGraph {
     double scale;                           // K / N (uniform scaling)
     const double* rscale;                   // per permuted row K / calM_m (degree scaling) or null
     const int32_t* node_comm;               // [n]
-    const int64_t* miss_off;                // [n+1]
-    const int64_t* pres_off;                // [n+1]
-    const int32_t* miss_cnt;                // [n]
-    const int32_t* pres_cnt;                // [n]
-    const int32_t* miss;                    // missing entries of dense blocks (permuted columns)
-    const int32_t* pres;                    // present entries of sparse blocks
+    const int32_t* gstream;                 // packed row groups (see Group in plan.hpp)
+    const Group* groups;
     const Tile* tiles;
     const int64_t* dptr;                    // [n_comm+1]
     const int32_t* dcol;
@@ -88,6 +87,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
 {
@@ -246,9 +249,10 @@ struct Acc2 {
     typename EntryT<MODE>::A s, c;
 };
 
-// Sums the entries of one stream segment into (as, ac) with sign SIGN.
+// Sums the entries of one row segment (16-byte aligned, in shared memory or,
+// for an oversized group, in global memory) into (as, ac) with sign SIGN.
 template <int MODE, int SIGN>
-__device__ __forceinline__ void sum_segment(const int32_t* __restrict__ seg, int cnt, int lane,
+__device__ __forceinline__ void sum_segment(const int32_t* seg, int cnt, int lane,
                                             const typename EntryT<MODE>::T* win, int wbeg, int wlen,
                                             const typename EntryT<MODE>::T* table,
                                             typename EntryT<MODE>::A& as, typename EntryT<MODE>::A& ac)
@@ -256,7 +260,7 @@ __device__ __forceinline__ void sum_segment(const int32_t* __restrict__ seg, int
     const int4* v4 = reinterpret_cast<const int4*>(seg);
 #pragma unroll 2
     for (int q = lane; q * 4 < cnt; q += 32) {
-        const int4 v = __ldcs(v4 + q);
+        const int4 v = v4[q];
         const int b = q * 4;
         const int idx[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -270,63 +274,119 @@ __device__ __forceinline__ void sum_segment(const int32_t* __restrict__ seg, int
     }
 }
 
+// One CTA per tile (rows of one community).  Warp ROW_CONSUMERS is the
+// producer: one elected lane streams the community's (sin, cos) window and
+// then the tile's row groups into a ring of shared-memory slots with TMA bulk
+// copies (full/empty mbarriers, every wait bounded in time).  The consumer
+// warps take the rows round-robin (row k -> warp k mod ROW_CONSUMERS), sum the
+// row's missing entries (subtracted) and present entries (added), gathering
+// (sin, cos) from the staged window or, off the window, from the L2-resident
+// table, and leave the row's sums in a stash.  Finally every thread takes rows
+// for the FP64 epilogue: f = omega + scale (cos th acc_s - sin th acc_c), and
+// the RK4 stage update.
 template <int MODE, int STAGE>
 __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk)
 {
     using E = typename EntryT<MODE>::T;
     using A = typename EntryT<MODE>::A;
+    constexpr int SLOT = slot_ints_for(MODE);
+    constexpr uint64_t LIMIT_NS = 1000000000ull;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t full_bar[ROW_SLOTS], empty_bar[ROW_SLOTS], win_bar;
     __shared__ Acc2<MODE> stash[TILE_MAX_ROWS];
     __shared__ int abort_flag;
+    __shared__ int issued[ROW_SLOTS];
 
+    int32_t* ring = reinterpret_cast<int32_t*>(smem_raw);
+    E* win = reinterpret_cast<E*>(smem_raw + size_t(ROW_SLOTS) * SLOT * sizeof(int32_t));
     const Tile t = g.tiles[blockIdx.x];
     const E* table = reinterpret_cast<const E*>(g.table);
-    E* win = reinterpret_cast<E*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ngroups = t.g1 - t.g0;
 
-    // ---- stage the community's (sin, cos) window with one TMA bulk copy
-    if (tid == 0) abort_flag = 0;
-    if (t.wlen > 0) {
-        if (tid == 0) {
-            mbar_init(&bar, 1);
-            const uint32_t bytes = static_cast<uint32_t>(t.wlen) * static_cast<uint32_t>(sizeof(E));
-            mbar_arrive_expect_tx(&bar, bytes);
-            bulk_g2s(win, table + t.wbeg, bytes, &bar);
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int sl = 0; sl < ROW_SLOTS; sl++) {
+            mbar_init(&full_bar[sl], 1);
+            mbar_init(&empty_bar[sl], ROW_CONSUMERS);
+            issued[sl] = 0;
         }
-        __syncthreads();
-        if (!mbar_wait_bounded(&bar, 0, 1000000000ull)) {
-            atomicOr(g.err, ERR_TIMEOUT);
-            abort_flag = 1;
-        }
-        __syncthreads();
-        if (abort_flag) {
-            // give the copy in flight one more bounded chance to land before leaving
-            if (tid == 0) mbar_wait_bounded(&bar, 0, 1000000000ull);
-            __syncthreads();
-            return;
-        }
-    } else {
-        __syncthreads();
-    }
-
-    // ---- one warp per row: gathers of the correction streams
-    const int nrows = t.r1 - t.r0;
-    for (int k = warp; k < nrows; k += ROW_WARPS) {
-        const int64_t row = int64_t(t.r0) + k;
-        A as = 0, ac = 0;
-        sum_segment<MODE, -1>(g.miss + g.miss_off[row], g.miss_cnt[row], lane, win, t.wbeg, t.wlen, table, as, ac);
-        sum_segment<MODE, +1>(g.pres + g.pres_off[row], g.pres_cnt[row], lane, win, t.wbeg, t.wlen, table, as, ac);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            as += __shfl_xor_sync(0xffffffffu, as, o);
-            ac += __shfl_xor_sync(0xffffffffu, ac, o);
-        }
-        if (lane == 0) stash[k] = Acc2<MODE>{as, ac};
+        mbar_init(&win_bar, 1);
     }
     __syncthreads();
 
-    // ---- one thread per row: the right-hand side and the RK4 stage, FP64
+    if (warp == ROW_CONSUMERS) {
+        // ---------------- producer
+        if (lane == 0) {
+            if (t.wlen > 0) {
+                const uint32_t bytes = uint32_t(t.wlen) * uint32_t(sizeof(E));
+                mbar_arrive_expect_tx(&win_bar, bytes);
+                bulk_g2s(win, table + t.wbeg, bytes, &win_bar);
+            }
+            for (int gi = 0; gi < ngroups; gi++) {
+                const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
+                if (fill > 0 && !mbar_wait_bounded(&empty_bar[sl], uint32_t(fill - 1) & 1u, LIMIT_NS)) {
+                    atomicOr(g.err, ERR_TIMEOUT);
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                const Group G = g.groups[t.g0 + gi];
+                if ((G.flags & GROUP_OVERSIZED) || G.len == 0) {
+                    mbar_arrive(&full_bar[sl]);
+                } else {
+                    const uint32_t bytes = uint32_t(G.len) * 4u;
+                    mbar_arrive_expect_tx(&full_bar[sl], bytes);
+                    bulk_g2s(ring + size_t(sl) * SLOT, g.gstream + G.off, bytes, &full_bar[sl]);
+                }
+                issued[sl] = fill + 1;
+            }
+        }
+    } else {
+        // ---------------- consumers
+        bool ok = (t.wlen == 0) || mbar_wait_bounded(&win_bar, 0u, LIMIT_NS);
+        if (!ok) { atomicOr(g.err, ERR_TIMEOUT); atomicExch(&abort_flag, 1); }
+        for (int gi = 0; gi < ngroups && ok; gi++) {
+            const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
+            if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
+                atomicOr(g.err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            const Group G = g.groups[t.g0 + gi];
+            const int32_t* base = (G.flags & GROUP_OVERSIZED) ? g.gstream + G.off : ring + size_t(sl) * SLOT;
+            const int kb = G.r0 - t.r0, ke = G.r1 - t.r0;
+            int k = kb + ((warp - kb) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
+            for (; k < ke; k += ROW_CONSUMERS) {
+                const int4 hdr = reinterpret_cast<const int4*>(base)[k - kb];
+                A as = 0, ac = 0;
+                sum_segment<MODE, -1>(base + hdr.x, hdr.y, lane, win, t.wbeg, t.wlen, table, as, ac);
+                sum_segment<MODE, +1>(base + hdr.z, hdr.w, lane, win, t.wbeg, t.wlen, table, as, ac);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    as += __shfl_xor_sync(0xffffffffu, as, o);
+                    ac += __shfl_xor_sync(0xffffffffu, ac, o);
+                }
+                if (lane == 0) stash[k] = Acc2<MODE>{as, ac};
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[sl]);
+            if (*(volatile int*)&abort_flag) break;
+        }
+    }
+    __syncthreads();
+    if (abort_flag) {
+        // let the copies in flight land (bounded) before the CTA leaves
+        if (tid == 0) {
+            for (int sl = 0; sl < ROW_SLOTS; sl++)
+                if (issued[sl] > 0) mbar_wait_bounded(&full_bar[sl], uint32_t(issued[sl] - 1) & 1u, LIMIT_NS);
+            if (t.wlen > 0) mbar_wait_bounded(&win_bar, 0u, LIMIT_NS);
+        }
+        __syncthreads();
+        return;
+    }
+
+    // ---------------- epilogue: one thread per row, FP64
+    const int nrows = t.r1 - t.r0;
     for (int k = tid; k < nrows; k += ROW_THREADS) {
         const int64_t row = int64_t(t.r0) + k;
         const Acc2<MODE> a = stash[k];

@@ -168,20 +168,97 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             p.miss_cnt[size_t(v)] = int32_t(dense_span[size_t(I)] - self_dense[size_t(I)] - in_dense);
             p.pres_cnt[size_t(v)] = int32_t(np_);
         }
-        p.miss_off.resize(size_t(n) + 1);
-        p.pres_off.resize(size_t(n) + 1);
-        p.miss_off[0] = p.pres_off[0] = 0;
         int64_t mx = 0;
         for (int64_t v = 0; v < n; v++) {
-            p.miss_off[size_t(v) + 1] = p.miss_off[size_t(v)] + round_up4(p.miss_cnt[size_t(v)]);
-            p.pres_off[size_t(v) + 1] = p.pres_off[size_t(v)] + round_up4(p.pres_cnt[size_t(v)]);
             p.miss_total += p.miss_cnt[size_t(v)];
             p.pres_total += p.pres_cnt[size_t(v)];
             mx = std::max<int64_t>(mx, int64_t(p.miss_cnt[size_t(v)]) + p.pres_cnt[size_t(v)]);
         }
         p.max_row_entries = mx;
-        p.miss.assign(size_t(std::max<int64_t>(p.miss_off[size_t(n)], 4)), 0);
-        p.pres.assign(size_t(std::max<int64_t>(p.pres_off[size_t(n)], 4)), 0);
+
+        // ---- tiles (rows of one community, bounded work and rows; staged
+        // window = the community's own columns joined with its dense column
+        // blocks when that span fits the cap, else the community's columns)
+        // and row groups (consecutive rows of a tile whose packed stream fits
+        // one slot of the row kernel; a row alone larger than a slot is an
+        // oversized group read in place).
+        auto row_ints = [&](int64_t v) {
+            return 4 + round_up4(p.miss_cnt[size_t(v)]) + round_up4(p.pres_cnt[size_t(v)]);
+        };
+        int64_t total_work = 0;
+        for (int64_t v = 0; v < n; v++) total_work += p.miss_cnt[size_t(v)] + p.pres_cnt[size_t(v)] + 8;
+        const int64_t target = in.tile_work > 0 ? in.tile_work : std::max<int64_t>(2048, total_work / (152 * 12));
+        std::vector<int64_t> row_pos(static_cast<size_t>(n));       // start of each row's missing segment in gstream
+        p.row_group.resize(size_t(n));
+        int64_t goff = 0;
+        for (int32_t I = 0; I < nc; I++) {
+            int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
+            if (rb == re) continue;
+            int64_t lo = rb, hi = re;
+            for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
+                lo = std::min(lo, p.comm_off[size_t(p.dcol[size_t(k)])]);
+                hi = std::max(hi, p.comm_off[size_t(p.dcol[size_t(k)]) + 1]);
+            }
+            if (hi - lo > in.window_cap) { lo = rb; hi = re; }
+            int64_t wb = lo & ~int64_t(1), we = (hi + 1) & ~int64_t(1);
+            int32_t wbeg = int32_t(wb), wlen = int32_t(we - wb);
+            if (wlen > in.window_cap + 2) { wbeg = 0; wlen = 0; }
+            p.max_wlen = std::max(p.max_wlen, wlen);
+            int64_t r = rb;
+            while (r < re) {
+                int64_t w = 0, s = r;
+                while (r < re && (r == s || (w < target && r - s < in.tile_max_rows))) {
+                    w += p.miss_cnt[size_t(r)] + p.pres_cnt[size_t(r)] + 8;
+                    r++;
+                }
+                Tile t{};
+                t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
+                t.g0 = int32_t(p.groups.size());
+                // groups of the tile rows [s, r)
+                int64_t q = s;
+                while (q < r) {
+                    Group G{};
+                    G.off = goff;
+                    G.r0 = int32_t(q);
+                    int64_t size = row_ints(q);
+                    if (size > in.slot_ints) {
+                        G.flags = GROUP_OVERSIZED;
+                        q++;
+                    } else {
+                        q++;
+                        while (q < r && size + row_ints(q) <= in.slot_ints) size += row_ints(q++);
+                    }
+                    G.r1 = int32_t(q);
+                    G.len = int32_t(size);
+                    // positions inside the group: headers, then missing, then present segments
+                    int64_t mpos = goff + 4 * (G.r1 - G.r0);
+                    for (int64_t v = G.r0; v < G.r1; v++) { row_pos[size_t(v)] = mpos; mpos += round_up4(p.miss_cnt[size_t(v)]); }
+                    const int32_t gi = int32_t(p.groups.size());
+                    for (int64_t v = G.r0; v < G.r1; v++) p.row_group[size_t(v)] = gi;
+                    goff += size;
+                    p.groups.push_back(G);
+                }
+                t.g1 = int32_t(p.groups.size());
+                p.tiles.push_back(t);
+            }
+        }
+        p.gstream.assign(size_t(std::max<int64_t>(goff, 4)), 0);
+        // headers (offsets relative to the group start)
+        #pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t gi = 0; gi < int64_t(p.groups.size()); gi++) {
+            const Group& G = p.groups[size_t(gi)];
+            int64_t mtot = 0;
+            for (int64_t v = G.r0; v < G.r1; v++) mtot += round_up4(p.miss_cnt[size_t(v)]);
+            int64_t ppos = row_pos[size_t(G.r0)] + mtot;
+            for (int64_t v = G.r0; v < G.r1; v++) {
+                int32_t* hdr = p.gstream.data() + G.off + 4 * (v - G.r0);
+                hdr[0] = int32_t(row_pos[size_t(v)] - G.off);
+                hdr[1] = p.miss_cnt[size_t(v)];
+                hdr[2] = int32_t(ppos - G.off);
+                hdr[3] = p.pres_cnt[size_t(v)];
+                ppos += round_up4(p.pres_cnt[size_t(v)]);
+            }
+        }
 
         // ---- fill: mark dense-block neighbours in a bitmap, scan the dense
         // column ranges for zeros (skipping the row's own diagonal entry),
@@ -193,7 +270,9 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             for (int64_t v = 0; v < n; v++) {
                 int32_t I = p.node_comm[size_t(v)];
                 int64_t o = p.perm[size_t(v)];
-                int32_t* pr = p.pres.data() + p.pres_off[size_t(v)];
+                const Group& G = p.groups[size_t(p.row_group[size_t(v)])];
+                const int32_t* hdr = p.gstream.data() + G.off + 4 * (v - G.r0);
+                int32_t* pr = p.gstream.data() + G.off + hdr[2];
                 int64_t np_ = 0;
                 for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
                     int32_t c = in.col[k];
@@ -203,7 +282,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     else pr[np_++] = w;
                 }
                 std::sort(pr, pr + np_);
-                int32_t* ms = p.miss.data() + p.miss_off[size_t(v)];
+                int32_t* ms = p.gstream.data() + G.off + hdr[0];
                 int64_t nm = 0;
                 for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
                     int32_t J = p.dcol[size_t(k)];
@@ -229,38 +308,6 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t w = p.inv_perm[size_t(c)];
                     bits[size_t(w) >> 6] = 0;
                 }
-            }
-        }
-
-        // ---- tiles: rows of one community, bounded work; staged window =
-        // the community's own columns joined with its dense column blocks
-        // when that span fits the cap, else the community's own columns.
-        int64_t total_work = 0;
-        for (int64_t v = 0; v < n; v++) total_work += p.miss_cnt[size_t(v)] + p.pres_cnt[size_t(v)] + 8;
-        int64_t target = in.tile_work > 0 ? in.tile_work : std::max<int64_t>(2048, total_work / (152 * 12));
-        for (int32_t I = 0; I < nc; I++) {
-            int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
-            if (rb == re) continue;
-            int64_t lo = rb, hi = re;
-            for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
-                lo = std::min(lo, p.comm_off[size_t(p.dcol[size_t(k)])]);
-                hi = std::max(hi, p.comm_off[size_t(p.dcol[size_t(k)]) + 1]);
-            }
-            if (hi - lo > in.window_cap) { lo = rb; hi = re; }
-            int64_t wb = lo & ~int64_t(1), we = (hi + 1) & ~int64_t(1);
-            int32_t wbeg = int32_t(wb), wlen = int32_t(we - wb);
-            if (wlen > in.window_cap + 2) { wbeg = 0; wlen = 0; }
-            p.max_wlen = std::max(p.max_wlen, wlen);
-            int64_t r = rb;
-            while (r < re) {
-                int64_t w = 0, s = r;
-                while (r < re && (r == s || (w < target && r - s < in.tile_max_rows))) {
-                    w += p.miss_cnt[size_t(r)] + p.pres_cnt[size_t(r)] + 8;
-                    r++;
-                }
-                Tile t{};
-                t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
-                p.tiles.push_back(t);
             }
         }
     } catch (const std::bad_alloc&) {

@@ -19,8 +19,23 @@ struct Tile {              // 32 bytes, read by the row kernel
     int32_t r0, r1;        // rows [r0, r1) in permuted order, all in one community
     int32_t comm;          // community of the rows
     int32_t wbeg, wlen;    // staged table window [wbeg, wbeg + wlen) (wlen = 0: none)
-    int32_t pad[3];
+    int32_t g0, g1;        // row groups [g0, g1) of the tile
+    int32_t pad;
 };
+
+// A row group: consecutive rows of one tile whose packed stream fits one
+// shared-memory slot of the row kernel (or one oversized row, read in place).
+// Packed layout at gstream[off, off + len) (int32 units, 16-byte aligned):
+//   rows x int4 header {miss_rel, n_miss, pres_rel, n_pres} (offsets relative to off)
+//   then the missing entries of every row, then the present entries of every
+//   row, each row's segment zero-padded to a multiple of 4.
+struct Group {
+    int64_t off;
+    int32_t len;
+    int32_t r0, r1;
+    int32_t flags;         // GROUP_OVERSIZED: larger than a slot, consumed from global memory
+};
+constexpr int32_t GROUP_OVERSIZED = 1;
 
 struct PlanInput {
     int64_t n = 0;
@@ -31,7 +46,8 @@ struct PlanInput {
     double tau = 0.5;                   // dense iff zero fraction < tau
     int32_t window_cap = 4096;          // max staged window entries per tile
     int64_t tile_work = 0;              // target entries per tile (0: automatic)
-    int32_t tile_max_rows = 1024;
+    int32_t tile_max_rows = 512;
+    int32_t slot_ints = 4096;           // capacity of one row-group slot (int32 units)
 };
 
 struct Plan {
@@ -46,11 +62,11 @@ struct Plan {
     std::vector<int32_t> deg;           // [n] degree without self-loops (permuted order)
     std::vector<int64_t> dptr;          // [n_comm+1] dense column blocks of each row block
     std::vector<int32_t> dcol;
-    // per-row streams; offsets in elements, each segment starts on a 16-byte
-    // boundary (multiple of 4 int32) and is zero-padded to one
-    std::vector<int64_t> miss_off, pres_off;
+    // per-row counts and the packed group stream (see Group)
     std::vector<int32_t> miss_cnt, pres_cnt;
-    std::vector<int32_t> miss, pres;    // permuted global column indices
+    std::vector<int32_t> gstream;       // permuted global column indices + headers
+    std::vector<Group> groups;
+    std::vector<int32_t> row_group;     // [n] group of each row
     std::vector<Tile> tiles;
     int32_t max_wlen = 0;
     // statistics
