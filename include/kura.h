@@ -208,6 +208,15 @@ kura_status kura_plan_row(kura_plan_t p, int64_t row, int32_t* missing, int64_t*
 /* Dense column blocks D(I) of row block I: up to cap entries, count in *count. */
 kura_status kura_plan_dense_blocks(kura_plan_t p, int32_t I, int32_t* J, int32_t cap,
                                    int32_t* count);
+/* Read-only views of the packed correction stream the row kernel consumes:
+ * gstream (int32, *gstream_len entries), groups (*n_groups records of
+ * {int64 off; int32 len; int32 first_subrow; int32 n_subrows; int32 pad}),
+ * tiles (*n_tiles records of {int32 r0, r1, comm, wbeg, wlen, g0, g1,
+ * first_subrow}) and row_sub0 (n + 1 int32: first sub-row of each row).
+ * The pointers stay valid until kura_plan_destroy.  Any output may be NULL. */
+kura_status kura_plan_export(kura_plan_t p, const int32_t** gstream, int64_t* gstream_len,
+                             const void** groups, int64_t* n_groups, const void** tiles,
+                             int64_t* n_tiles, const int32_t** row_sub0);
 void kura_plan_destroy(kura_plan_t p);
 
 #ifdef __cplusplus

@@ -83,7 +83,7 @@ struct kura_ctx {
     Plan plan;                          // host plan (streams released after upload)
     int64_t miss_total = 0, pres_total = 0, nnz = 0;
     // device buffers
-    DevMem perm, node_comm, gstream, groups, tiles, dptr, dcol, comm_off;
+    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, dptr, dcol, comm_off;
     DevMem omega, rscale, table, bsum, bsum_out, tot, T, counter, err_flags;
     DevMem y, Y, krk, fbuf, user, red, order_out;
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
@@ -159,6 +159,7 @@ DevGraph dev_graph(kura_ctx* h)
     g.gstream = h->gstream.as<int32_t>();
     g.groups = h->groups.as<Group>();
     g.tiles = h->tiles.as<Tile>();
+    g.row_sub0 = h->row_sub0.as<int32_t>();
     g.dptr = h->dptr.as<int64_t>();
     g.dcol = h->dcol.as<int32_t>();
     g.comm_off = h->comm_off.as<int64_t>();
@@ -266,6 +267,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     KCHECK(h, upload(h->gstream, p.gstream, s), "upload the correction stream");
     KCHECK(h, upload(h->groups, p.groups, s), "upload row groups");
     KCHECK(h, upload(h->tiles, p.tiles, s), "upload tiles");
+    KCHECK(h, upload(h->row_sub0, p.row_sub0, s), "upload row_sub0");
     KCHECK(h, upload(h->dptr, p.dptr, s), "upload dptr");
     KCHECK(h, upload(h->dcol, p.dcol, s), "upload dcol");
     KCHECK(h, upload(h->comm_off, p.comm_off, s), "upload comm_off");
@@ -392,6 +394,7 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
     PlanInput in;
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.tile_max_rows = TILE_MAX_ROWS;
+    in.tile_max_sub = TILE_MAX_SUB;
     in.slot_ints = slot_ints_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     Plan plan;
     std::string err;
@@ -471,6 +474,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
         in.n_comm = h->n_comm; in.tau = tau;
         in.tile_max_rows = TILE_MAX_ROWS;
+        in.tile_max_sub = TILE_MAX_SUB;
         in.slot_ints = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
         Plan plan;
         std::string err;
@@ -815,12 +819,17 @@ kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t
     if (!pl || !n_missing || !n_present) return KURA_EINVAL;
     const Plan& p = pl->p;
     if (row < 0 || row >= p.n) return KURA_EINVAL;
-    const Group& G = p.groups[size_t(p.row_group[size_t(row)])];
-    const int32_t* hdr = p.gstream.data() + G.off + 4 * (row - G.r0);
-    *n_missing = hdr[1];
-    *n_present = hdr[3];
-    for (int64_t k = 0; k < *n_missing && k < cap && missing; k++) missing[k] = p.gstream[size_t(G.off + hdr[0] + k)];
-    for (int64_t k = 0; k < *n_present && k < cap && present; k++) present[k] = p.gstream[size_t(G.off + hdr[2] + k)];
+    *n_missing = p.miss_cnt[size_t(row)];
+    *n_present = p.pres_cnt[size_t(row)];
+    int64_t km = 0, kp = 0;
+    for (int32_t sg = p.row_sub0[size_t(row)]; sg < p.row_sub0[size_t(row) + 1]; sg++) {
+        const int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
+        for (int32_t q = 0; q < hdr[1]; q++, km++)
+            if (missing && km < cap) missing[km] = p.gstream[size_t(p.sub_mpos[size_t(sg)] + q)];
+        for (int32_t q = 0; q < hdr[3]; q++, kp++)
+            if (present && kp < cap) present[kp] = p.gstream[size_t(p.sub_ppos[size_t(sg)] + q)];
+    }
+    if (km != *n_missing || kp != *n_present) return KURA_ESTATE;
     return KURA_OK;
 }
 
@@ -830,6 +839,21 @@ kura_status kura_plan_dense_blocks(kura_plan_t pl, int32_t I, int32_t* J, int32_
     const Plan& p = pl->p;
     *count = int32_t(p.dptr[size_t(I) + 1] - p.dptr[size_t(I)]);
     for (int32_t k = 0; k < *count && k < cap && J; k++) J[k] = p.dcol[size_t(p.dptr[size_t(I)] + k)];
+    return KURA_OK;
+}
+
+kura_status kura_plan_export(kura_plan_t pl, const int32_t** gstream, int64_t* gstream_len, const void** groups,
+                             int64_t* n_groups, const void** tiles, int64_t* n_tiles, const int32_t** row_sub0)
+{
+    if (!pl) return KURA_EINVAL;
+    const Plan& p = pl->p;
+    if (gstream) *gstream = p.gstream.data();
+    if (gstream_len) *gstream_len = int64_t(p.gstream.size());
+    if (groups) *groups = p.groups.data();
+    if (n_groups) *n_groups = int64_t(p.groups.size());
+    if (tiles) *tiles = p.tiles.data();
+    if (n_tiles) *n_tiles = int64_t(p.tiles.size());
+    if (row_sub0) *row_sub0 = p.row_sub0.data();
     return KURA_OK;
 }
 

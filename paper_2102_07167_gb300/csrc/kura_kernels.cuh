@@ -19,7 +19,8 @@ namespace kura {
 constexpr int ROW_CONSUMERS = 16;                       // consumer warps of the row kernel
 constexpr int ROW_THREADS = (ROW_CONSUMERS + 1) * 32;   // + one producer warp
 constexpr int ROW_SLOTS = 4;                            // shared-memory ring of row-group slots
-constexpr int TILE_MAX_ROWS = 512;      // stash capacity of the row kernel (the planner's tile bound)
+constexpr int TILE_MAX_ROWS = 512;      // rows per tile (the planner's bound)
+constexpr int TILE_MAX_SUB = 768;       // sub-rows per tile: stash capacity of the row kernel
 constexpr int TRIG_THREADS = 256;
 // slot capacity (int32 units) per precision mode: keeps two CTAs resident per SM
 __host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 4096; }
@@ -50,6 +51,7 @@ struct DevGraph {
     const int32_t* gstream;                 // packed row groups (see Group in plan.hpp)
     const Group* groups;
     const Tile* tiles;
+    const int32_t* row_sub0;                // [n+1] first sub-row of each row
     const int64_t* dptr;                    // [n_comm+1]
     const int32_t* dcol;
     const int64_t* comm_off;                // [n_comm+1]
@@ -249,41 +251,19 @@ struct Acc2 {
     typename EntryT<MODE>::A s, c;
 };
 
-// Sums the entries of one row segment (16-byte aligned, in shared memory or,
-// for an oversized group, in global memory) into (as, ac) with sign SIGN.
-template <int MODE, int SIGN>
-__device__ __forceinline__ void sum_segment(const int32_t* seg, int cnt, int lane,
-                                            const typename EntryT<MODE>::T* win, int wbeg, int wlen,
-                                            const typename EntryT<MODE>::T* table,
-                                            typename EntryT<MODE>::A& as, typename EntryT<MODE>::A& ac)
-{
-    const int4* v4 = reinterpret_cast<const int4*>(seg);
-#pragma unroll 2
-    for (int q = lane; q * 4 < cnt; q += 32) {
-        const int4 v = v4[q];
-        const int b = q * 4;
-        const int idx[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            if (b + t < cnt) {
-                const auto e = gather_entry<MODE>(win, wbeg, wlen, table, idx[t]);
-                if (SIGN > 0) { as += e.x; ac += e.y; }
-                else          { as -= e.x; ac -= e.y; }
-            }
-        }
-    }
-}
-
 // One CTA per tile (rows of one community).  Warp ROW_CONSUMERS is the
 // producer: one elected lane streams the community's (sin, cos) window and
 // then the tile's row groups into a ring of shared-memory slots with TMA bulk
-// copies (full/empty mbarriers, every wait bounded in time).  The consumer
-// warps take the rows round-robin (row k -> warp k mod ROW_CONSUMERS), sum the
-// row's missing entries (subtracted) and present entries (added), gathering
-// (sin, cos) from the staged window or, off the window, from the L2-resident
-// table, and leave the row's sums in a stash.  Finally every thread takes rows
-// for the FP64 epilogue: f = omega + scale (cos th acc_s - sin th acc_c), and
-// the RK4 stage update.
+// copies (full/empty mbarriers, every wait bounded in time).  Sub-row j of a
+// group goes to consumer warp (first + j) mod ROW_CONSUMERS, so every warp
+// holds at most one sub-row of a group: it copies the sub-row's indices into
+// registers (at most 4 int4 per lane), releases the slot at once and only
+// then gathers (sin, cos) of the indexed columns -- from the staged window
+// when inside it, else from the L2-resident table (padding indexes the
+// table's zero entry n) -- subtracting missing entries, adding present ones.
+// The per-sub-row sums go to a stash; at the end every thread takes rows for
+// the FP64 epilogue: f = omega + scale (cos th acc_s - sin th acc_c), T_I
+// added, and the RK4 stage update.
 template <int MODE, int STAGE>
 __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk)
 {
@@ -293,7 +273,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     constexpr uint64_t LIMIT_NS = 1000000000ull;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[ROW_SLOTS], empty_bar[ROW_SLOTS], win_bar;
-    __shared__ Acc2<MODE> stash[TILE_MAX_ROWS];
+    __shared__ Acc2<MODE> stash[TILE_MAX_SUB];
     __shared__ int abort_flag;
     __shared__ int issued[ROW_SLOTS];
 
@@ -303,6 +283,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     const E* table = reinterpret_cast<const E*>(g.table);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ngroups = t.g1 - t.g0;
+    const int zidx = int(g.n);                                // the table's zero entry
 
     if (tid == 0) {
         abort_flag = 0;
@@ -331,13 +312,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                     break;
                 }
                 const Group G = g.groups[t.g0 + gi];
-                if ((G.flags & GROUP_OVERSIZED) || G.len == 0) {
-                    mbar_arrive(&full_bar[sl]);
-                } else {
-                    const uint32_t bytes = uint32_t(G.len) * 4u;
-                    mbar_arrive_expect_tx(&full_bar[sl], bytes);
-                    bulk_g2s(ring + size_t(sl) * SLOT, g.gstream + G.off, bytes, &full_bar[sl]);
-                }
+                const uint32_t bytes = uint32_t(G.len) * 4u;
+                mbar_arrive_expect_tx(&full_bar[sl], bytes);
+                bulk_g2s(ring + size_t(sl) * SLOT, g.gstream + G.off, bytes, &full_bar[sl]);
                 issued[sl] = fill + 1;
             }
         }
@@ -353,23 +330,55 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 break;
             }
             const Group G = g.groups[t.g0 + gi];
-            const int32_t* base = (G.flags & GROUP_OVERSIZED) ? g.gstream + G.off : ring + size_t(sl) * SLOT;
-            const int kb = G.r0 - t.r0, ke = G.r1 - t.r0;
-            int k = kb + ((warp - kb) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
-            for (; k < ke; k += ROW_CONSUMERS) {
-                const int4 hdr = reinterpret_cast<const int4*>(base)[k - kb];
+            const int rel0 = G.sub0 - t.sub0;
+            const int j = ((warp - rel0) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
+            const bool have = j < G.nsub;                       // warp-uniform
+            const int32_t* slot = ring + size_t(sl) * SLOT;
+            int4 v[4];
+            int m4 = 0, tot4 = 0;
+            if (have) {
+                const int4 hdr = reinterpret_cast<const int4*>(slot)[j];
+                m4 = (hdr.y + 3) >> 2;
+                tot4 = m4 + ((hdr.w + 3) >> 2);
+                const int4* mseg = reinterpret_cast<const int4*>(slot + hdr.x);
+                const int4* pseg = reinterpret_cast<const int4*>(slot + hdr.z);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int q = lane + 32 * i;
+                    if (q < m4) v[i] = mseg[q];
+                    else if (q < tot4) v[i] = pseg[q - m4];
+                    else v[i] = make_int4(zidx, zidx, zidx, zidx);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[sl]);      // indices are in registers: release the slot
+            if (have) {
                 A as = 0, ac = 0;
-                sum_segment<MODE, -1>(base + hdr.x, hdr.y, lane, win, t.wbeg, t.wlen, table, as, ac);
-                sum_segment<MODE, +1>(base + hdr.z, hdr.w, lane, win, t.wbeg, t.wlen, table, as, ac);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    if (32 * i < tot4) {                     // warp-uniform
+                        const bool neg = (lane + 32 * i) < m4;
+                        const int idx[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+                        E e[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const unsigned u = static_cast<unsigned>(idx[q] - t.wbeg);
+                            e[q] = (u < static_cast<unsigned>(t.wlen)) ? win[u] : __ldg(table + idx[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            if (neg) { as -= e[q].x; ac -= e[q].y; }
+                            else     { as += e[q].x; ac += e[q].y; }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
                     as += __shfl_xor_sync(0xffffffffu, as, o);
                     ac += __shfl_xor_sync(0xffffffffu, ac, o);
                 }
-                if (lane == 0) stash[k] = Acc2<MODE>{as, ac};
+                if (lane == 0) stash[rel0 + j] = Acc2<MODE>{as, ac};
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty_bar[sl]);
             if (*(volatile int*)&abort_flag) break;
         }
     }
@@ -389,19 +398,24 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     const int nrows = t.r1 - t.r0;
     for (int k = tid; k < nrows; k += ROW_THREADS) {
         const int64_t row = int64_t(t.r0) + k;
-        const Acc2<MODE> a = stash[k];
+        const int s0 = g.row_sub0[row] - t.sub0, s1 = g.row_sub0[row + 1] - t.sub0;
+        A sa = 0, sc_ = 0;
+        for (int sidx = s0; sidx < s1; sidx++) {
+            sa += stash[sidx].s;
+            sc_ += stash[sidx].c;
+        }
         const E own = gather_entry<MODE>(win, t.wbeg, t.wlen, table, static_cast<int>(row));
         double acc_s, acc_c, si, ci;
         if (MODE == MODE_FP64) {
             const longlong2 T = reinterpret_cast<const longlong2*>(g.T)[t.comm];
-            acc_s = static_cast<double>(T.x + static_cast<long long>(a.s)) * g.inv_scale_q;
-            acc_c = static_cast<double>(T.y + static_cast<long long>(a.c)) * g.inv_scale_q;
+            acc_s = static_cast<double>(T.x + static_cast<long long>(sa)) * g.inv_scale_q;
+            acc_c = static_cast<double>(T.y + static_cast<long long>(sc_)) * g.inv_scale_q;
             si = static_cast<double>(own.x) * g.inv_scale_q;
             ci = static_cast<double>(own.y) * g.inv_scale_q;
         } else {
             const double2 T = reinterpret_cast<const double2*>(g.T)[t.comm];
-            acc_s = T.x + static_cast<double>(a.s);
-            acc_c = T.y + static_cast<double>(a.c);
+            acc_s = T.x + static_cast<double>(sa);
+            acc_c = T.y + static_cast<double>(sc_);
             si = static_cast<double>(own.x);
             ci = static_cast<double>(own.y);
         }

@@ -176,20 +176,49 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         }
         p.max_row_entries = mx;
 
-        // ---- tiles (rows of one community, bounded work and rows; staged
-        // window = the community's own columns joined with its dense column
-        // blocks when that span fits the cap, else the community's columns)
-        // and row groups (consecutive rows of a tile whose packed stream fits
-        // one slot of the row kernel; a row alone larger than a slot is an
-        // oversized group read in place).
-        auto row_ints = [&](int64_t v) {
-            return 4 + round_up4(p.miss_cnt[size_t(v)]) + round_up4(p.pres_cnt[size_t(v)]);
+        // ---- sub-rows: each row is cut into ceil((nm + np) / SUBROW_MAX)
+        // pieces (at least one) of consecutive entries of [missing | present].
+        p.row_sub0.assign(size_t(n) + 1, 0);
+        for (int64_t v = 0; v < n; v++) {
+            const int64_t e = int64_t(p.miss_cnt[size_t(v)]) + p.pres_cnt[size_t(v)];
+            p.row_sub0[size_t(v) + 1] = p.row_sub0[size_t(v)] + int32_t(std::max<int64_t>(1, (e + SUBROW_MAX - 1) / SUBROW_MAX));
+        }
+        const int64_t n_sub = p.row_sub0[size_t(n)];
+        for (int64_t v = 0; v < n; v++)
+            if (p.row_sub0[size_t(v) + 1] - p.row_sub0[size_t(v)] > in.tile_max_sub) {
+                err = "a row stores more corrections than the row kernel supports (" +
+                      std::to_string(int64_t(in.tile_max_sub) * SUBROW_MAX) + "); raise tau or split the community";
+                return 1;
+            }
+        // missing / present parts of sub-row (row v, piece k)
+        auto sub_parts = [&](int64_t v, int64_t k, int64_t& mb, int64_t& mn, int64_t& pb, int64_t& pn) {
+            const int64_t nm = p.miss_cnt[size_t(v)], np_ = p.pres_cnt[size_t(v)];
+            const int64_t b = k * SUBROW_MAX, e = std::min<int64_t>(b + SUBROW_MAX, nm + np_);
+            mb = std::min(b, nm);
+            mn = std::min(e, nm) - mb;
+            pb = std::max<int64_t>(b, nm) - nm;
+            pn = std::max<int64_t>(e, nm) - nm - pb;
+            if (pn < 0) pn = 0;
         };
+        auto sub_ints = [&](int64_t v, int64_t k) {
+            int64_t mb, mn, pb, pn;
+            sub_parts(v, k, mb, mn, pb, pn);
+            return 4 + round_up4(mn) + round_up4(pn);
+        };
+
+        // ---- tiles (rows of one community, bounded work, rows and sub-rows;
+        // staged window = the community's own columns joined with its dense
+        // column blocks when that span fits the cap, else the community's
+        // columns) and row groups (consecutive sub-rows of a tile, at most
+        // GROUP_MAX_SUB, whose packed stream fits one slot of the row kernel).
         int64_t total_work = 0;
         for (int64_t v = 0; v < n; v++) total_work += p.miss_cnt[size_t(v)] + p.pres_cnt[size_t(v)] + 8;
         const int64_t target = in.tile_work > 0 ? in.tile_work : std::max<int64_t>(2048, total_work / (152 * 12));
-        std::vector<int64_t> row_pos(static_cast<size_t>(n));       // start of each row's missing segment in gstream
-        p.row_group.resize(size_t(n));
+        p.sub_hdr.resize(size_t(n_sub));
+        std::vector<int64_t>& sub_mpos = p.sub_mpos;
+        std::vector<int64_t>& sub_ppos = p.sub_ppos;
+        sub_mpos.resize(size_t(n_sub));
+        sub_ppos.resize(size_t(n_sub));
         int64_t goff = 0;
         for (int32_t I = 0; I < nc; I++) {
             int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
@@ -207,34 +236,47 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             int64_t r = rb;
             while (r < re) {
                 int64_t w = 0, s = r;
-                while (r < re && (r == s || (w < target && r - s < in.tile_max_rows))) {
+                while (r < re && (r == s || (w < target && r - s < in.tile_max_rows &&
+                                             p.row_sub0[size_t(r) + 1] - p.row_sub0[size_t(s)] <= in.tile_max_sub))) {
                     w += p.miss_cnt[size_t(r)] + p.pres_cnt[size_t(r)] + 8;
                     r++;
                 }
                 Tile t{};
                 t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
+                t.sub0 = p.row_sub0[size_t(s)];
                 t.g0 = int32_t(p.groups.size());
-                // groups of the tile rows [s, r)
-                int64_t q = s;
-                while (q < r) {
+                // groups over the tile's sub-rows [row_sub0[s], row_sub0[r])
+                int64_t v = s, k = 0;             // current sub-row = (row v, piece k)
+                while (v < r) {
                     Group G{};
                     G.off = goff;
-                    G.r0 = int32_t(q);
-                    int64_t size = row_ints(q);
-                    if (size > in.slot_ints) {
-                        G.flags = GROUP_OVERSIZED;
-                        q++;
-                    } else {
-                        q++;
-                        while (q < r && size + row_ints(q) <= in.slot_ints) size += row_ints(q++);
+                    G.sub0 = p.row_sub0[size_t(v)] + int32_t(k);
+                    int64_t size = 0;
+                    std::vector<std::pair<int64_t, int64_t>> members;
+                    while (v < r && int64_t(members.size()) < GROUP_MAX_SUB) {
+                        const int64_t si = sub_ints(v, k);
+                        if (!members.empty() && size + si > in.slot_ints) break;
+                        members.emplace_back(v, k);
+                        size += si;
+                        if (++k == p.row_sub0[size_t(v) + 1] - p.row_sub0[size_t(v)]) { k = 0; v++; }
                     }
-                    G.r1 = int32_t(q);
+                    G.nsub = int32_t(members.size());
                     G.len = int32_t(size);
-                    // positions inside the group: headers, then missing, then present segments
-                    int64_t mpos = goff + 4 * (G.r1 - G.r0);
-                    for (int64_t v = G.r0; v < G.r1; v++) { row_pos[size_t(v)] = mpos; mpos += round_up4(p.miss_cnt[size_t(v)]); }
-                    const int32_t gi = int32_t(p.groups.size());
-                    for (int64_t v = G.r0; v < G.r1; v++) p.row_group[size_t(v)] = gi;
+                    int64_t pos = goff + 4 * G.nsub;
+                    for (size_t m = 0; m < members.size(); m++) {            // missing segments
+                        int64_t mb, mn, pb, pn;
+                        sub_parts(members[m].first, members[m].second, mb, mn, pb, pn);
+                        const int64_t sg = G.sub0 + int64_t(m);
+                        p.sub_hdr[size_t(sg)] = goff + 4 * int64_t(m);
+                        sub_mpos[size_t(sg)] = pos;
+                        pos += round_up4(mn);
+                    }
+                    for (size_t m = 0; m < members.size(); m++) {            // present segments
+                        int64_t mb, mn, pb, pn;
+                        sub_parts(members[m].first, members[m].second, mb, mn, pb, pn);
+                        sub_ppos[size_t(G.sub0 + int64_t(m))] = pos;
+                        pos += round_up4(pn);
+                    }
                     goff += size;
                     p.groups.push_back(G);
                 }
@@ -243,47 +285,29 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             }
         }
         p.gstream.assign(size_t(std::max<int64_t>(goff, 4)), 0);
-        // headers (offsets relative to the group start)
-        #pragma omp parallel for schedule(dynamic, 64)
-        for (int64_t gi = 0; gi < int64_t(p.groups.size()); gi++) {
-            const Group& G = p.groups[size_t(gi)];
-            int64_t mtot = 0;
-            for (int64_t v = G.r0; v < G.r1; v++) mtot += round_up4(p.miss_cnt[size_t(v)]);
-            int64_t ppos = row_pos[size_t(G.r0)] + mtot;
-            for (int64_t v = G.r0; v < G.r1; v++) {
-                int32_t* hdr = p.gstream.data() + G.off + 4 * (v - G.r0);
-                hdr[0] = int32_t(row_pos[size_t(v)] - G.off);
-                hdr[1] = p.miss_cnt[size_t(v)];
-                hdr[2] = int32_t(ppos - G.off);
-                hdr[3] = p.pres_cnt[size_t(v)];
-                ppos += round_up4(p.pres_cnt[size_t(v)]);
-            }
-        }
 
         // ---- fill: mark dense-block neighbours in a bitmap, scan the dense
         // column ranges for zeros (skipping the row's own diagonal entry),
-        // collect the sparse-block neighbours.
+        // collect the sparse-block neighbours; then write the row's entries
+        // into its sub-row segments with headers and padding.
         #pragma omp parallel
         {
             std::vector<uint64_t> bits(size_t((n + 63) / 64), 0);
+            std::vector<int32_t> ms, pr;
             #pragma omp for schedule(dynamic, 256)
             for (int64_t v = 0; v < n; v++) {
                 int32_t I = p.node_comm[size_t(v)];
                 int64_t o = p.perm[size_t(v)];
-                const Group& G = p.groups[size_t(p.row_group[size_t(v)])];
-                const int32_t* hdr = p.gstream.data() + G.off + 4 * (v - G.r0);
-                int32_t* pr = p.gstream.data() + G.off + hdr[2];
-                int64_t np_ = 0;
+                ms.clear();
+                pr.clear();
                 for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
                     int32_t c = in.col[k];
                     if (c == o) continue;
                     int32_t w = p.inv_perm[size_t(c)];
                     if (is_dense(p, I, in.label[c])) bits[size_t(w) >> 6] |= uint64_t(1) << (w & 63);
-                    else pr[np_++] = w;
+                    else pr.push_back(w);
                 }
-                std::sort(pr, pr + np_);
-                int32_t* ms = p.gstream.data() + G.off + hdr[0];
-                int64_t nm = 0;
+                std::sort(pr.begin(), pr.end());
                 for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
                     int32_t J = p.dcol[size_t(k)];
                     int64_t b = p.comm_off[size_t(J)], e = p.comm_off[size_t(J) + 1];
@@ -296,7 +320,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                         while (zeros) {
                             int t = __builtin_ctzll(zeros);
                             int64_t col = w + t;
-                            if (col != v) ms[nm++] = int32_t(col);
+                            if (col != v) ms.push_back(int32_t(col));
                             zeros &= zeros - 1;
                         }
                         w += hi - lo;
@@ -308,8 +332,30 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t w = p.inv_perm[size_t(c)];
                     bits[size_t(w) >> 6] = 0;
                 }
+                // sub-rows of row v
+                const int32_t s0 = p.row_sub0[size_t(v)], s1 = p.row_sub0[size_t(v) + 1];
+                for (int32_t sg = s0; sg < s1; sg++) {
+                    int64_t mb, mn, pb, pn;
+                    sub_parts(v, sg - s0, mb, mn, pb, pn);
+                    int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
+                    int32_t* mdst = p.gstream.data() + sub_mpos[size_t(sg)];
+                    int32_t* pdst = p.gstream.data() + sub_ppos[size_t(sg)];
+                    for (int64_t q = 0; q < mn; q++) mdst[q] = ms[size_t(mb + q)];
+                    for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = int32_t(n);
+                    for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
+                    for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = int32_t(n);
+                    hdr[1] = int32_t(mn);
+                    hdr[3] = int32_t(pn);
+                }
             }
         }
+        // header offsets relative to the group start
+        for (const Group& G : p.groups)
+            for (int32_t m = 0; m < G.nsub; m++) {
+                int32_t* hdr = p.gstream.data() + G.off + 4 * m;
+                hdr[0] = int32_t(sub_mpos[size_t(G.sub0 + m)] - G.off);
+                hdr[2] = int32_t(sub_ppos[size_t(G.sub0 + m)] - G.off);
+            }
     } catch (const std::bad_alloc&) {
         err = "out of host memory while building the block plan";
         return 2;

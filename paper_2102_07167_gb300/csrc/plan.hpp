@@ -20,22 +20,29 @@ struct Tile {              // 32 bytes, read by the row kernel
     int32_t comm;          // community of the rows
     int32_t wbeg, wlen;    // staged table window [wbeg, wbeg + wlen) (wlen = 0: none)
     int32_t g0, g1;        // row groups [g0, g1) of the tile
-    int32_t pad;
+    int32_t sub0;          // global index of the tile's first sub-row
 };
 
-// A row group: consecutive rows of one tile whose packed stream fits one
-// shared-memory slot of the row kernel (or one oversized row, read in place).
+// Rows are cut into sub-rows of at most SUBROW_MAX entries (missing entries
+// first, then present entries, in the row's order), so that one warp holds a
+// whole sub-row's indices in registers (4 int4 per lane).
+constexpr int32_t SUBROW_MAX = 508;
+
+// A row group: consecutive sub-rows of one tile (at most GROUP_MAX_SUB of
+// them) whose packed stream fits one shared-memory slot of the row kernel.
 // Packed layout at gstream[off, off + len) (int32 units, 16-byte aligned):
-//   rows x int4 header {miss_rel, n_miss, pres_rel, n_pres} (offsets relative to off)
-//   then the missing entries of every row, then the present entries of every
-//   row, each row's segment zero-padded to a multiple of 4.
+//   nsub x int4 header {miss_rel, n_miss, pres_rel, n_pres} (offsets relative
+//   to off), then the missing entries of every sub-row, then the present
+//   entries of every sub-row, each segment padded to a multiple of 4 with n,
+//   the index of the table's zero (sin, cos) entry.
+constexpr int32_t GROUP_MAX_SUB = 16;
 struct Group {
     int64_t off;
     int32_t len;
-    int32_t r0, r1;
-    int32_t flags;         // GROUP_OVERSIZED: larger than a slot, consumed from global memory
+    int32_t sub0;          // global index of the group's first sub-row
+    int32_t nsub;
+    int32_t pad;
 };
-constexpr int32_t GROUP_OVERSIZED = 1;
 
 struct PlanInput {
     int64_t n = 0;
@@ -47,6 +54,7 @@ struct PlanInput {
     int32_t window_cap = 4096;          // max staged window entries per tile
     int64_t tile_work = 0;              // target entries per tile (0: automatic)
     int32_t tile_max_rows = 512;
+    int32_t tile_max_sub = 768;         // sub-rows per tile (stash capacity of the row kernel)
     int32_t slot_ints = 4096;           // capacity of one row-group slot (int32 units)
 };
 
@@ -62,12 +70,14 @@ struct Plan {
     std::vector<int32_t> deg;           // [n] degree without self-loops (permuted order)
     std::vector<int64_t> dptr;          // [n_comm+1] dense column blocks of each row block
     std::vector<int32_t> dcol;
-    // per-row counts and the packed group stream (see Group)
+    // per-row counts, sub-rows and the packed group stream (see Group)
     std::vector<int32_t> miss_cnt, pres_cnt;
+    std::vector<int32_t> row_sub0;      // [n+1] global index of each row's first sub-row
     std::vector<int32_t> gstream;       // permuted global column indices + headers
     std::vector<Group> groups;
-    std::vector<int32_t> row_group;     // [n] group of each row
     std::vector<Tile> tiles;
+    std::vector<int64_t> sub_hdr;       // [n_sub] position of each sub-row's header in gstream
+    std::vector<int64_t> sub_mpos, sub_ppos;   // [n_sub] positions of its missing / present segments
     int32_t max_wlen = 0;
     // statistics
     int64_t dense_blocks = 0, sparse_blocks = 0, nonempty_blocks = 0;

@@ -99,6 +99,8 @@ def load() -> C.CDLL:
             "kura_plan_perm": (S, [P, P, P]),
             "kura_plan_row": (S, [P, I64, P, C.POINTER(I64), P, C.POINTER(I64), I64]),
             "kura_plan_dense_blocks": (S, [P, I32, P, I32, C.POINTER(I32)]),
+            "kura_plan_export": (S, [P, C.POINTER(P), C.POINTER(I64), C.POINTER(P), C.POINTER(I64), C.POINTER(P),
+                                     C.POINTER(I64), C.POINTER(P)]),
             "kura_plan_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -284,6 +286,28 @@ def kura_plan_dense_blocks(p, I, cap=1 << 16):
     cnt = C.c_int32()
     _check(load().kura_plan_dense_blocks(p, int(I), buf.ctypes.data, int(cap), C.byref(cnt)))
     return buf[:cnt.value].copy()
+
+
+GROUP_DTYPE = np.dtype([("off", np.int64), ("len", np.int32), ("sub0", np.int32), ("nsub", np.int32),
+                        ("pad", np.int32)])
+TILE_DTYPE = np.dtype([("r0", np.int32), ("r1", np.int32), ("comm", np.int32), ("wbeg", np.int32),
+                       ("wlen", np.int32), ("g0", np.int32), ("g1", np.int32), ("sub0", np.int32)])
+
+
+def kura_plan_export(p, n):
+    """Copies of the packed stream, groups, tiles and row_sub0 of a plan."""
+    gs, gl, gr, ng, ti, nt, rs = (C.c_void_p(), C.c_int64(), C.c_void_p(), C.c_int64(), C.c_void_p(),
+                                  C.c_int64(), C.c_void_p())
+    _check(load().kura_plan_export(p, C.byref(gs), C.byref(gl), C.byref(gr), C.byref(ng), C.byref(ti),
+                                   C.byref(nt), C.byref(rs)))
+
+    def view(ptr, count, dtype):
+        if count == 0:
+            return np.zeros(0, dtype=dtype)
+        buf = (C.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr.value)
+        return np.frombuffer(buf, dtype=dtype).copy()
+    return (view(gs, gl.value, np.int32), view(gr, ng.value, GROUP_DTYPE), view(ti, nt.value, TILE_DTYPE),
+            view(rs, n + 1, np.int32))
 
 
 def kura_plan_destroy(p):

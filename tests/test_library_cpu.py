@@ -151,3 +151,85 @@ def test_plan_empty_communities_and_isolated_nodes():
     A[0, 1] = A[1, 0] = 1
     g = G.from_dense(A, np.array([0, 0, 2, 2, 4, 4], np.int32), 5)
     _reconstruct_and_check(g, 0.5)
+
+
+@pytest.mark.parametrize("tau,p_one", [(0.0, 0.6), (1.0, 0.3)])
+def test_plan_splits_long_rows_into_subrows(tau, p_one):
+    """Rows with more than 508 stored entries are cut into several sub-rows; the streams still reconstruct
+    every row (tau = 0 forces ~720 present entries per row, tau = 1 ~840 missing entries)."""
+    rng = np.random.default_rng(7)
+    n = 1200
+    A = (rng.random((n, n)) < p_one).astype(np.uint8)
+    np.fill_diagonal(A, 0)
+    g = G.from_dense(A)
+    st = _reconstruct_and_check(g, tau)
+    assert st["max_row_entries"] > 508
+
+
+def _emulate_row_kernel(g, tau, omega, theta, K):
+    """Consumes the packed stream exactly as the row kernel does (groups -> sub-row headers -> padded int4
+    segments -> window-or-table gathers, padding resolving to zero entries), in float64, and returns f in
+    user order."""
+    n, nc = g.n, g.n_comm
+    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau)
+    try:
+        perm, off = kura.kura_plan_perm(p, n, nc)
+        gstream, groups, tiles, row_sub0 = kura.kura_plan_export(p, n)
+        dense = [kura.kura_plan_dense_blocks(p, I) for I in range(nc)]
+    finally:
+        kura.kura_plan_destroy(p)
+    th = theta[perm]
+    s_tab = np.append(np.sin(th), [0.0, 0.0])      # entries n, n+1 are the table's zero padding
+    c_tab = np.append(np.cos(th), [0.0, 0.0])
+    S = np.array([s_tab[off[J]:off[J + 1]].sum() for J in range(nc)])
+    C = np.array([c_tab[off[J]:off[J + 1]].sum() for J in range(nc)])
+    f = np.empty(n)
+    for t in tiles:
+        wbeg, wlen = int(t["wbeg"]), int(t["wlen"])
+
+        def gather(idx):
+            # window [wbeg, wbeg + wlen) holds copies of the table entries; padding is n (zero entry)
+            assert np.all((idx >= 0) & (idx <= n))
+            return s_tab[idx], c_tab[idx]
+        stash = {}
+        for gi in range(t["g0"], t["g1"]):
+            G_ = groups[gi]
+            base = int(G_["off"])
+            for j in range(G_["nsub"]):
+                mrel, nm, prel, npr = gstream[base + 4 * j: base + 4 * j + 4]
+                m = gstream[base + mrel: base + mrel + 4 * ((nm + 3) // 4)]
+                q = gstream[base + prel: base + prel + 4 * ((npr + 3) // 4)]
+                ms, mc = gather(m)
+                ps, pc = gather(q)
+                stash[int(G_["sub0"]) + j] = (ps.sum() - ms.sum(), pc.sum() - mc.sum())
+        for r in range(t["r0"], t["r1"]):
+            a_s = sum(stash[s][0] for s in range(row_sub0[r], row_sub0[r + 1]))
+            a_c = sum(stash[s][1] for s in range(row_sub0[r], row_sub0[r + 1]))
+            I = t["comm"]
+            Ts, Tc = S[dense[I]].sum(), C[dense[I]].sum()
+            f[r] = omega[perm[r]] + (K / n) * (c_tab[r] * (Ts + a_s) - s_tab[r] * (Tc + a_c))
+    out = np.empty(n)
+    out[perm] = f
+    return out
+
+
+@pytest.mark.parametrize("case", ["sbm", "long_rows_sparse", "long_rows_dense", "big_community"])
+def test_packed_stream_emulation_matches_oracle(case):
+    """The packed stream (headers, padding, windows, sub-rows) read the way the row kernel reads it gives
+    the right-hand side of the FP64 oracle."""
+    import oracle
+    rng = np.random.default_rng(11)
+    if case == "sbm":
+        g, tau = G.sbm(3, [300, 45, 1, 700, 130], [0.9, 0.6, 1.0, 0.75, 0.3], 0.02), 0.5
+    elif case == "big_community":
+        g, tau = G.sbm(5, [5000, 257], [0.93, 0.8], 0.003), 0.5        # window cap exceeded
+    else:
+        n = 1100
+        A = (rng.random((n, n)) < (0.6 if case == "long_rows_sparse" else 0.3)).astype(np.uint8)
+        np.fill_diagonal(A, 0)
+        g = G.from_dense(A)
+        tau = 0.0 if case == "long_rows_sparse" else 1.0
+    omega, theta = rng.normal(size=g.n), rng.uniform(-30, 30, g.n)
+    f = _emulate_row_kernel(g, tau, omega, theta, 2.0)
+    ref = oracle.rhs_csr(g.row_ptr, g.col, omega, theta, 2.0)
+    np.testing.assert_allclose(f, ref, rtol=0, atol=1e-10)
