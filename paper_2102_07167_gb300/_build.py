@@ -35,14 +35,17 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", INCLUDE, "-I", CSRC]
-    cu_obj = os.path.join(BUILD, "kura_capi.o")
+    cu_srcs = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    objs, cmds = [], []
+    for f in cu_srcs:
+        o = os.path.join(BUILD, f[:-3] + ".o")
+        objs.append(o)
+        cmds.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", *inc,
+                     "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(CSRC, f), "-o", o])
     cpp_obj = os.path.join(BUILD, "plan.o")
-    cmds = [
-        [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", *inc,
-         "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(CSRC, "kura_capi.cu"), "-o", cu_obj],
-        ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c", os.path.join(CSRC, "plan.cpp"),
-         "-o", cpp_obj],
-    ]
+    objs.append(cpp_obj)
+    cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c", os.path.join(CSRC, "plan.cpp"),
+                 "-o", cpp_obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -50,12 +53,12 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"build step failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return r.stdout + r.stderr
 
-    with ThreadPoolExecutor(2) as ex:
+    with ThreadPoolExecutor(len(cmds)) as ex:
         outs = list(ex.map(run, cmds))
     if verbose:
-        print(outs[0])
+        print("".join(outs))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, ARCH, "-shared", "-o", tmp, cu_obj, cpp_obj, "-Xcompiler", "-fopenmp", "-lgomp"])
+    run([nvcc, ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

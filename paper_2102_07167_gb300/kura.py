@@ -94,6 +94,7 @@ def load() -> C.CDLL:
             "kura_sync": (S, [P]),
             "kura_last_error": (C.c_char_p, [P]),
             "kura_destroy": (None, [P]),
+            "kura_order_params_static": (S, [I64, P, P, I32, P, P]),
             "kura_plan_build": (S, [I64, P, P, P, I32, D, C.POINTER(P)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
             "kura_plan_perm": (S, [P, P, P]),
@@ -230,6 +231,19 @@ def kura_kernel_times(h, cap: int = 4096) -> np.ndarray:
     cnt = C.c_int32()
     _check(load().kura_kernel_times(h, buf.ctypes.data, cap, C.byref(cnt)), h)
     return buf[:min(cnt.value, cap)].copy()
+
+
+STATIC_MAX_COMM = 4096
+
+
+def kura_order_params_static(n, theta, label, n_comm, out, stream=None):
+    """Order parameters into out[2 + 2 n_comm] (device) with the library's static scratch; allocates
+    nothing.  theta, label (or None), out: device tensors."""
+    s = _current_stream() if stream is None else int(stream)
+    rc = load().kura_order_params_static(int(n), _ptr(theta, n=n),
+                                         _ptr(label, np.int32, n) if label is not None else None,
+                                         int(n_comm), _ptr(out, n=2 + 2 * n_comm), s or None)
+    _check(rc, None)
 
 
 def kura_set_stream(h, stream):
