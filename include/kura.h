@@ -74,7 +74,12 @@ typedef struct {
     /* keep a host copy of the CSR (needed by kura_classify_blocks with a new
      * tau and by the direct-summation baseline); default 1 */
     int32_t keep_host_csr;
-    int32_t reserved[7];
+    int32_t reserved0;
+    /* index encoding of a community's dense-block zeros: a bitmap over the
+     * staged window when their fraction exceeds this, else an index list;
+     * negative (default): always index lists */
+    double bitmap_zmin;
+    int32_t reserved[4];
 } kura_opts;
 
 typedef struct {
@@ -221,10 +226,11 @@ kura_status kura_order_params_static(int64_t n, const double* theta, const int32
 /* ---------------------------------------------------------------------
  * Host-only block plan (no GPU needed): the permutation, classification and
  * correction streams that kura_create uploads, exposed for inspection.
- * Arguments as for kura_create; tau in [0, 1].
+ * Arguments as for kura_create (opts nullable: defaults); the layout follows
+ * opts->precision, opts->tau and opts->bitmap_zmin.
  */
 kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* col,
-                            const int32_t* label, int32_t n_comm, double tau,
+                            const int32_t* label, int32_t n_comm, const kura_opts* opts,
                             kura_plan_t* out);
 /* stats of the plan (the byte counts assume KURA_PREC_FP64) */
 kura_status kura_plan_stats(kura_plan_t p, kura_block_stats* stats);
@@ -240,15 +246,18 @@ kura_status kura_plan_row(kura_plan_t p, int64_t row, int32_t* missing, int64_t*
 /* Dense column blocks D(I) of row block I: up to cap entries, count in *count. */
 kura_status kura_plan_dense_blocks(kura_plan_t p, int32_t I, int32_t* J, int32_t cap,
                                    int32_t* count);
-/* Read-only views of the packed correction stream the row kernel consumes:
+/* Read-only views of the packed correction data the row kernel consumes:
  * gstream (int32, *gstream_len entries), groups (*n_groups records of
  * {int64 off; int32 len; int32 first_subrow; int32 n_subrows; int32 pad}),
  * tiles (*n_tiles records of {int32 r0, r1, comm, wbeg, wlen, g0, g1,
- * first_subrow}) and row_sub0 (n + 1 int32: first sub-row of each row).
- * The pointers stay valid until kura_plan_destroy.  Any output may be NULL. */
+ * first_subrow; int64 bitmap_off; int32 n_superwords, flags}), row_sub0
+ * (n + 1 int32: first sub-row of each row) and the row bitmaps of tiles with
+ * flag 1 (uint32, *bitmap_len words).  The pointers stay valid until
+ * kura_plan_destroy.  Any output may be NULL. */
 kura_status kura_plan_export(kura_plan_t p, const int32_t** gstream, int64_t* gstream_len,
                              const void** groups, int64_t* n_groups, const void** tiles,
-                             int64_t* n_tiles, const int32_t** row_sub0);
+                             int64_t* n_tiles, const int32_t** row_sub0, const uint32_t** bitmap,
+                             int64_t* bitmap_len);
 void kura_plan_destroy(kura_plan_t p);
 
 #ifdef __cplusplus

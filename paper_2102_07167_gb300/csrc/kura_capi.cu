@@ -81,9 +81,9 @@ struct kura_ctx {
     std::vector<int32_t> h_col, h_label;
     std::vector<double> h_omega;        // user order
     Plan plan;                          // host plan (streams released after upload)
-    int64_t miss_total = 0, pres_total = 0, nnz = 0;
+    int64_t miss_total = 0, pres_total = 0, nnz = 0, stream_bytes = 0, bitmap_rows = 0;
     // device buffers
-    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, dptr, dcol, comm_off;
+    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off;
     DevMem omega, rscale, table, bsum, bsum_out, tot, T, counter, err_flags;
     DevMem y, Y, krk, fbuf, user, red, order_out;
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
@@ -160,6 +160,7 @@ DevGraph dev_graph(kura_ctx* h)
     g.groups = h->groups.as<Group>();
     g.tiles = h->tiles.as<Tile>();
     g.row_sub0 = h->row_sub0.as<int32_t>();
+    g.bitmap = h->bitmap.as<uint32_t>();
     g.dptr = h->dptr.as<int64_t>();
     g.dcol = h->dcol.as<int32_t>();
     g.comm_off = h->comm_off.as<int64_t>();
@@ -245,6 +246,18 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
     }
 }
 
+// Bytes of the correction data one right-hand side reads: the listed indices
+// (4 B each), the sub-row headers (16 B each) and the row bitmaps.
+int64_t plan_stream_bytes(const Plan& p)
+{
+    int64_t listed = 0;
+    for (const Group& G : p.groups) listed += G.len - 4 * int64_t(G.nsub);   // includes segment padding
+    int64_t bm = 0;
+    for (const Tile& t : p.tiles)
+        if (t.flags & TILE_BITMAP) bm += int64_t(t.r1 - t.r0) * t.nsw * 128;
+    return 4 * listed + 16 * int64_t(p.row_sub0.empty() ? 0 : p.row_sub0.back()) + bm;
+}
+
 kura_status build_device(kura_ctx* h, Plan&& plan)
 {
     cudaStream_t s = h->stream;
@@ -254,10 +267,13 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     h->max_wlen = p.max_wlen;
     h->miss_total = p.miss_total;
     h->pres_total = p.pres_total;
+    h->bitmap_rows = p.bitmap_rows;
+    h->stream_bytes = plan_stream_bytes(p);
     h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2));
     const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
     const int slot = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
-    h->row_smem = size_t(ROW_SLOTS) * size_t(slot) * 4 + size_t(std::max(p.max_wlen, 2)) * esize;
+    const int nslots = slots_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
+    h->row_smem = size_t(nslots) * size_t(slot) * 4 + size_t(std::max(p.max_wlen, 2)) * esize;
     KCHECK(h, (h->opts.precision == KURA_PREC_MIXED ? set_row_attrs<MODE_MIXED>(h->row_smem)
                                                     : set_row_attrs<MODE_FP64>(h->row_smem)),
            "setting the row kernel's shared-memory size");
@@ -268,6 +284,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     KCHECK(h, upload(h->groups, p.groups, s), "upload row groups");
     KCHECK(h, upload(h->tiles, p.tiles, s), "upload tiles");
     KCHECK(h, upload(h->row_sub0, p.row_sub0, s), "upload row_sub0");
+    KCHECK(h, upload(h->bitmap, p.bitmap, s), "upload row bitmaps");
     KCHECK(h, upload(h->dptr, p.dptr, s), "upload dptr");
     KCHECK(h, upload(h->dcol, p.dcol, s), "upload dcol");
     KCHECK(h, upload(h->comm_off, p.comm_off, s), "upload comm_off");
@@ -301,6 +318,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     KCHECK(h, cudaStreamSynchronize(s), "upload");
     // the correction stream now lives on the device
     std::vector<int32_t>().swap(p.gstream);
+    std::vector<uint32_t>().swap(p.bitmap);
     h->graphs.clear();
     h->last_graph = nullptr;
     return KURA_OK;
@@ -354,6 +372,7 @@ void kura_default_opts(kura_opts* o)
     o->scaling = KURA_SCALING_UNIFORM;
     o->tau = 0.5;
     o->keep_host_csr = 1;
+    o->bitmap_zmin = -1.0;
 }
 
 int32_t kura_version(void) { return 100; }
@@ -394,8 +413,10 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
     PlanInput in;
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.tile_max_rows = TILE_MAX_ROWS;
-    in.tile_max_sub = TILE_MAX_SUB;
+    in.tile_max_sub = tile_max_sub_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     in.slot_ints = slot_ints_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
+    in.entry_bytes = o.precision == KURA_PREC_MIXED ? 8 : 16;
+    in.bitmap_zmin = o.bitmap_zmin;
     Plan plan;
     std::string err;
     int rc = build_plan(in, plan, err);
@@ -453,8 +474,8 @@ kura_status kura_get_stats(kura_t h, kura_block_stats* s)
     s->tiles = h->n_tiles;
     s->max_window = h->max_wlen;
     const int64_t esize = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
-    // algorithmic bytes: 4 B per stored index + a 16 B header per row
-    s->stream_bytes = 4 * (h->miss_total + h->pres_total) + 16 * h->n;
+    // algorithmic bytes: 4 B per listed index, a 16 B header per sub-row, the row bitmaps
+    s->stream_bytes = h->stream_bytes;
     // row kernel per node: omega, y, krk (read+write), Y (write) or y (write), own entry
     s->node_bytes_row = (8 + 8 + 16 + 8 + esize) * h->n;
     // trig kernel per node: theta read, table write, community id
@@ -474,8 +495,10 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
         in.n_comm = h->n_comm; in.tau = tau;
         in.tile_max_rows = TILE_MAX_ROWS;
-        in.tile_max_sub = TILE_MAX_SUB;
+        in.tile_max_sub = tile_max_sub_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
         in.slot_ints = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
+        in.entry_bytes = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
+        in.bitmap_zmin = h->opts.bitmap_zmin;
         Plan plan;
         std::string err;
         int rc = build_plan(in, plan, err);
@@ -763,15 +786,24 @@ struct kura_plan_s {
 };
 
 kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
-                            int32_t n_comm, double tau, kura_plan_t* out)
+                            int32_t n_comm, const kura_opts* opts, kura_plan_t* out)
 {
     g_create_error.clear();
     if (!out) return KURA_EINVAL;
     *out = nullptr;
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
     std::unique_ptr<kura_plan_s> p(new (std::nothrow) kura_plan_s());
     if (!p) return KURA_ENOMEM;
+    const int mode = o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
     PlanInput in;
-    in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = tau;
+    in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
+    in.tile_max_rows = TILE_MAX_ROWS;
+    in.tile_max_sub = tile_max_sub_for(mode);
+    in.slot_ints = slot_ints_for(mode);
+    in.entry_bytes = mode == MODE_MIXED ? 8 : 16;
+    in.bitmap_zmin = o.bitmap_zmin;
     std::string err;
     int rc = build_plan(in, p->p, err);
     if (rc) { g_create_error = err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
@@ -798,7 +830,7 @@ kura_status kura_plan_stats(kura_plan_t pl, kura_block_stats* s)
     s->max_row_entries = p.max_row_entries;
     s->tiles = int64_t(p.tiles.size());
     s->max_window = p.max_wlen;
-    s->stream_bytes = 4 * (p.miss_total + p.pres_total) + 16 * p.n;
+    s->stream_bytes = plan_stream_bytes(p);
     s->node_bytes_row = (8 + 8 + 16 + 8 + 16) * p.n;
     s->node_bytes_trig = (8 + 16 + 4) * p.n;
     s->direct_edges = p.nnz_in - p.self_loops;
@@ -822,6 +854,15 @@ kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t
     *n_missing = p.miss_cnt[size_t(row)];
     *n_present = p.pres_cnt[size_t(row)];
     int64_t km = 0, kp = 0;
+    const Tile& T = p.tiles[size_t(p.row_tile[size_t(row)])];
+    if (T.flags & TILE_BITMAP) {
+        const uint32_t* bm = p.bitmap.data() + T.bm_off + (row - T.r0) * int64_t(T.nsw) * 32;
+        for (int64_t k = 0; k < T.wlen; k++)
+            if ((bm[(k >> 10) * 32 + (k & 31)] >> ((k >> 5) & 31)) & 1u) {
+                if (missing && km < cap) missing[km] = int32_t(T.wbeg + k);
+                km++;
+            }
+    }
     for (int32_t sg = p.row_sub0[size_t(row)]; sg < p.row_sub0[size_t(row) + 1]; sg++) {
         const int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
         for (int32_t q = 0; q < hdr[1]; q++, km++)
@@ -830,6 +871,7 @@ kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t
             if (present && kp < cap) present[kp] = p.gstream[size_t(p.sub_ppos[size_t(sg)] + q)];
     }
     if (km != *n_missing || kp != *n_present) return KURA_ESTATE;
+    if (missing) std::sort(missing, missing + std::min(km, cap));      // stored in bank-balanced order
     return KURA_OK;
 }
 
@@ -843,7 +885,8 @@ kura_status kura_plan_dense_blocks(kura_plan_t pl, int32_t I, int32_t* J, int32_
 }
 
 kura_status kura_plan_export(kura_plan_t pl, const int32_t** gstream, int64_t* gstream_len, const void** groups,
-                             int64_t* n_groups, const void** tiles, int64_t* n_tiles, const int32_t** row_sub0)
+                             int64_t* n_groups, const void** tiles, int64_t* n_tiles, const int32_t** row_sub0,
+                             const uint32_t** bitmap, int64_t* bitmap_len)
 {
     if (!pl) return KURA_EINVAL;
     const Plan& p = pl->p;
@@ -854,6 +897,8 @@ kura_status kura_plan_export(kura_plan_t pl, const int32_t** gstream, int64_t* g
     if (tiles) *tiles = p.tiles.data();
     if (n_tiles) *n_tiles = int64_t(p.tiles.size());
     if (row_sub0) *row_sub0 = p.row_sub0.data();
+    if (bitmap) *bitmap = p.bitmap.data();
+    if (bitmap_len) *bitmap_len = int64_t(p.bitmap.size());
     return KURA_OK;
 }
 

@@ -18,12 +18,15 @@ namespace kura {
 
 constexpr int ROW_CONSUMERS = 16;                       // consumer warps of the row kernel
 constexpr int ROW_THREADS = (ROW_CONSUMERS + 1) * 32;   // + one producer warp
-constexpr int ROW_SLOTS = 4;                            // shared-memory ring of row-group slots
 constexpr int TILE_MAX_ROWS = 512;      // rows per tile (the planner's bound)
-constexpr int TILE_MAX_SUB = 768;       // sub-rows per tile: stash capacity of the row kernel
+constexpr int BM_ROWS = 4;              // rows per warp in the bitmap pass
 constexpr int TRIG_THREADS = 256;
 // slot capacity (int32 units) per precision mode: keeps two CTAs resident per SM
+// Per precision mode (FP64 entries are 16 bytes, mixed 8): ring slots, slot
+// capacity (int32 units) and sub-rows per tile -- two CTAs stay resident per SM.
 __host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 4096; }
+__host__ __device__ constexpr int slots_for(int mode) { return mode == 0 ? 3 : 4; }
+__host__ __device__ constexpr int tile_max_sub_for(int mode) { return mode == 0 ? 512 : 768; }
 
 enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
 enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4 };
@@ -52,6 +55,7 @@ struct DevGraph {
     const Group* groups;
     const Tile* tiles;
     const int32_t* row_sub0;                // [n+1] first sub-row of each row
+    const uint32_t* bitmap;                 // row bitmaps of TILE_BITMAP tiles
     const int64_t* dptr;                    // [n_comm+1]
     const int32_t* dcol;
     const int64_t* comm_off;                // [n_comm+1]
@@ -270,10 +274,12 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     using E = typename EntryT<MODE>::T;
     using A = typename EntryT<MODE>::A;
     constexpr int SLOT = slot_ints_for(MODE);
+    constexpr int ROW_SLOTS = slots_for(MODE);
     constexpr uint64_t LIMIT_NS = 1000000000ull;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[ROW_SLOTS], empty_bar[ROW_SLOTS], win_bar;
-    __shared__ Acc2<MODE> stash[TILE_MAX_SUB];
+    __shared__ Acc2<MODE> stash[tile_max_sub_for(MODE)];
+    __shared__ Acc2<MODE> bm_stash[TILE_MAX_ROWS];
     __shared__ int abort_flag;
     __shared__ int issued[ROW_SLOTS];
 
@@ -322,6 +328,58 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         // ---------------- consumers
         bool ok = (t.wlen == 0) || mbar_wait_bounded(&win_bar, 0u, LIMIT_NS);
         if (!ok) { atomicOr(g.err, ERR_TIMEOUT); atomicExch(&abort_flag, 1); }
+        if (ok && (t.flags & TILE_BITMAP)) {
+            // ---- bitmap pass: BM_ROWS rows per warp; lane q reads window
+            // columns 32 j + q (consecutive across lanes: conflict-free) once
+            // for all BM_ROWS rows and adds the columns whose bit is set.
+            const int nrows_t = t.r1 - t.r0;
+            const uint32_t* bm = g.bitmap + t.bm_off;
+            for (int b = warp * BM_ROWS; b < nrows_t; b += ROW_CONSUMERS * BM_ROWS) {
+                A as[BM_ROWS], ac[BM_ROWS];
+                uint32_t nxt[BM_ROWS];
+#pragma unroll
+                for (int r = 0; r < BM_ROWS; r++) {
+                    as[r] = 0;
+                    ac[r] = 0;
+                    nxt[r] = (b + r < nrows_t) ? __ldcs(bm + size_t(b + r) * t.nsw * 32 + lane) : 0u;
+                }
+                for (int sw = 0; sw < t.nsw; sw++) {
+                    uint32_t cur[BM_ROWS];
+#pragma unroll
+                    for (int r = 0; r < BM_ROWS; r++) {
+                        cur[r] = nxt[r];
+                        nxt[r] = (sw + 1 < t.nsw && b + r < nrows_t)
+                                     ? __ldcs(bm + (size_t(b + r) * t.nsw + sw + 1) * 32 + lane) : 0u;
+                    }
+                    const int cb = sw * 1024;
+#pragma unroll 4
+                    for (int j = 0; j < 32; j++) {
+                        if (cb + 32 * j >= t.wlen) break;               // warp-uniform
+                        const int col = cb + 32 * j + lane;
+                        E e;
+                        if (col < t.wlen) e = win[col];
+                        else { e.x = 0; e.y = 0; }
+#pragma unroll
+                        for (int r = 0; r < BM_ROWS; r++) {
+                            if ((cur[r] >> j) & 1u) { as[r] += e.x; ac[r] += e.y; }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < BM_ROWS; r++) {
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) {
+                        as[r] += __shfl_xor_sync(0xffffffffu, as[r], o);
+                        ac[r] += __shfl_xor_sync(0xffffffffu, ac[r], o);
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < BM_ROWS; r++)
+                        if (b + r < nrows_t) bm_stash[b + r] = Acc2<MODE>{as[r], ac[r]};
+                }
+            }
+        }
         for (int gi = 0; gi < ngroups && ok; gi++) {
             const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
             if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
@@ -403,6 +461,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         for (int sidx = s0; sidx < s1; sidx++) {
             sa += stash[sidx].s;
             sc_ += stash[sidx].c;
+        }
+        if (t.flags & TILE_BITMAP) {     // missing entries given by the bitmap: subtracted
+            sa -= bm_stash[k].s;
+            sc_ -= bm_stash[k].c;
         }
         const E own = gather_entry<MODE>(win, t.wbeg, t.wlen, table, static_cast<int>(row));
         double acc_s, acc_c, si, ci;

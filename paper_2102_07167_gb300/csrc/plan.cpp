@@ -17,6 +17,51 @@ namespace {
 
 inline int64_t round_up4(int64_t x) { return (x + 3) & ~int64_t(3); }
 
+// Writes the n missing entries of one sub-row to out[0, n) in an order that
+// spreads the shared-memory banks of each warp-wide gather: the row kernel's
+// lane l gathers, in step t of iteration i, the entry at position
+// 128 i + 4 l + t, so the 32 positions {128 i + 4 l + t : l} are read by one
+// instruction.  Entries are bucketed by bank group ((column - wbeg) mod K,
+// K = 128 bytes / entry size) and dealt to each instruction one per bucket
+// per round, fullest buckets first, so every instruction touches every bank
+// group about equally often.  Any order gives
+// the same sum up to rounding; this one is deterministic.
+void balance_banks(const int32_t* in, int64_t n, int32_t wbeg, int K, int32_t* out)
+{
+    int32_t cnt[16] = {0}, start[17] = {0}, fill[16] = {0};
+    std::vector<int32_t> sorted(size_t(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; k++) cnt[((in[k] - wbeg) % K + K) % K]++;
+    for (int b = 0; b < K; b++) start[b + 1] = start[b] + cnt[b];
+    for (int64_t k = 0; k < n; k++) {
+        const int b = ((in[k] - wbeg) % K + K) % K;
+        sorted[size_t(start[b] + fill[b]++)] = in[k];
+    }
+    std::fill(fill, fill + 16, 0);
+    // per instruction: deal one entry per bucket per round, fullest buckets
+    // first, so the buckets drain evenly and the tail stays spread too
+    int order[16];
+    int64_t pos_list[32];
+    for (int64_t i = 0; 128 * i < n; i++)
+        for (int t = 0; t < 4; t++) {
+            int np_ = 0;
+            for (int l = 0; l < 32; l++)
+                if (128 * i + 4 * l + t < n) pos_list[np_++] = 128 * i + 4 * l + t;
+            int taken = 0;
+            while (taken < np_) {
+                for (int b = 0; b < K; b++) order[b] = b;
+                std::sort(order, order + K, [&](int a, int b) {
+                    const int ra = cnt[a] - fill[a], rb = cnt[b] - fill[b];
+                    return ra != rb ? ra > rb : a < b;
+                });
+                for (int k = 0; k < K && taken < np_; k++) {
+                    const int b = order[k];
+                    if (fill[b] == cnt[b]) break;
+                    out[pos_list[taken++]] = sorted[size_t(start[b] + fill[b]++)];
+                }
+            }
+        }
+}
+
 // Dense-block membership of column block J for row block I (sorted list).
 inline bool is_dense(const Plan& p, int32_t I, int32_t J)
 {
@@ -176,11 +221,52 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         }
         p.max_row_entries = mx;
 
+        // ---- staged window of every community: its own columns joined with
+        // its dense column blocks when that span fits the cap, else its own
+        // columns (aligned to an even start and length for 16-byte copies);
+        // bitmap encoding when every dense column is inside the window and
+        // the zero fraction over the dense columns exceeds bitmap_zmin.
+        std::vector<int32_t> c_wbeg(size_t(nc), 0), c_wlen(size_t(nc), 0), c_nsw(size_t(nc), 0);
+        std::vector<uint8_t> c_bitmap(size_t(nc), 0);
+        for (int32_t I = 0; I < nc; I++) {
+            int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
+            if (rb == re) continue;
+            int64_t lo = rb, hi = re;
+            for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
+                lo = std::min(lo, p.comm_off[size_t(p.dcol[size_t(k)])]);
+                hi = std::max(hi, p.comm_off[size_t(p.dcol[size_t(k)]) + 1]);
+            }
+            bool covers = true;
+            if (hi - lo > in.window_cap) { lo = rb; hi = re; covers = false; }
+            int64_t wb = lo & ~int64_t(1), we = (hi + 1) & ~int64_t(1);
+            int32_t wbeg = int32_t(wb), wlen = int32_t(we - wb);
+            if (wlen > in.window_cap + 2) { wbeg = 0; wlen = 0; covers = false; }
+            c_wbeg[size_t(I)] = wbeg;
+            c_wlen[size_t(I)] = wlen;
+            p.max_wlen = std::max(p.max_wlen, wlen);
+            if (covers && wlen > 0 && in.bitmap_zmin >= 0 && p.dptr[I + 1] > p.dptr[I]) {
+                double zeros = 0, entries = 0;
+                for (int64_t v = rb; v < re; v++) zeros += p.miss_cnt[size_t(v)];
+                entries = double(re - rb) * double(dense_span[size_t(I)]);
+                const int32_t nsw = int32_t((wlen + 1023) / 1024);
+                if (entries > 0 && zeros / entries > in.bitmap_zmin && nsw <= BITMAP_MAX_SW) {
+                    c_bitmap[size_t(I)] = 1;
+                    c_nsw[size_t(I)] = nsw;
+                    p.bitmap_rows += re - rb;
+                }
+            }
+        }
+        // missing entries given as index lists (not in a bitmap)
+        auto listed_miss = [&](int64_t v) -> int64_t {
+            return c_bitmap[size_t(p.node_comm[size_t(v)])] ? 0 : p.miss_cnt[size_t(v)];
+        };
+
         // ---- sub-rows: each row is cut into ceil((nm + np) / SUBROW_MAX)
-        // pieces (at least one) of consecutive entries of [missing | present].
+        // pieces (at least one) of consecutive entries of [missing | present]
+        // (nm = listed missing entries).
         p.row_sub0.assign(size_t(n) + 1, 0);
         for (int64_t v = 0; v < n; v++) {
-            const int64_t e = int64_t(p.miss_cnt[size_t(v)]) + p.pres_cnt[size_t(v)];
+            const int64_t e = listed_miss(v) + p.pres_cnt[size_t(v)];
             p.row_sub0[size_t(v) + 1] = p.row_sub0[size_t(v)] + int32_t(std::max<int64_t>(1, (e + SUBROW_MAX - 1) / SUBROW_MAX));
         }
         const int64_t n_sub = p.row_sub0[size_t(n)];
@@ -192,7 +278,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             }
         // missing / present parts of sub-row (row v, piece k)
         auto sub_parts = [&](int64_t v, int64_t k, int64_t& mb, int64_t& mn, int64_t& pb, int64_t& pn) {
-            const int64_t nm = p.miss_cnt[size_t(v)], np_ = p.pres_cnt[size_t(v)];
+            const int64_t nm = listed_miss(v), np_ = p.pres_cnt[size_t(v)];
             const int64_t b = k * SUBROW_MAX, e = std::min<int64_t>(b + SUBROW_MAX, nm + np_);
             mb = std::min(b, nm);
             mn = std::min(e, nm) - mb;
@@ -220,30 +306,30 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         sub_mpos.resize(size_t(n_sub));
         sub_ppos.resize(size_t(n_sub));
         int64_t goff = 0;
+        int64_t bm_words = 0;
+        p.row_tile.resize(size_t(n));
         for (int32_t I = 0; I < nc; I++) {
             int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
             if (rb == re) continue;
-            int64_t lo = rb, hi = re;
-            for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
-                lo = std::min(lo, p.comm_off[size_t(p.dcol[size_t(k)])]);
-                hi = std::max(hi, p.comm_off[size_t(p.dcol[size_t(k)]) + 1]);
-            }
-            if (hi - lo > in.window_cap) { lo = rb; hi = re; }
-            int64_t wb = lo & ~int64_t(1), we = (hi + 1) & ~int64_t(1);
-            int32_t wbeg = int32_t(wb), wlen = int32_t(we - wb);
-            if (wlen > in.window_cap + 2) { wbeg = 0; wlen = 0; }
-            p.max_wlen = std::max(p.max_wlen, wlen);
+            const int32_t wbeg = c_wbeg[size_t(I)], wlen = c_wlen[size_t(I)];
             int64_t r = rb;
             while (r < re) {
                 int64_t w = 0, s = r;
                 while (r < re && (r == s || (w < target && r - s < in.tile_max_rows &&
                                              p.row_sub0[size_t(r) + 1] - p.row_sub0[size_t(s)] <= in.tile_max_sub))) {
-                    w += p.miss_cnt[size_t(r)] + p.pres_cnt[size_t(r)] + 8;
+                    w += (c_bitmap[size_t(I)] ? 8 * c_nsw[size_t(I)] : p.miss_cnt[size_t(r)]) + p.pres_cnt[size_t(r)] + 8;
                     r++;
                 }
                 Tile t{};
                 t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
                 t.sub0 = p.row_sub0[size_t(s)];
+                if (c_bitmap[size_t(I)]) {
+                    t.flags |= TILE_BITMAP;
+                    t.nsw = c_nsw[size_t(I)];
+                    t.bm_off = bm_words;
+                    bm_words += (r - s) * int64_t(t.nsw) * 32;
+                }
+                for (int64_t q = s; q < r; q++) p.row_tile[size_t(q)] = int32_t(p.tiles.size());
                 t.g0 = int32_t(p.groups.size());
                 // groups over the tile's sub-rows [row_sub0[s], row_sub0[r])
                 int64_t v = s, k = 0;             // current sub-row = (row v, piece k)
@@ -285,6 +371,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             }
         }
         p.gstream.assign(size_t(std::max<int64_t>(goff, 4)), 0);
+        p.bitmap.assign(size_t(std::max<int64_t>(bm_words, 4)), 0u);
 
         // ---- fill: mark dense-block neighbours in a bitmap, scan the dense
         // column ranges for zeros (skipping the row's own diagonal entry),
@@ -332,6 +419,16 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t w = p.inv_perm[size_t(c)];
                     bits[size_t(w) >> 6] = 0;
                 }
+                // bitmap rows: the missing entries become bits over the window
+                if (c_bitmap[size_t(I)]) {
+                    const Tile& T = p.tiles[size_t(p.row_tile[size_t(v)])];
+                    uint32_t* bm = p.bitmap.data() + T.bm_off + (v - T.r0) * int64_t(T.nsw) * 32;
+                    for (int32_t c : ms) {
+                        const int64_t k = int64_t(c) - T.wbeg;
+                        bm[(k >> 10) * 32 + (k & 31)] |= uint32_t(1) << ((k >> 5) & 31);
+                    }
+                    ms.clear();
+                }
                 // sub-rows of row v
                 const int32_t s0 = p.row_sub0[size_t(v)], s1 = p.row_sub0[size_t(v) + 1];
                 for (int32_t sg = s0; sg < s1; sg++) {
@@ -340,7 +437,8 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
                     int32_t* mdst = p.gstream.data() + sub_mpos[size_t(sg)];
                     int32_t* pdst = p.gstream.data() + sub_ppos[size_t(sg)];
-                    for (int64_t q = 0; q < mn; q++) mdst[q] = ms[size_t(mb + q)];
+                    balance_banks(ms.data() + mb, mn, p.tiles[size_t(p.row_tile[size_t(v)])].wbeg,
+                                  in.entry_bytes >= 16 ? 8 : 16, mdst);
                     for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = int32_t(n);
                     for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
                     for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = int32_t(n);

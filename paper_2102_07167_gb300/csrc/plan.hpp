@@ -15,13 +15,21 @@
 
 namespace kura {
 
-struct Tile {              // 32 bytes, read by the row kernel
+struct Tile {              // 48 bytes, read by the row kernel
     int32_t r0, r1;        // rows [r0, r1) in permuted order, all in one community
     int32_t comm;          // community of the rows
     int32_t wbeg, wlen;    // staged table window [wbeg, wbeg + wlen) (wlen = 0: none)
     int32_t g0, g1;        // row groups [g0, g1) of the tile
     int32_t sub0;          // global index of the tile's first sub-row
+    int64_t bm_off;        // TILE_BITMAP: first word of the tile's row bitmaps
+    int32_t nsw;           // TILE_BITMAP: 1024-column super-words per row
+    int32_t flags;
 };
+// The tile's missing entries are given as bitmaps over its window instead of
+// index lists: per row nsw super-words of 32 words, bit j of word q of
+// super-word w set iff window column w * 1024 + 32 j + q is a missing entry.
+constexpr int32_t TILE_BITMAP = 1;
+constexpr int32_t BITMAP_MAX_SW = 5;
 
 // Rows are cut into sub-rows of at most SUBROW_MAX entries (missing entries
 // first, then present entries, in the row's order), so that one warp holds a
@@ -56,6 +64,10 @@ struct PlanInput {
     int32_t tile_max_rows = 512;
     int32_t tile_max_sub = 768;         // sub-rows per tile (stash capacity of the row kernel)
     int32_t slot_ints = 4096;           // capacity of one row-group slot (int32 units)
+    // bitmap encoding for a community's dense blocks when its zero fraction
+    // there exceeds this (and the window holds every dense column); < 0: never
+    double bitmap_zmin = -1.0;
+    int32_t entry_bytes = 8;            // (sin, cos) table entry size of the row kernel: 8 or 16
 };
 
 struct Plan {
@@ -78,6 +90,9 @@ struct Plan {
     std::vector<Tile> tiles;
     std::vector<int64_t> sub_hdr;       // [n_sub] position of each sub-row's header in gstream
     std::vector<int64_t> sub_mpos, sub_ppos;   // [n_sub] positions of its missing / present segments
+    std::vector<uint32_t> bitmap;              // row bitmaps of TILE_BITMAP tiles
+    std::vector<int32_t> row_tile;             // [n] tile of each row
+    int64_t bitmap_rows = 0;
     int32_t max_wlen = 0;
     // statistics
     int64_t dense_blocks = 0, sparse_blocks = 0, nonempty_blocks = 0;

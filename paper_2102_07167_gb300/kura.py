@@ -42,7 +42,8 @@ class KuraError(RuntimeError):
 
 class KuraOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scaling", C.c_int32), ("tau", C.c_double),
-                ("keep_host_csr", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("keep_host_csr", C.c_int32), ("reserved0", C.c_int32), ("bitmap_zmin", C.c_double),
+                ("reserved", C.c_int32 * 4)]
 
 
 class KuraBlockStats(C.Structure):
@@ -95,13 +96,13 @@ def load() -> C.CDLL:
             "kura_last_error": (C.c_char_p, [P]),
             "kura_destroy": (None, [P]),
             "kura_order_params_static": (S, [I64, P, P, I32, P, P]),
-            "kura_plan_build": (S, [I64, P, P, P, I32, D, C.POINTER(P)]),
+            "kura_plan_build": (S, [I64, P, P, P, I32, C.POINTER(KuraOpts), C.POINTER(P)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
             "kura_plan_perm": (S, [P, P, P]),
             "kura_plan_row": (S, [P, I64, P, C.POINTER(I64), P, C.POINTER(I64), I64]),
             "kura_plan_dense_blocks": (S, [P, I32, P, I32, C.POINTER(I32)]),
             "kura_plan_export": (S, [P, C.POINTER(P), C.POINTER(I64), C.POINTER(P), C.POINTER(I64), C.POINTER(P),
-                                     C.POINTER(I64), C.POINTER(P)]),
+                                     C.POINTER(I64), C.POINTER(P), C.POINTER(P), C.POINTER(I64)]),
             "kura_plan_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -262,13 +263,15 @@ def kura_destroy(h):
     load().kura_destroy(h)
 
 
-def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5):
+def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5, precision=PREC_MIXED, bitmap_zmin=-1.0):
     p = C.c_void_p()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     label = np.ascontiguousarray(label, dtype=np.int32)
+    o = kura_default_opts()
+    o.tau, o.precision, o.bitmap_zmin = float(tau), int(precision), float(bitmap_zmin)
     rc = load().kura_plan_build(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
-                                label.ctypes.data, int(n_comm), float(tau), C.byref(p))
+                                label.ctypes.data, int(n_comm), C.byref(o), C.byref(p))
     _check(rc, None)
     return p
 
@@ -305,15 +308,17 @@ def kura_plan_dense_blocks(p, I, cap=1 << 16):
 GROUP_DTYPE = np.dtype([("off", np.int64), ("len", np.int32), ("sub0", np.int32), ("nsub", np.int32),
                         ("pad", np.int32)])
 TILE_DTYPE = np.dtype([("r0", np.int32), ("r1", np.int32), ("comm", np.int32), ("wbeg", np.int32),
-                       ("wlen", np.int32), ("g0", np.int32), ("g1", np.int32), ("sub0", np.int32)])
+                       ("wlen", np.int32), ("g0", np.int32), ("g1", np.int32), ("sub0", np.int32),
+                       ("bm_off", np.int64), ("nsw", np.int32), ("flags", np.int32)])
+TILE_BITMAP = 1
 
 
 def kura_plan_export(p, n):
-    """Copies of the packed stream, groups, tiles and row_sub0 of a plan."""
-    gs, gl, gr, ng, ti, nt, rs = (C.c_void_p(), C.c_int64(), C.c_void_p(), C.c_int64(), C.c_void_p(),
-                                  C.c_int64(), C.c_void_p())
+    """Copies of the packed stream, groups, tiles, row_sub0 and row bitmaps of a plan."""
+    gs, gl, gr, ng, ti, nt, rs, bm, bl = (C.c_void_p(), C.c_int64(), C.c_void_p(), C.c_int64(), C.c_void_p(),
+                                          C.c_int64(), C.c_void_p(), C.c_void_p(), C.c_int64())
     _check(load().kura_plan_export(p, C.byref(gs), C.byref(gl), C.byref(gr), C.byref(ng), C.byref(ti),
-                                   C.byref(nt), C.byref(rs)))
+                                   C.byref(nt), C.byref(rs), C.byref(bm), C.byref(bl)))
 
     def view(ptr, count, dtype):
         if count == 0:
@@ -321,7 +326,7 @@ def kura_plan_export(p, n):
         buf = (C.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr.value)
         return np.frombuffer(buf, dtype=dtype).copy()
     return (view(gs, gl.value, np.int32), view(gr, ng.value, GROUP_DTYPE), view(ti, nt.value, TILE_DTYPE),
-            view(rs, n + 1, np.int32))
+            view(rs, n + 1, np.int32), view(bm, bl.value, np.uint32))
 
 
 def kura_plan_destroy(p):
@@ -333,11 +338,13 @@ class Kuramoto:
     """A libkura handle: the graph, omega and K resident on the GPU."""
 
     def __init__(self, row_ptr, col, label, n_comm, omega, K, precision=PREC_FP64,
-                 scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None):
+                 scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None, bitmap_zmin=None):
         self.n = int(np.asarray(row_ptr).shape[0] - 1)
         self.n_comm = int(n_comm)
         o = kura_default_opts()
         o.precision, o.scaling, o.tau, o.keep_host_csr = int(precision), int(scaling), float(tau), int(keep_host_csr)
+        if bitmap_zmin is not None:
+            o.bitmap_zmin = float(bitmap_zmin)
         self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
 
     def rhs(self, theta, out):

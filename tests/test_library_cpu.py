@@ -54,9 +54,9 @@ def test_invalid_input_is_rejected(bad):
     assert kura.kura_last_error(None)
 
 
-def _reconstruct_and_check(g, tau):
+def _reconstruct_and_check(g, tau, bitmap_zmin=-1.0, precision=1):
     n, nc = g.n, g.n_comm
-    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau)
+    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin)
     try:
         perm, off = kura.kura_plan_perm(p, n, nc)
         st = kura.kura_plan_stats(p)
@@ -125,11 +125,13 @@ def test_plan_reconstructs_random_graphs(seed):
         np.fill_diagonal(A, 1)           # self-loops must be dropped
     g = G.from_dense(A, lab, nc)
     for tau in (0.0, 0.25, 0.5, 0.75, 1.0):
-        _reconstruct_and_check(g, tau)
+        for zmin, prec in ((-1.0, 1), (0.0, 1), (-1.0, 0)):
+            _reconstruct_and_check(g, tau, zmin, prec)
 
 
 def test_plan_reconstructs_sbm_and_extremes():
     g = G.sbm(4, [40, 25, 60, 13], [0.9, 0.6, 0.95, 0.3], 0.04)
+    _reconstruct_and_check(g, 0.5, 0.0)
     st = _reconstruct_and_check(g, 0.5)
     assert st["dense_blocks"] == 3          # the p_in = 0.3 community stays sparse
     st0 = _reconstruct_and_check(g, 0.0)
@@ -163,18 +165,19 @@ def test_plan_splits_long_rows_into_subrows(tau, p_one):
     np.fill_diagonal(A, 0)
     g = G.from_dense(A)
     st = _reconstruct_and_check(g, tau)
+    _reconstruct_and_check(g, tau, 0.0)
     assert st["max_row_entries"] > 508
 
 
-def _emulate_row_kernel(g, tau, omega, theta, K):
+def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
     """Consumes the packed stream exactly as the row kernel does (groups -> sub-row headers -> padded int4
     segments -> window-or-table gathers, padding resolving to zero entries), in float64, and returns f in
     user order."""
     n, nc = g.n, g.n_comm
-    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau)
+    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin)
     try:
         perm, off = kura.kura_plan_perm(p, n, nc)
-        gstream, groups, tiles, row_sub0 = kura.kura_plan_export(p, n)
+        gstream, groups, tiles, row_sub0, bitmap = kura.kura_plan_export(p, n)
         dense = [kura.kura_plan_dense_blocks(p, I) for I in range(nc)]
     finally:
         kura.kura_plan_destroy(p)
@@ -205,6 +208,15 @@ def _emulate_row_kernel(g, tau, omega, theta, K):
         for r in range(t["r0"], t["r1"]):
             a_s = sum(stash[s][0] for s in range(row_sub0[r], row_sub0[r + 1]))
             a_c = sum(stash[s][1] for s in range(row_sub0[r], row_sub0[r + 1]))
+            if t["flags"] & kura.TILE_BITMAP:
+                # lane-major bitmap: bit j of word q of super-word w <-> window column 1024 w + 32 j + q
+                nsw = int(t["nsw"])
+                words = bitmap[int(t["bm_off"]) + (r - t["r0"]) * nsw * 32: int(t["bm_off"]) + (r - t["r0"] + 1) * nsw * 32]
+                k = np.arange(wlen)
+                bits = (words[(k >> 10) * 32 + (k & 31)] >> ((k >> 5) & 31).astype(np.uint32)) & 1
+                cols = wbeg + k[bits == 1]
+                a_s -= s_tab[cols].sum()
+                a_c -= c_tab[cols].sum()
             I = t["comm"]
             Ts, Tc = S[dense[I]].sum(), C[dense[I]].sum()
             f[r] = omega[perm[r]] + (K / n) * (c_tab[r] * (Ts + a_s) - s_tab[r] * (Tc + a_c))
@@ -213,8 +225,9 @@ def _emulate_row_kernel(g, tau, omega, theta, K):
     return out
 
 
+@pytest.mark.parametrize("zmin,prec", [(-1.0, 1), (0.05, 1), (-1.0, 0)])
 @pytest.mark.parametrize("case", ["sbm", "long_rows_sparse", "long_rows_dense", "big_community"])
-def test_packed_stream_emulation_matches_oracle(case):
+def test_packed_stream_emulation_matches_oracle(case, zmin, prec):
     """The packed stream (headers, padding, windows, sub-rows) read the way the row kernel reads it gives
     the right-hand side of the FP64 oracle."""
     import oracle
@@ -230,6 +243,39 @@ def test_packed_stream_emulation_matches_oracle(case):
         g = G.from_dense(A)
         tau = 0.0 if case == "long_rows_sparse" else 1.0
     omega, theta = rng.normal(size=g.n), rng.uniform(-30, 30, g.n)
-    f = _emulate_row_kernel(g, tau, omega, theta, 2.0)
+    f = _emulate_row_kernel(g, tau, omega, theta, 2.0, zmin, prec)
     ref = oracle.rhs_csr(g.row_ptr, g.col, omega, theta, 2.0)
     np.testing.assert_allclose(f, ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_missing_entries_are_bank_balanced(prec):
+    """Each warp-wide gather of missing entries (positions 128 i + 4 l + t, l = 0..31) touches every shared
+    memory bank group about equally: on average at most 2.5 (of 32) entries per group of 128 / entry-size
+    bytes (the ideal is 32 / groups = 2 or 4); only a row's tail can be lopsided."""
+    g = G.sbm(2, [900, 700, 1200], [0.6, 0.7, 0.8], 0.01)
+    p = kura.kura_plan_build(g.n, g.row_ptr, g.col, g.label, g.n_comm, 0.5, prec)
+    try:
+        gstream, groups, tiles, row_sub0, _ = kura.kura_plan_export(p, g.n)
+    finally:
+        kura.kura_plan_destroy(p)
+    K = 16 if prec == 1 else 8
+    maxima = []
+    for t in tiles:
+        for gi in range(t["g0"], t["g1"]):
+            G_ = groups[gi]
+            base = int(G_["off"])
+            for j in range(G_["nsub"]):
+                mrel, nm = gstream[base + 4 * j], gstream[base + 4 * j + 1]
+                seg = gstream[base + mrel: base + mrel + nm]
+                for i in range(0, (nm + 127) // 128):
+                    for tt in range(4):
+                        pos = [128 * i + 4 * l + tt for l in range(32) if 128 * i + 4 * l + tt < nm]
+                        if len(pos) < 32:
+                            continue
+                        keys = (seg[pos] - t["wbeg"]) % K
+                        maxima.append(np.bincount(keys, minlength=K).max())
+    ideal = 32 // K
+    maxima = np.array(maxima)
+    assert maxima.size > 100 and maxima.mean() <= ideal + 0.5 and np.percentile(maxima, 99) <= ideal + 3, \
+        (maxima.size, maxima.mean(), np.percentile(maxima, 99))
