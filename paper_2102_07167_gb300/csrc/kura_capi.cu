@@ -273,7 +273,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
     const int slot = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     const int nslots = slots_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
-    h->row_smem = size_t(nslots) * size_t(slot) * 4 + size_t(std::max(p.max_wlen, 2)) * esize;
+    h->row_smem = size_t(nslots) * size_t(slot) * 4 + 16 + size_t(std::max(p.max_wlen, 2)) * esize;
     KCHECK(h, (h->opts.precision == KURA_PREC_MIXED ? set_row_attrs<MODE_MIXED>(h->row_smem)
                                                     : set_row_attrs<MODE_FP64>(h->row_smem)),
            "setting the row kernel's shared-memory size");

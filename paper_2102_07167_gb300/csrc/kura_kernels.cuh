@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     __shared__ int issued[ROW_SLOTS];
 
     int32_t* ring = reinterpret_cast<int32_t*>(smem_raw);
-    E* win = reinterpret_cast<E*>(smem_raw + size_t(ROW_SLOTS) * SLOT * sizeof(int32_t));
+    // window at win[0, wlen), preceded by 16 bytes holding a zero entry at win[-1]
+    E* win = reinterpret_cast<E*>(smem_raw + size_t(ROW_SLOTS) * SLOT * sizeof(int32_t) + 16);
     const Tile t = g.tiles[blockIdx.x];
     const E* table = reinterpret_cast<const E*>(g.table);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -293,6 +294,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
 
     if (tid == 0) {
         abort_flag = 0;
+        E z;
+        z.x = 0;
+        z.y = 0;
+        win[-1] = z;             // target of the padding of in-window missing segments
         for (int sl = 0; sl < ROW_SLOTS; sl++) {
             mbar_init(&full_bar[sl], 1);
             mbar_init(&empty_bar[sl], ROW_CONSUMERS);
@@ -398,35 +403,37 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 const int4 hdr = reinterpret_cast<const int4*>(slot)[j];
                 m4 = (hdr.y + 3) >> 2;
                 tot4 = m4 + ((hdr.w + 3) >> 2);
-                const int4* mseg = reinterpret_cast<const int4*>(slot + hdr.x);
-                const int4* pseg = reinterpret_cast<const int4*>(slot + hdr.z);
+                const int4* seg = reinterpret_cast<const int4*>(slot + hdr.x);    // [missing | present]
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     const int q = lane + 32 * i;
-                    if (q < m4) v[i] = mseg[q];
-                    else if (q < tot4) v[i] = pseg[q - m4];
-                    else v[i] = make_int4(zidx, zidx, zidx, zidx);
+                    v[i] = (q < tot4) ? seg[q] : make_int4(zidx, zidx, zidx, zidx);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_bar[sl]);      // indices are in registers: release the slot
             if (have) {
                 A as = 0, ac = 0;
+                const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     if (32 * i < tot4) {                     // warp-uniform
-                        const bool neg = (lane + 32 * i) < m4;
                         const int idx[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
                         E e[4];
+                        if (lane + 32 * i < m4) {            // missing entries: subtracted
 #pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const unsigned u = static_cast<unsigned>(idx[q] - t.wbeg);
-                            e[q] = (u < static_cast<unsigned>(t.wlen)) ? win[u] : __ldg(table + idx[q]);
-                        }
+                            for (int q = 0; q < 4; q++)
+                                e[q] = miss_fast ? win[idx[q] - t.wbeg]
+                                                 : gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx[q]);
 #pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            if (neg) { as -= e[q].x; ac -= e[q].y; }
-                            else     { as += e[q].x; ac += e[q].y; }
+                            for (int q = 0; q < 4; q++) { as -= e[q].x; ac -= e[q].y; }
+                        } else {                             // present entries (and tail padding): added
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+                                e[q] = pres_check ? gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx[q])
+                                                  : __ldg(table + idx[q]);
+#pragma unroll
+                            for (int q = 0; q < 4; q++) { as += e[q].x; ac += e[q].y; }
                         }
                     }
                 }

@@ -227,7 +227,8 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         // bitmap encoding when every dense column is inside the window and
         // the zero fraction over the dense columns exceeds bitmap_zmin.
         std::vector<int32_t> c_wbeg(size_t(nc), 0), c_wlen(size_t(nc), 0), c_nsw(size_t(nc), 0);
-        std::vector<uint8_t> c_bitmap(size_t(nc), 0);
+        std::vector<uint8_t> c_bitmap(size_t(nc), 0), c_inwin(size_t(nc), 0);
+        std::vector<int32_t> c_mpad(static_cast<size_t>(nc), static_cast<int32_t>(n));
         for (int32_t I = 0; I < nc; I++) {
             int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
             if (rb == re) continue;
@@ -243,6 +244,10 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             if (wlen > in.window_cap + 2) { wbeg = 0; wlen = 0; covers = false; }
             c_wbeg[size_t(I)] = wbeg;
             c_wlen[size_t(I)] = wlen;
+            if (covers && wlen > 0) {
+                c_inwin[size_t(I)] = 1;
+                c_mpad[size_t(I)] = wbeg - 1;
+            }
             p.max_wlen = std::max(p.max_wlen, wlen);
             if (covers && wlen > 0 && in.bitmap_zmin >= 0 && p.dptr[I + 1] > p.dptr[I]) {
                 double zeros = 0, entries = 0;
@@ -323,6 +328,9 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 Tile t{};
                 t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
                 t.sub0 = p.row_sub0[size_t(s)];
+                if (c_inwin[size_t(I)]) t.flags |= TILE_MISS_IN_WINDOW;
+                if (!std::binary_search(p.dcol.begin() + p.dptr[I], p.dcol.begin() + p.dptr[I + 1], I))
+                    t.flags |= TILE_PRES_CHECK;
                 if (c_bitmap[size_t(I)]) {
                     t.flags |= TILE_BITMAP;
                     t.nsw = c_nsw[size_t(I)];
@@ -349,18 +357,14 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     G.nsub = int32_t(members.size());
                     G.len = int32_t(size);
                     int64_t pos = goff + 4 * G.nsub;
-                    for (size_t m = 0; m < members.size(); m++) {            // missing segments
+                    for (size_t m = 0; m < members.size(); m++) {            // [missing | present] per sub-row
                         int64_t mb, mn, pb, pn;
                         sub_parts(members[m].first, members[m].second, mb, mn, pb, pn);
                         const int64_t sg = G.sub0 + int64_t(m);
                         p.sub_hdr[size_t(sg)] = goff + 4 * int64_t(m);
                         sub_mpos[size_t(sg)] = pos;
                         pos += round_up4(mn);
-                    }
-                    for (size_t m = 0; m < members.size(); m++) {            // present segments
-                        int64_t mb, mn, pb, pn;
-                        sub_parts(members[m].first, members[m].second, mb, mn, pb, pn);
-                        sub_ppos[size_t(G.sub0 + int64_t(m))] = pos;
+                        sub_ppos[size_t(sg)] = pos;
                         pos += round_up4(pn);
                     }
                     goff += size;
@@ -439,7 +443,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t* pdst = p.gstream.data() + sub_ppos[size_t(sg)];
                     balance_banks(ms.data() + mb, mn, p.tiles[size_t(p.row_tile[size_t(v)])].wbeg,
                                   in.entry_bytes >= 16 ? 8 : 16, mdst);
-                    for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = int32_t(n);
+                    for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = c_mpad[size_t(I)];
                     for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
                     for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = int32_t(n);
                     hdr[1] = int32_t(mn);

@@ -29,6 +29,14 @@ struct Tile {              // 48 bytes, read by the row kernel
 // index lists: per row nsw super-words of 32 words, bit j of word q of
 // super-word w set iff window column w * 1024 + 32 j + q is a missing entry.
 constexpr int32_t TILE_BITMAP = 1;
+// every dense column of the tile lies in its window: missing entries are read
+// from the window without a range check, and missing-segment padding is
+// wbeg - 1, which the row kernel maps to a zero entry kept just before the
+// staged window (other tiles pad with n and range-check every gather)
+constexpr int32_t TILE_MISS_IN_WINDOW = 2;
+// the diagonal block is sparse: present entries may lie in the window and are
+// range-checked (otherwise they are gathered from the global table directly)
+constexpr int32_t TILE_PRES_CHECK = 4;
 constexpr int32_t BITMAP_MAX_SW = 5;
 
 // Rows are cut into sub-rows of at most SUBROW_MAX entries (missing entries
@@ -40,9 +48,11 @@ constexpr int32_t SUBROW_MAX = 508;
 // them) whose packed stream fits one shared-memory slot of the row kernel.
 // Packed layout at gstream[off, off + len) (int32 units, 16-byte aligned):
 //   nsub x int4 header {miss_rel, n_miss, pres_rel, n_pres} (offsets relative
-//   to off), then the missing entries of every sub-row, then the present
-//   entries of every sub-row, each segment padded to a multiple of 4 with n,
-//   the index of the table's zero (sin, cos) entry.
+//   to off), then per sub-row its missing entries followed directly by its
+//   present entries (pres_rel = miss_rel + round_up4(n_miss)), each part
+//   padded to a multiple of 4 with the index of a zero (sin, cos) entry:
+//   n for present parts; for missing parts wbeg - 1 in TILE_MISS_IN_WINDOW
+//   tiles, else n.
 constexpr int32_t GROUP_MAX_SUB = 16;
 struct Group {
     int64_t off;

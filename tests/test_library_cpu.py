@@ -190,10 +190,14 @@ def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
     for t in tiles:
         wbeg, wlen = int(t["wbeg"]), int(t["wlen"])
 
-        def gather(idx):
-            # window [wbeg, wbeg + wlen) holds copies of the table entries; padding is n (zero entry)
-            assert np.all((idx >= 0) & (idx <= n))
-            return s_tab[idx], c_tab[idx]
+        def gather(idx, missing):
+            # the window [wbeg, wbeg + wlen) holds copies of the table entries; padding is n (the table's
+            # zero entry) or, for missing parts of tiles whose dense columns all lie in the window, wbeg - 1
+            # (the zero entry kept just before the staged window)
+            zero = idx == wbeg - 1 if (missing and t["flags"] & 2) else np.zeros(idx.shape, bool)
+            assert np.all(((idx >= 0) & (idx <= n)) | zero)
+            safe = np.where(zero, n, idx)
+            return s_tab[safe], c_tab[safe]
         stash = {}
         for gi in range(t["g0"], t["g1"]):
             G_ = groups[gi]
@@ -202,8 +206,8 @@ def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
                 mrel, nm, prel, npr = gstream[base + 4 * j: base + 4 * j + 4]
                 m = gstream[base + mrel: base + mrel + 4 * ((nm + 3) // 4)]
                 q = gstream[base + prel: base + prel + 4 * ((npr + 3) // 4)]
-                ms, mc = gather(m)
-                ps, pc = gather(q)
+                ms, mc = gather(m, True)
+                ps, pc = gather(q, False)
                 stash[int(G_["sub0"]) + j] = (ps.sum() - ms.sum(), pc.sum() - mc.sum())
         for r in range(t["r0"], t["r1"]):
             a_s = sum(stash[s][0] for s in range(row_sub0[r], row_sub0[r + 1]))
