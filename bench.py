@@ -110,6 +110,20 @@ def _dist():
     return world, rank, local
 
 
+def aggregate_replicas(el_ms_local: float, n: int, steps: int, dist=None, device=None):
+    """Replica runs: every rank integrates its own copy of the workload.  Returns (value, max elapsed ms):
+    value = total oscillator-steps of all ranks / the slowest rank's time."""
+    import torch
+    world = 1
+    el = float(el_ms_local)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([el], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    return world * n * steps / (el / 1e3), el
+
+
 def _workload(name: str):
     from paper_2102_07167_gb300 import gen as G
     if name == "sbm-2p20":
@@ -216,12 +230,8 @@ def run_ours(args):
         barrier()
     el_ms = ev0.elapsed_time(ev1)
     launch_ms = k.kernel_times()
-    if dist is not None:
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
+    value, el_ms = aggregate_replicas(el_ms, n, args.steps, dist, dev)
     ms_step = el_ms / args.steps
-    value = world * n * args.steps / (el_ms / 1e3)
     gpu_launches = 8 * args.steps + 2
 
     # ---- roofline of the dominant kernel (row kernel): algorithmic bytes / mean launch time

@@ -61,10 +61,12 @@ def _load():
                                        C.c_void_p, C.c_void_p]
         L.orc_potential_csr.argtypes = [I64, _i64, _i32, _d, _d, D, C.c_int, C.POINTER(D)]
         L.orc_mean_deviation.argtypes = [I64, _d, _d, _d, D, C.POINTER(D)]
+        L.orc_adjoint_rk4_csr.argtypes = [I64, _i64, _i32, _d, D, C.c_int, _d, D, I64, C.c_int, C.c_void_p,
+                                          C.POINTER(D), _d, C.POINTER(D), _d]
         L.orc_trig_count.restype = C.c_int64
         for f in ("orc_rhs_dense", "orc_rhs_csr", "orc_rhs_csr_rows", "orc_rhs_complete_op",
                   "orc_rhs_block", "orc_rk4_csr", "orc_rk4_complete", "orc_order_params",
-                  "orc_potential_csr", "orc_mean_deviation"):
+                  "orc_potential_csr", "orc_mean_deviation", "orc_adjoint_rk4_csr"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -187,3 +189,26 @@ def mean_deviation(theta_t, theta_0, omega, t):
     _check(_load().orc_mean_deviation(theta_t.shape[0], theta_t, _f64(theta_0), _f64(omega), float(t),
                                       C.byref(v)), "mean_deviation")
     return v.value
+
+
+def adjoint_rk4_csr(row_ptr, col, omega, K, theta0, h, n_steps, loss_kind=0, target=None, scaling=0):
+    """Discrete adjoint of RK4 for L = 1 - r(theta(T)) (loss_kind 0) or 1/2 ||theta(T) - target||^2 (1).
+    Returns (L, dL/domega, dL/dK, dL/dtheta0)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    n = row_ptr.shape[0] - 1
+    loss, gK = C.c_double(), C.c_double()
+    g_om, g_th = np.empty(n), np.empty(n)
+    tgt = None if target is None else _f64(target)
+    _check(_load().orc_adjoint_rk4_csr(n, row_ptr, np.ascontiguousarray(col, dtype=np.int32), _f64(omega),
+                                       float(K), int(scaling), _f64(theta0), float(h), int(n_steps),
+                                       int(loss_kind), None if tgt is None else tgt.ctypes.data,
+                                       C.byref(loss), g_om, C.byref(gK), g_th), "adjoint_rk4_csr")
+    return loss.value, g_om, gK.value, g_th
+
+
+def loss_rk4_csr(row_ptr, col, omega, K, theta0, h, n_steps, loss_kind=0, target=None, scaling=0):
+    """Forward loss only (for finite differences)."""
+    th = rk4_csr(row_ptr, col, omega, K, theta0, h, n_steps, scaling)
+    if loss_kind == 0:
+        return 1.0 - order_params(th)[0]
+    return 0.5 * float(np.sum((th - np.asarray(target)) ** 2))

@@ -405,3 +405,133 @@ int orc_mean_deviation(int64_t n, const double* theta_t, const double* theta_0,
     *out = acc_val(&a) / (double)n;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the classical RK4 integrator orc_rk4_csr for a
+ * terminal loss L(theta(T)):
+ *   loss_kind 0: L = 1 - r(theta(T)), r of eq:OrderParameter;
+ *   loss_kind 1: L = 1/2 sum_m (theta_m(T) - target_m)^2.
+ * Returns L and the gradients with respect to omega (g_omega[n]), K (*g_K)
+ * and theta(0) (g_theta0[n]).  The adjoint of one step y' = y + h/6 (k1 + 2 k2
+ * + 2 k3 + k4) with stages k_s = f(Y_s), given lambda = dL/dy':
+ *   w4 = h/6 lambda,              a4 = J(Y4)^T w4
+ *   w3 = h/3 lambda + h a4,       a3 = J(Y3)^T w3
+ *   w2 = h/3 lambda + h/2 a3,     a2 = J(Y2)^T w2
+ *   w1 = h/6 lambda + h/2 a2,     a1 = J(Y1)^T w1
+ *   dL/dy = lambda + a1 + a2 + a3 + a4,
+ *   dL/domega += w1 + w2 + w3 + w4,   dL/dK += sum_s w_s . u(Y_s),
+ * with f = omega + K u and J the Jacobian of f (eq:KuramotoGraph):
+ *   df_m/dtheta_l = (K/calM_m) A_{ml} cos(theta_l - theta_m)  (l != m),
+ *   df_m/dtheta_m = -sum_l of the above.
+ * J^T is applied edge by edge from that definition (any A, symmetric or
+ * not).  All states are kept, so memory is (n_steps + 1) n doubles. */
+static void unit_coupling(int64_t n, const int64_t* row_ptr, const int32_t* col, int scaling,
+                          const double* th, double* u)
+{
+    for (int64_t m = 0; m < n; m++) {
+        acc_t sum = {0, 0};
+        int64_t deg = 0;
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            int64_t l = col[e];
+            if (l == m) continue;
+            acc_add(&sum, sin(th[l] - th[m]));
+            deg++;
+        }
+        double calM = scaling ? (double)deg : (double)n;
+        u[m] = deg > 0 ? acc_val(&sum) / calM : 0.0;
+    }
+}
+
+static void jacobian_t(int64_t n, const int64_t* row_ptr, const int32_t* col, double K, int scaling,
+                       const double* th, const double* mu, double* out)
+{
+    for (int64_t m = 0; m < n; m++) out[m] = 0.0;
+    for (int64_t m = 0; m < n; m++) {
+        int64_t deg = 0;
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) if (col[e] != m) deg++;
+        if (deg == 0) continue;
+        double scale = K / (scaling ? (double)deg : (double)n);
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            int64_t l = col[e];
+            if (l == m) continue;
+            double v = scale * mu[m] * cos(th[l] - th[m]);
+            out[l] += v;
+            out[m] -= v;
+        }
+    }
+}
+
+int orc_adjoint_rk4_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* omega,
+                        double K, int scaling, const double* theta0, double h, int64_t n_steps,
+                        int loss_kind, const double* target, double* loss, double* g_omega,
+                        double* g_K, double* g_theta0)
+{
+    if (n <= 0 || !theta0 || n_steps < 0 || !loss || !g_omega || !g_K || !g_theta0) return -1;
+    if (loss_kind == 1 && !target) return -1;
+    double* ys = malloc(sizeof(double) * (size_t)n * (size_t)(n_steps + 1));
+    double *Y[5], *k[5], *w = malloc(sizeof(double) * (size_t)n), *a[5], *lam = malloc(sizeof(double) * (size_t)n);
+    double* u = malloc(sizeof(double) * (size_t)n);
+    int rc = 0;
+    for (int s = 0; s < 5; s++) {
+        Y[s] = malloc(sizeof(double) * (size_t)n);
+        k[s] = malloc(sizeof(double) * (size_t)n);
+        a[s] = malloc(sizeof(double) * (size_t)n);
+    }
+    if (!ys || !w || !lam || !u) { rc = -2; goto done; }
+    for (int s = 0; s < 5; s++) if (!Y[s] || !k[s] || !a[s]) { rc = -2; goto done; }
+    /* forward, keeping every state */
+    memcpy(ys, theta0, sizeof(double) * (size_t)n);
+    for (int64_t t = 0; t < n_steps; t++) {
+        memcpy(ys + (t + 1) * n, ys + t * n, sizeof(double) * (size_t)n);
+        if ((rc = orc_rk4_csr(n, row_ptr, col, omega, K, scaling, ys + (t + 1) * n, h, 1))) goto done;
+    }
+    /* terminal loss and lambda = dL/dtheta(T) */
+    const double* yT = ys + n_steps * n;
+    if (loss_kind == 0) {
+        double r, psi;
+        orc_order_params(n, yT, &r, &psi, NULL, 0, NULL, NULL);
+        *loss = 1.0 - r;
+        for (int64_t m = 0; m < n; m++) lam[m] = -sin(psi - yT[m]) / (double)n;
+    } else {
+        acc_t L = {0, 0};
+        for (int64_t m = 0; m < n; m++) {
+            double d = yT[m] - target[m];
+            acc_add(&L, 0.5 * d * d);
+            lam[m] = d;
+        }
+        *loss = acc_val(&L);
+    }
+    for (int64_t m = 0; m < n; m++) g_omega[m] = 0.0;
+    *g_K = 0.0;
+    /* backward */
+    for (int64_t t = n_steps - 1; t >= 0; t--) {
+        const double* y = ys + t * n;
+        /* stages of step t: Y1 = y, Y2 = y + h/2 k1, Y3 = y + h/2 k2, Y4 = y + h k3 */
+        memcpy(Y[1], y, sizeof(double) * (size_t)n);
+        orc_rhs_csr(n, row_ptr, col, omega, Y[1], K, scaling, k[1]);
+        for (int64_t m = 0; m < n; m++) Y[2][m] = y[m] + 0.5 * h * k[1][m];
+        orc_rhs_csr(n, row_ptr, col, omega, Y[2], K, scaling, k[2]);
+        for (int64_t m = 0; m < n; m++) Y[3][m] = y[m] + 0.5 * h * k[2][m];
+        orc_rhs_csr(n, row_ptr, col, omega, Y[3], K, scaling, k[3]);
+        for (int64_t m = 0; m < n; m++) Y[4][m] = y[m] + h * k[3][m];
+        const double cl[5] = {0, h / 6.0, h / 3.0, h / 3.0, h / 6.0};      /* weight of lambda */
+        const double ca[5] = {0, 0.5 * h, 0.5 * h, h, 0};                 /* weight of a_{s+1} */
+        for (int s = 4; s >= 1; s--) {
+            for (int64_t m = 0; m < n; m++) w[m] = cl[s] * lam[m] + (s < 4 ? ca[s] * a[s + 1][m] : 0.0);
+            jacobian_t(n, row_ptr, col, K, scaling, Y[s], w, a[s]);
+            unit_coupling(n, row_ptr, col, scaling, Y[s], u);
+            acc_t gk = {0, 0};
+            for (int64_t m = 0; m < n; m++) {
+                g_omega[m] += w[m];
+                acc_add(&gk, w[m] * u[m]);
+            }
+            *g_K += acc_val(&gk);
+        }
+        for (int64_t m = 0; m < n; m++) lam[m] += a[1][m] + a[2][m] + a[3][m] + a[4][m];
+    }
+    memcpy(g_theta0, lam, sizeof(double) * (size_t)n);
+done:
+    free(ys); free(w); free(lam); free(u);
+    for (int s = 0; s < 5; s++) { free(Y[s]); free(k[s]); free(a[s]); }
+    return rc;
+}

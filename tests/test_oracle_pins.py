@@ -350,3 +350,44 @@ def test_paper_classical_runs_synchronise(K):
     assert abs(r - _locked_r(K, 2.0)) < 0.01
     th1 = oracle.rk4_complete(omega, 1.0, theta0, 0.05, 4000)
     assert oracle.order_params(th1)[0] < 0.1
+
+
+# ----------------------------------------------------------------------------- discrete adjoint
+@pytest.mark.parametrize("loss_kind", [0, 1])
+def test_adjoint_matches_central_finite_differences(loss_kind):
+    """The oracle's discrete RK4 adjoint against central differences of the oracle's own forward loss
+    (eps = 1e-6): directional derivatives in theta0 and omega, and the K derivative."""
+    rng = np.random.default_rng(21 + loss_kind)
+    g = G.sbm(5, [30, 25, 20], [0.8, 0.7, 0.9], 0.1)
+    n = g.n
+    omega, theta0 = rng.normal(size=n), rng.uniform(0, 2 * np.pi, n)
+    K, h, steps = 3.0, 0.02, 15
+    target = theta0 + 0.3 * rng.normal(size=n) if loss_kind == 1 else None
+    L, g_om, g_K, g_th = oracle.adjoint_rk4_csr(g.row_ptr, g.col, omega, K, theta0, h, steps, loss_kind, target)
+    f = lambda om, KK, th: oracle.loss_rk4_csr(g.row_ptr, g.col, om, KK, th, h, steps, loss_kind, target)
+    assert abs(L - f(omega, K, theta0)) < 1e-13
+    eps = 1e-6
+    for _ in range(4):
+        d = rng.normal(size=n)
+        fd = (f(omega, K, theta0 + eps * d) - f(omega, K, theta0 - eps * d)) / (2 * eps)
+        assert abs(fd - g_th @ d) <= 1e-7 * (1 + abs(fd))
+        fd = (f(omega + eps * d, K, theta0) - f(omega - eps * d, K, theta0)) / (2 * eps)
+        assert abs(fd - g_om @ d) <= 1e-7 * (1 + abs(fd))
+    fd = (f(omega, K + eps, theta0) - f(omega, K - eps, theta0)) / (2 * eps)
+    assert abs(fd - g_K) <= 1e-7 * (1 + abs(fd))
+
+
+def test_adjoint_uncoupled_closed_form():
+    """K = 0: theta(T) = theta0 + T omega, so for L = 1/2 ||theta(T) - target||^2 the gradients are
+    dL/dtheta0 = theta(T) - target and dL/domega = T (theta(T) - target) exactly."""
+    rng = np.random.default_rng(3)
+    g = G.sbm(6, [40, 30], 0.5, 0.1)
+    n = g.n
+    omega, theta0, target = rng.normal(size=n), rng.uniform(0, 6, n), rng.normal(size=n)
+    h, steps = 0.05, 20
+    T = h * steps
+    L, g_om, g_K, g_th = oracle.adjoint_rk4_csr(g.row_ptr, g.col, omega, 0.0, theta0, h, steps, 1, target)
+    resid = theta0 + T * omega - target
+    np.testing.assert_allclose(g_th, resid, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(g_om, T * resid, atol=1e-12, rtol=0)
+    assert abs(L - 0.5 * resid @ resid) < 1e-11
