@@ -168,6 +168,38 @@ def cpu_baseline_oracle(w, seconds: float = 12.0):
                       f"{g.n}-node graph in {el:.1f} s; RK4 step = 4 evaluations, extrapolated to N rows"}
 
 
+def bench_adjoint(dev):
+    """Loss 1 - r(T) and its gradients on the 65536-node SBM: T = 20, h = 0.01 (2000 steps), a checkpoint every
+    64 steps, FP32 right-hand side, FP64 state.  Reports forward-only and forward+backward wall time."""
+    import torch
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_sbm_small()
+    g = w.graph
+    h, steps, M = 0.01, 2000, 64
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+        th0 = torch.tensor(w.theta0, device=dev)
+        k.adjoint(th0, h, 64, M, 0)                       # warm-up (buffers, graphs)
+        th = th0.clone()
+        k.rk4_steps(th, h, 8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        th = th0.clone()
+        e0.record()
+        k.rk4_steps(th, h, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+        t0 = time.perf_counter()
+        L, gom, gK, gth = k.adjoint(th0, h, steps, M, 0)
+        torch.cuda.synchronize()
+        adj_ms = (time.perf_counter() - t0) * 1e3
+    return {"workload": "SBM N=65536 (64 communities, p_in 0.95, p_out 0.001), loss 1 - r(T), T = 20, "
+                        "h = 0.01, 2000 RK4 steps, checkpoint every 64", "precision": "mixed (FP32 RHS, FP64 state)",
+            "forward_ms": fwd_ms, "forward_backward_ms": adj_ms, "ratio": adj_ms / fwd_ms, "loss": L,
+            "g_K": gK, "g_theta0_norm": float(torch.linalg.norm(gth)), "g_omega_norm": float(torch.linalg.norm(gom))}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -322,6 +354,8 @@ def run_ours(args):
         k2.close()
     if k is not None:
         k.close()
+    if not args.quick and rank == 0 and not args.no_adjoint:
+        extra["adjoint"] = bench_adjoint(dev)
 
     cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds) if (rank == 0 and world == 1 and not args.quick) \
         else None
@@ -351,6 +385,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip the extra comparisons and the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

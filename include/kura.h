@@ -155,6 +155,24 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
 kura_status kura_order_params(kura_t h, const double* theta, double* r, double* psi,
                               double* r_comm, double* psi_comm);
 
+/* Gradient of a terminal loss of an RK4 trajectory by the discrete adjoint
+ * of the classical RK4 step (backward sweep over the stage Jacobians of
+ * eq:KuramotoGraph; the paper's integrator section, Sec. 2, extended to a
+ * loss as the spec training use):
+ *   loss_kind 0: L = 1 - r(theta(T)) (eq:OrderParameter);
+ *   loss_kind 1: L = 1/2 sum_m (theta_m(T) - target_m)^2 (target[n], user order).
+ * theta0[n] (user order, device or host) is not modified.  The forward pass
+ * keeps a checkpoint every ckpt_every steps; the backward pass recomputes one
+ * segment at a time, keeping its stage inputs and stage row sums
+ * (4 * ckpt_every * 24 bytes per node).  Outputs: *loss and *g_K (host),
+ * g_omega[n] and g_theta0[n] (user order, device or host).  Needs a handle
+ * created with KURA_PREC_MIXED (FP32 right-hand side, FP64 state and
+ * accumulations) and a symmetric adjacency matrix (checked once on the host
+ * CSR copy): KURA_ESTATE otherwise.  Synchronises the stream. */
+kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_steps,
+                         int32_t ckpt_every, int32_t loss_kind, const double* target,
+                         double* loss, double* g_omega, double* g_K, double* g_theta0);
+
 /* Replaces omega (nullable; n entries, user order, device or host) and/or
  * K (nullable). */
 kura_status kura_set_param(kura_t h, const double* omega, const double* K);

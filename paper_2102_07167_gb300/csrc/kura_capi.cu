@@ -84,7 +84,12 @@ struct kura_ctx {
     int64_t miss_total = 0, pres_total = 0, nnz = 0, stream_bytes = 0, bitmap_rows = 0;
     // device buffers
     DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off;
-    DevMem omega, rscale, table, bsum, bsum_out, tot, T, counter, err_flags;
+    DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
+    // adjoint (allocated on first use)
+    DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
+        ad_tgt, ad_scratch;
+    int64_t ad_M = 0, ad_nck = 0;
+    int sym = -1;   // host CSR symmetric? (-1 unknown)
     DevMem y, Y, krk, fbuf, user, red, order_out;
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
     int q_bits = 0;
@@ -155,6 +160,8 @@ DevGraph dev_graph(kura_ctx* h)
     g.inv_scale_q = std::ldexp(1.0, -h->q_bits);
     g.scale = h->K / double(h->n);
     g.rscale = h->opts.scaling == KURA_SCALING_DEGREE ? h->rscale.as<double>() : nullptr;
+    g.rinvdeg = h->opts.scaling == KURA_SCALING_DEGREE ? h->rinvdeg.as<double>() : nullptr;
+    g.inv_n = 1.0 / double(h->n);
     g.node_comm = h->node_comm.as<int32_t>();
     g.gstream = h->gstream.as<int32_t>();
     g.groups = h->groups.as<Group>();
@@ -187,9 +194,9 @@ void launch_trig(kura_ctx* h, const DevGraph& g, const double* theta_perm, int w
 }
 
 template <int MODE, int STAGE>
-void launch_row(kura_ctx* h, const DevGraph& g, const RkArgs& rk, cudaStream_t s)
+void launch_row(kura_ctx* h, const DevGraph& g, const RkArgs& rk, cudaStream_t s, const AdjArgs& adj = AdjArgs{})
 {
-    k_row_stage<MODE, STAGE><<<unsigned(h->n_tiles), ROW_THREADS, h->row_smem, s>>>(g, rk);
+    k_row_stage<MODE, STAGE><<<unsigned(h->n_tiles), ROW_THREADS, h->row_smem, s>>>(g, rk, adj);
 }
 
 template <int MODE>
@@ -210,7 +217,7 @@ cudaError_t set_row_attrs(size_t smem)
     cudaError_t e = cudaSuccess;
     const void* fns[] = {(const void*)k_row_stage<MODE, ST_RHS>, (const void*)k_row_stage<MODE, ST_1>,
                          (const void*)k_row_stage<MODE, ST_2>, (const void*)k_row_stage<MODE, ST_3>,
-                         (const void*)k_row_stage<MODE, ST_4>};
+                         (const void*)k_row_stage<MODE, ST_4>, (const void*)k_row_stage<MODE, ST_ADJ>};
     for (const void* f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
@@ -298,6 +305,12 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
             for (int64_t v = 0; v < h->n; v++) rs[size_t(v)] = p.deg[size_t(v)] > 0 ? h->K / p.deg[size_t(v)] : 0.0;
         }
         KCHECK(h, upload(h->rscale, rs, s), "upload rscale");
+        std::vector<double> ri;
+        if (h->opts.scaling == KURA_SCALING_DEGREE) {
+            ri.resize(size_t(h->n));
+            for (int64_t v = 0; v < h->n; v++) ri[size_t(v)] = p.deg[size_t(v)] > 0 ? 1.0 / p.deg[size_t(v)] : 0.0;
+        }
+        KCHECK(h, upload(h->rinvdeg, ri, s), "upload rinvdeg");
     }
     const size_t n = size_t(h->n), nc = size_t(h->n_comm);
     KCHECK(h, h->table.alloc(esize * (n + 2)), "alloc table");
@@ -753,6 +766,210 @@ kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t 
     if (host) {
         KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
         KCHECK(h, cudaStreamSynchronize(s), "synchronise");
+    }
+    return KURA_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+static bool csr_symmetric(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& col)
+{
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 1024) reduction(|:bad)
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t e = rp[size_t(i)]; e < rp[size_t(i) + 1] && !bad; e++) {
+            const int64_t j = col[size_t(e)];
+            if (j == i) continue;
+            if (!std::binary_search(col.begin() + rp[size_t(j)], col.begin() + rp[size_t(j) + 1], int32_t(i))) bad = 1;
+        }
+    }
+    return !bad;
+}
+
+// RK4 steps on the permuted state y through the cached graphs (no boundary permutation).
+static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps)
+{
+    const int64_t chunk_max = 8;
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int64_t c = std::min(left, chunk_max);
+        auto key = std::make_pair(step, c * (h->timing ? -1 : 1));
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            std::unique_ptr<GraphEntry> ge(new GraphEntry());
+            if (h->timing) {
+                ge->events.resize(size_t(8 * c));
+                for (auto& e : ge->events) KCHECK(h, cudaEventCreate(&e), "cudaEventCreate");
+            }
+            cudaGraph_t graph = nullptr;
+            KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int64_t k = 0; k < c; k++)
+                enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
+            ec = cudaGraphInstantiate(&ge->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate graph");
+            it = h->graphs.emplace(key, std::move(ge)).first;
+        }
+        KCHECK(h, cudaGraphLaunch(it->second->exec, h->stream), "graph launch");
+        h->last_graph = it->second.get();
+        left -= c;
+    }
+    return KURA_OK;
+}
+
+kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_steps, int32_t ckpt_every,
+                         int32_t loss_kind, const double* target, double* loss, double* g_omega, double* g_K,
+                         double* g_theta0)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!theta0 || !loss || !g_omega || !g_K || !g_theta0) return h->fail(KURA_EINVAL, "NULL argument");
+    if (!(step > 0) || !std::isfinite(step) || n_steps < 1 || ckpt_every < 1)
+        return h->fail(KURA_EINVAL, "step > 0, n_steps >= 1 and ckpt_every >= 1 are required");
+    if (loss_kind != 0 && loss_kind != 1) return h->fail(KURA_EINVAL, "loss_kind must be 0 or 1");
+    if (loss_kind == 1 && !target) return h->fail(KURA_EINVAL, "loss_kind 1 needs a target");
+    if (h->opts.precision != KURA_PREC_MIXED)
+        return h->fail(KURA_ESTATE, "the adjoint runs on handles created with KURA_PREC_MIXED");
+    if (h->sym < 0) {
+        if (h->h_col.empty() && h->nnz > 0)
+            return h->fail(KURA_ESTATE, "the adjoint needs the host CSR copy to check symmetry");
+        h->sym = csr_symmetric(h->n, h->h_row_ptr, h->h_col) ? 1 : 0;
+    }
+    if (!h->sym) return h->fail(KURA_ESTATE, "the adjoint supports symmetric adjacency matrices only");
+    cudaStream_t s = h->stream;
+    const size_t n = size_t(h->n), N8 = 8 * n;
+    const int64_t M = ckpt_every;
+    const int64_t nck = (n_steps + M - 1) / M;
+    // buffers
+    if (h->ad_M != M || h->ad_nck < nck || !h->ad_lam.p) {
+        KCHECK(h, h->ad_ck.alloc(N8 * size_t(nck)), "alloc checkpoints");
+        KCHECK(h, h->ad_Y.alloc(N8 * size_t(4 * M + 1)), "alloc stage inputs");
+        KCHECK(h, h->ad_F.alloc(16 * n * size_t(4 * M)), "alloc stage sums");
+        for (DevMem* d : {&h->ad_lam, &h->ad_asum, &h->ad_a0, &h->ad_a1, &h->ad_w, &h->ad_nu, &h->ad_gom, &h->ad_tgt,
+                          &h->ad_scratch})
+            KCHECK(h, d->alloc(N8), "alloc adjoint vectors");
+        KCHECK(h, h->ad_sc.alloc(8 * n), "alloc sc");
+        KCHECK(h, h->ad_bs.alloc(16 * size_t(h->n_comm)), "alloc block sums");
+        KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(h->n_tiles, 1))), "alloc dK accumulators");
+        KCHECK(h, h->ad_part.alloc(8 * ((n + 255) / 256)), "alloc loss partials");
+        h->ad_M = M;
+        h->ad_nck = nck;
+    }
+    double* ck = h->ad_ck.as<double>();
+    double* Ybuf = h->ad_Y.as<double>();                // stage inputs: slot 4 t + (s - 1), plus one spare
+    double2* Fbuf = h->ad_F.as<double2>();              // forward row sums per (t, s)
+    const unsigned nb = blocks_for(h->n, 256);
+    const DevGraph g = dev_graph(h);
+
+    // ---- forward with checkpoints (permuted state y)
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta0, &th_dev, &host)) return st;
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), th_dev, h->y.as<double>());
+    if (loss_kind == 1) {
+        const double* tg_dev;
+        bool th;
+        if (kura_status st = stage_in(h, target, &tg_dev, &th)) return st;
+        k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), tg_dev, h->ad_tgt.as<double>());
+    }
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    for (int64_t c = 0; c < nck; c++) {
+        KCHECK(h, cudaMemcpyAsync(ck + size_t(c) * n, h->y.p, N8, cudaMemcpyDeviceToDevice, s), "checkpoint");
+        if (kura_status st = run_steps_perm(h, step, std::min(M, n_steps - c * M))) return st;
+    }
+    // ---- terminal loss and lambda
+    double* lam = h->ad_lam.as<double>();
+    double* yT = h->y.as<double>();
+    if (loss_kind == 0) {
+        launch_trig<MODE_FP64>(h, g, yT, 0, s);   // exact block sums of FP64 sin/cos of theta(T)
+        k_order_finalize<<<blocks_for(std::max(h->n_comm, 1), 256), 256, 0, s>>>(
+            h->n_comm, h->n, h->bsum_out.as<long long>(), h->tot.as<long long>(), h->comm_off.as<int64_t>(),
+            std::ldexp(1.0, -h->q_bits), h->order_out.as<double>());
+        k_adj_terminal_r<<<nb, 256, 0, s>>>(h->n, yT, h->order_out.as<double>(), lam);
+    } else {
+        k_adj_terminal_misfit<<<nb, 256, 0, s>>>(h->n, yT, h->ad_tgt.as<double>(), lam, h->ad_part.as<double>());
+    }
+    KCHECK(h, cudaMemsetAsync(h->ad_gom.p, 0, N8, s), "zero g_omega");
+    KCHECK(h, cudaMemsetAsync(h->ad_gk.p, 0, h->ad_gk.bytes, s), "zero dK accumulators");
+    KCHECK(h, cudaGetLastError(), "launching the terminal adjoint");
+
+    // ---- backward, segment by segment
+    const double cl[5] = {0, step / 6.0, step / 3.0, step / 3.0, step / 6.0};
+    const double ca[5] = {0, 0.5 * step, 0.5 * step, step, 0.0};
+    for (int64_t c = nck - 1; c >= 0; c--) {
+        const int64_t L = std::min(M, n_steps - c * M);
+        // recompute the segment, keeping every stage input and the forward row sums
+        KCHECK(h, cudaMemcpyAsync(Ybuf, ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, s), "restore checkpoint");
+        for (int64_t t = 0; t < L; t++) {
+            for (int st = ST_1; st <= ST_4; st++) {
+                RkArgs rk{};
+                rk.y = Ybuf + size_t(4 * t) * n;
+                rk.Y = Ybuf + size_t(4 * t + st) * n;                         // next stage input
+                rk.y_out = (t + 1 < L) ? Ybuf + size_t(4 * (t + 1)) * n : h->ad_scratch.as<double>();
+                rk.krk = h->krk.as<double>();
+                rk.sums_out = Fbuf + size_t(4 * t + st - 1) * n;
+                rk.h = step;
+                launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, s);
+                launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
+            }
+        }
+        // adjoint steps, last to first
+        for (int64_t t = L - 1; t >= 0; t--) {
+            for (int st = 4; st >= 1; st--) {
+                double* a_next = (st < 4) ? ((st % 2 == 1) ? h->ad_a0.as<double>() : h->ad_a1.as<double>()) : nullptr;
+                double* a_out = (st % 2 == 0) ? h->ad_a0.as<double>() : h->ad_a1.as<double>();
+                k_adj_prep<<<nb, 256, 0, s>>>(g, Ybuf + size_t(4 * t + st - 1) * n, lam, a_next, cl[st], ca[st],
+                                              h->ad_w.as<double>(), h->ad_nu.as<double>(), h->ad_sc.as<float2>(),
+                                              h->ad_gom.as<double>());
+                k_adj_blocksum<<<unsigned(std::max(h->n_comm, 1)), 256, 0, s>>>(g, h->ad_bs.as<double2>());
+                k_adj_T<<<blocks_for(std::max(h->n_comm, 1), 256), 256, 0, s>>>(g, h->ad_bs.as<double2>());
+                AdjArgs adj{};
+                adj.fsums = Fbuf + size_t(4 * t + st - 1) * n;
+                adj.sc = h->ad_sc.as<float2>();
+                adj.nu = h->ad_nu.as<double>();
+                adj.w = h->ad_w.as<double>();
+                adj.a_out = a_out;
+                adj.asum = h->ad_asum.as<double>();
+                adj.lam = lam;
+                adj.gk_acc = h->ad_gk.as<double>();
+                adj.stage = st;
+                RkArgs rk{};
+                launch_row<MODE_MIXED, ST_ADJ>(h, g, rk, s, adj);
+            }
+        }
+        KCHECK(h, cudaGetLastError(), "launching the adjoint");
+    }
+    // ---- outputs
+    double* gth_dev = host ? h->user.as<double>() : g_theta0;
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), lam, gth_dev);
+    const bool gom_host = !is_device_ptr(g_omega);
+    double* gom_dev = gom_host ? h->fbuf.as<double>() : g_omega;
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->ad_gom.as<double>(), gom_dev);
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    std::vector<double> gk(size_t(std::max(h->n_tiles, 1)));
+    KCHECK(h, cudaMemcpyAsync(gk.data(), h->ad_gk.p, gk.size() * 8, cudaMemcpyDeviceToHost, s), "copy dK");
+    double Lval = 0.0;
+    std::vector<double> part;
+    if (loss_kind == 0) {
+        KCHECK(h, cudaMemcpyAsync(&Lval, h->order_out.p, 8, cudaMemcpyDeviceToHost, s), "copy r");
+    } else {
+        part.resize((n + 255) / 256);
+        KCHECK(h, cudaMemcpyAsync(part.data(), h->ad_part.p, part.size() * 8, cudaMemcpyDeviceToHost, s), "copy loss");
+    }
+    if (host && g_theta0 != gth_dev)
+        KCHECK(h, cudaMemcpyAsync(g_theta0, gth_dev, N8, cudaMemcpyDeviceToHost, s), "copy g_theta0");
+    if (gom_host) KCHECK(h, cudaMemcpyAsync(g_omega, gom_dev, N8, cudaMemcpyDeviceToHost, s), "copy g_omega");
+    kura_status st = read_flags(h);
+    if (st) return st;
+    double gks = 0.0;
+    for (double v : gk) gks += v;
+    *g_K = gks;
+    if (loss_kind == 0) {
+        *loss = 1.0 - Lval;
+    } else {
+        double lsum = 0.0;
+        for (double v : part) lsum += v;
+        *loss = lsum;
     }
     return KURA_OK;
 }

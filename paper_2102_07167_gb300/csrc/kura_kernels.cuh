@@ -29,7 +29,7 @@ __host__ __device__ constexpr int slots_for(int mode) { return mode == 0 ? 3 : 4
 __host__ __device__ constexpr int tile_max_sub_for(int mode) { return mode == 0 ? 512 : 768; }
 
 enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
-enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4 };
+enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4, ST_ADJ = 5 };
 enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 enum : int { TB_TABLE = 1, TB_T = 2 };   // what k_trig_blocksum writes
 
@@ -50,6 +50,8 @@ struct DevGraph {
     double scale_q, inv_scale_q;            // 2^q, 2^-q
     double scale;                           // K / N (uniform scaling)
     const double* rscale;                   // per permuted row K / calM_m (degree scaling) or null
+    const double* rinvdeg;                  // per permuted row 1 / calM_m (degree scaling) or null
+    double inv_n;                           // 1 / N (uniform scaling)
     const int32_t* node_comm;               // [n]
     const int32_t* gstream;                 // packed row groups (see Group in plan.hpp)
     const Group* groups;
@@ -75,7 +77,22 @@ struct RkArgs {
     double* Y;            // next stage input
     double* krk;          // k1 + 2 k2 + 2 k3 accumulator
     double* out;          // ST_RHS: f
+    double2* sums_out;    // nullable: row sums sum_l A_ml (sin th_l, cos th_l) of the stage
     double h;
+};
+
+// Adjoint stage s of the discrete RK4 adjoint (ST_ADJ): the table holds
+// (nu sin th, nu cos th) of the stage input, nu = w K / calM.
+struct AdjArgs {
+    const double2* fsums;   // forward row sums (A sin th, A cos th) at the stage input
+    const float2* sc;       // (sin th, cos th) of the stage input
+    const double* nu;       // w K / calM per row
+    const double* w;        // adjoint weight w_s per row
+    double* a_out;          // a_s = J^T w_s (stages 4..2)
+    double* asum;           // a_4 + a_3 + a_2 accumulated over the step
+    double* lam;            // lambda; stage 1 adds a_1 + asum and clears asum
+    double* gk_acc;         // per-CTA accumulators of dL/dK
+    int stage;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -269,7 +286,7 @@ struct Acc2 {
 // the FP64 epilogue: f = omega + scale (cos th acc_s - sin th acc_c), T_I
 // added, and the RK4 stage update.
 template <int MODE, int STAGE>
-__global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk)
+__global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk, AdjArgs adj)
 {
     using E = typename EntryT<MODE>::T;
     using A = typename EntryT<MODE>::A;
@@ -461,6 +478,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
 
     // ---------------- epilogue: one thread per row, FP64
     const int nrows = t.r1 - t.r0;
+    double gk_local = 0.0;
     for (int k = tid; k < nrows; k += ROW_THREADS) {
         const int64_t row = int64_t(t.r0) + k;
         const int s0 = g.row_sub0[row] - t.sub0, s1 = g.row_sub0[row + 1] - t.sub0;
@@ -488,9 +506,28 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             si = static_cast<double>(own.x);
             ci = static_cast<double>(own.y);
         }
+        if (STAGE == ST_ADJ) {
+            // a = (J^T w)_m for symmetric A: c_m A(nu c)_m + s_m A(nu s)_m - nu_m (c_m (A c)_m + s_m (A s)_m)
+            const double2 fs = adj.fsums[row];
+            const float2 scv = adj.sc[row];
+            const double sj = static_cast<double>(scv.x), cj = static_cast<double>(scv.y);
+            const double nu = adj.nu[row];
+            const double a = cj * acc_c + sj * acc_s - nu * (cj * fs.y + sj * fs.x);
+            const double inv_m = g.rinvdeg ? g.rinvdeg[row] : g.inv_n;
+            gk_local += adj.w[row] * inv_m * (cj * fs.x - sj * fs.y);    // w . df/dK
+            if (!isfinite(a)) atomicOr(g.err, ERR_NONFINITE);
+            if (adj.stage > 1) {
+                adj.a_out[row] = a;
+                adj.asum[row] = (adj.stage == 4 ? 0.0 : adj.asum[row]) + a;
+            } else {
+                adj.lam[row] = adj.lam[row] + adj.asum[row] + a;
+            }
+            continue;
+        }
         const double sc = g.rscale ? g.rscale[row] : g.scale;
         const double f = g.omega[row] + sc * (ci * acc_s - si * acc_c);
         if (!isfinite(f)) atomicOr(g.err, ERR_NONFINITE);
+        if (rk.sums_out) rk.sums_out[row] = make_double2(acc_s, acc_c);
         if (STAGE == ST_RHS) {
             rk.out[row] = f;
         } else if (STAGE == ST_1) {
@@ -506,6 +543,119 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             rk.y_out[row] = rk.y[row] + (rk.h / 6.0) * (rk.krk[row] + f);
         }
     }
+    if (STAGE == ST_ADJ) {
+        // fixed-order CTA reduction of dL/dK into this tile's accumulator
+        __shared__ double gk_red[ROW_THREADS / 32];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) gk_local += __shfl_xor_sync(0xffffffffu, gk_local, o);
+        if (lane == 0) gk_red[warp] = gk_local;
+        __syncthreads();
+        if (tid == 0) {
+            double v = 0.0;
+            for (int q = 0; q < ROW_THREADS / 32; q++) v += gk_red[q];
+            adj.gk_acc[blockIdx.x] += v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- adjoint helpers
+// Per node, adjoint stage s: w = c_lam lambda + c_a a_{s+1}, nu = w K / calM,
+// (sin, cos) of the stage input in FP32 (as in the mixed forward), the table
+// entry (nu sin, nu cos), and dL/domega += w.
+__global__ void k_adj_prep(DevGraph g, const double* __restrict__ Ys, const double* __restrict__ lam,
+                           const double* __restrict__ a_next, double c_lam, double c_a, double* __restrict__ w,
+                           double* __restrict__ nu, float2* __restrict__ sc, double* __restrict__ g_omega)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const double wi = c_lam * lam[i] + (a_next ? c_a * a_next[i] : 0.0);
+    const double scale = g.rscale ? g.rscale[i] : g.scale;
+    const double nui = wi * scale;
+    const double th = Ys[i];
+    const double k = rint(th * KURA_INV_TWO_PI);
+    double r = fma(-k, KURA_TWO_PI_HI, th);
+    r = fma(-k, KURA_TWO_PI_LO, r);
+    float s, c;
+    sincosf(static_cast<float>(r), &s, &c);
+    w[i] = wi;
+    nu[i] = nui;
+    sc[i] = make_float2(s, c);
+    reinterpret_cast<float2*>(g.table)[i] =
+        make_float2(static_cast<float>(nui * static_cast<double>(s)), static_cast<float>(nui * static_cast<double>(c)));
+    g_omega[i] += wi;
+}
+
+// One CTA per community: FP64 sums of the (nu sin, nu cos) table over the
+// community's nodes in a fixed order (deterministic), into out[J].
+__global__ void __launch_bounds__(256) k_adj_blocksum(DevGraph g, double2* __restrict__ out)
+{
+    const int J = blockIdx.x;
+    const int64_t b = g.comm_off[J], e = g.comm_off[J + 1];
+    const float2* tab = reinterpret_cast<const float2*>(g.table);
+    double s = 0.0, c = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+        const float2 v = tab[i];
+        s += static_cast<double>(v.x);
+        c += static_cast<double>(v.y);
+    }
+    __shared__ double rs[256], rc[256];
+    rs[threadIdx.x] = s;
+    rc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            rs[threadIdx.x] += rs[threadIdx.x + o];
+            rc[threadIdx.x] += rc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[J] = make_double2(rs[0], rc[0]);
+}
+
+// T_I = sum over the dense column blocks J of I of the block sums (mixed layout).
+__global__ void k_adj_T(DevGraph g, const double2* __restrict__ bs)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= g.n_comm) return;
+    double s = 0.0, c = 0.0;
+    for (int64_t k = g.dptr[I]; k < g.dptr[I + 1]; k++) {
+        const double2 v = bs[g.dcol[k]];
+        s += v.x;
+        c += v.y;
+    }
+    reinterpret_cast<double2*>(g.T)[I] = make_double2(s, c);
+}
+
+// Terminal adjoint of L = 1 - r: lambda_m = -sin(psi - theta_m) / N, psi from order_out[1].
+__global__ void k_adj_terminal_r(int64_t n, const double* __restrict__ y, const double* __restrict__ order_out,
+                                 double* __restrict__ lam)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    lam[i] = -sin(order_out[1] - y[i]) / static_cast<double>(n);
+}
+
+// Terminal adjoint of L = 1/2 ||theta - target||^2: lambda = theta - target (permuted target), and
+// per-CTA partial sums of the loss in a fixed order.
+__global__ void __launch_bounds__(256) k_adj_terminal_misfit(int64_t n, const double* __restrict__ y,
+                                                             const double* __restrict__ target_perm,
+                                                             double* __restrict__ lam, double* __restrict__ part)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < n) {
+        const double d = y[i] - target_perm[i];
+        lam[i] = d;
+        l = 0.5 * d * d;
+    }
+    __shared__ double r[256];
+    r[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = r[0];
 }
 
 // ---------------------------------------------------------------- order parameters

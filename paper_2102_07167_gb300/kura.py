@@ -87,6 +87,7 @@ def load() -> C.CDLL:
             "kura_rk4_steps": (S, [P, P, D, I64]),
             "kura_order_params": (S, [P, P, C.POINTER(D), C.POINTER(D), P, P]),
             "kura_set_param": (S, [P, P, P]),
+            "kura_adjoint": (S, [P, P, D, I64, I32, I32, P, C.POINTER(D), P, C.POINTER(D), P]),
             "kura_direct_rhs": (S, [P, P, P, I32]),
             "kura_direct_rk4_steps": (S, [P, P, D, I64, I32]),
             "kura_set_timing": (S, [P, I32]),
@@ -213,6 +214,15 @@ def kura_order_params(h, theta, n, n_comm, per_community: bool = False):
 def kura_set_param(h, omega=None, K=None, n=None):
     k = C.c_double(float(K)) if K is not None else None
     _check(load().kura_set_param(h, _ptr(omega, n=n), C.byref(k) if k is not None else None), h)
+
+
+def kura_adjoint(h, theta0, step, n_steps, ckpt_every, loss_kind, target, g_omega, g_theta0, n):
+    """Returns (loss, g_K); fills g_omega[n] and g_theta0[n] (tensors or arrays, user order)."""
+    loss, gK = C.c_double(), C.c_double()
+    _check(load().kura_adjoint(h, _ptr(theta0, n=n), float(step), int(n_steps), int(ckpt_every), int(loss_kind),
+                               _ptr(target, n=n) if target is not None else None, C.byref(loss),
+                               _ptr(g_omega, n=n), C.byref(gK), _ptr(g_theta0, n=n)), h)
+    return loss.value, gK.value
 
 
 def kura_direct_rhs(h, theta, dtheta, precision, n):
@@ -364,6 +374,17 @@ class Kuramoto:
 
     def stats(self):
         return kura_get_stats(self.h)
+
+    def adjoint(self, theta0, step, n_steps, ckpt_every=64, loss_kind=0, target=None, g_omega=None, g_theta0=None):
+        """Loss and gradients (loss, g_omega, g_K, g_theta0) of the RK4 trajectory from theta0."""
+        import torch
+        if g_omega is None:
+            g_omega = torch.empty_like(theta0) if hasattr(theta0, "data_ptr") else np.empty(self.n)
+        if g_theta0 is None:
+            g_theta0 = torch.empty_like(theta0) if hasattr(theta0, "data_ptr") else np.empty(self.n)
+        loss, gK = kura_adjoint(self.h, theta0, step, n_steps, ckpt_every, loss_kind, target, g_omega, g_theta0,
+                                self.n)
+        return loss, g_omega, gK, g_theta0
 
     def direct_rhs(self, theta, out, precision=PREC_FP64):
         kura_direct_rhs(self.h, theta, out, precision, self.n)

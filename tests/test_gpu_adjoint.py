@@ -1,0 +1,128 @@
+"""GPU discrete RK4 adjoint (kura_adjoint, FP32 right-hand side, FP64 state) against the FP64 oracle adjoint
+and against central finite differences of the forward map."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_07167_gb300 import gen as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2102_07167_gb300 import kura
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = G.workload_sbm_small(n=3000, n_comm=5, min_size=200, seed=7)
+    return w
+
+
+@pytest.mark.parametrize("loss_kind", [0, 1])
+def test_adjoint_matches_oracle_adjoint(small, loss_kind):
+    w = small
+    g = w.graph
+    h, steps, M = 0.01, 30, 8          # 4 segments: 8 + 8 + 8 + 6
+    rng = np.random.default_rng(loss_kind)
+    target = w.theta0 + 0.2 * rng.normal(size=g.n) if loss_kind == 1 else None
+    L_ref, gom_ref, gK_ref, gth_ref = oracle.adjoint_rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, h, steps,
+                                                             loss_kind, target)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+        th0 = torch.tensor(w.theta0, device="cuda:0")
+        tg = torch.tensor(target, device="cuda:0") if target is not None else None
+        L, gom, gK, gth = k.adjoint(th0, h, steps, M, loss_kind, tg)
+        torch.cuda.synchronize()
+        gom, gth = gom.cpu().numpy(), gth.cpu().numpy()
+        assert np.array_equal(th0.cpu().numpy(), w.theta0)          # theta0 is not modified
+        # a second call gives the bitwise same result (deterministic reductions)
+        L2, gom2, gK2, gth2 = k.adjoint(th0, h, steps, M, loss_kind, tg)
+        assert L2 == L and gK2 == gK and np.array_equal(gom2.cpu().numpy(), gom)
+    assert abs(L - L_ref) <= 1e-6 * max(1.0, abs(L_ref))
+    assert _rel(gth, gth_ref) < 2e-4, _rel(gth, gth_ref)
+    assert _rel(gom, gom_ref) < 2e-4, _rel(gom, gom_ref)
+    assert abs(gK - gK_ref) <= 2e-4 * max(abs(gK_ref), 1e-12), (gK, gK_ref)
+
+
+def test_adjoint_matches_finite_differences_of_forward(small):
+    """Directional derivatives by central differences (eps = 1e-6) of the FP64 forward loss 1 - r(T)."""
+    w = small
+    g = w.graph
+    h, steps = 0.01, 40
+    rng = np.random.default_rng(5)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as ka, \
+            kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as kf:
+        L, gom, gK, gth = ka.adjoint(torch.tensor(w.theta0, device="cuda:0"), h, steps, 16, 0)
+        gth, gom = gth.cpu().numpy(), gom.cpu().numpy()
+
+        def loss(theta0, omega, K):
+            kf.set_param(omega=np.ascontiguousarray(omega), K=K)
+            th = torch.tensor(theta0, device="cuda:0")
+            kf.rk4_steps(th, h, steps)
+            return 1.0 - kf.order_params(th)[0]
+
+        eps = 1e-6
+        for _ in range(3):
+            d = rng.normal(size=g.n)
+            fd = (loss(w.theta0 + eps * d, w.omega, w.K) - loss(w.theta0 - eps * d, w.omega, w.K)) / (2 * eps)
+            assert abs(fd - gth @ d) <= 1e-3 * abs(fd) + 1e-7, (fd, gth @ d)
+            fd = (loss(w.theta0, w.omega + eps * d, w.K) - loss(w.theta0, w.omega - eps * d, w.K)) / (2 * eps)
+            assert abs(fd - gom @ d) <= 1e-3 * abs(fd) + 1e-7, (fd, gom @ d)
+        fd = (loss(w.theta0, w.omega, w.K + eps) - loss(w.theta0, w.omega, w.K - eps)) / (2 * eps)
+        assert abs(fd - gK) <= 1e-3 * abs(fd) + 1e-7, (fd, gK)
+
+
+def test_adjoint_uncoupled_closed_form(small):
+    w = small
+    g = w.graph
+    h, steps = 0.05, 12
+    T = h * steps
+    target = np.zeros(g.n)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, 0.0, precision=kura.PREC_MIXED) as k:
+        L, gom, gK, gth = k.adjoint(np.ascontiguousarray(w.theta0), h, steps, 5, 1, target)
+    resid = w.theta0 + T * w.omega
+    np.testing.assert_allclose(gth, resid, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(gom, T * resid, atol=1e-11, rtol=0)
+
+
+def test_adjoint_rejects_unsupported_handles(small):
+    w = small
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as k:      # FP64 handle
+        with pytest.raises(kura.KuraError) as e:
+            k.adjoint(np.ascontiguousarray(w.theta0), 0.01, 2)
+        assert e.value.status == kura.KURA_ESTATE
+    A = np.zeros((6, 6), np.uint8)
+    A[0, 1] = 1                                                                        # directed edge
+    gd = G.from_dense(A)
+    with kura.Kuramoto(gd.row_ptr, gd.col, gd.label, 1, np.zeros(6), 1.0, precision=kura.PREC_MIXED) as k:
+        with pytest.raises(kura.KuraError) as e:
+            k.adjoint(np.zeros(6), 0.01, 2)
+        assert e.value.status == kura.KURA_ESTATE
+
+
+def test_autograd_function(small):
+    from paper_2102_07167_gb300.autograd import KuraRK4Loss
+    w = small
+    g = w.graph
+    dev = torch.device("cuda", 0)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+        th0 = torch.tensor(w.theta0, device=dev, requires_grad=True)
+        om = torch.tensor(w.omega, device=dev, requires_grad=True)
+        K = torch.tensor(w.K, dtype=torch.float64, device=dev, requires_grad=True)
+        loss = KuraRK4Loss.apply(th0, om, K, k, 0.01, 20, 8, 0, None)
+        (2.0 * loss).backward()
+        L, gom, gK, gth = k.adjoint(torch.tensor(w.theta0, device=dev), 0.01, 20, 8, 0)
+        assert abs(loss.item() - L) < 1e-15
+        assert torch.allclose(th0.grad, 2.0 * gth, rtol=0, atol=0)
+        assert torch.allclose(om.grad, 2.0 * gom, rtol=0, atol=0)
+        assert abs(K.grad.item() - 2.0 * gK) < 1e-15
+        # one gradient step on K lowers 1 - r (strengthening the coupling synchronises)
+        with torch.no_grad():
+            K2 = K - 50.0 * K.grad
+        loss2 = KuraRK4Loss.apply(th0.detach(), om.detach(), K2, k, 0.01, 20, 8, 0, None)
+        assert loss2.item() < loss.item()
