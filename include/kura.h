@@ -173,6 +173,34 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                          int32_t ckpt_every, int32_t loss_kind, const double* target,
                          double* loss, double* g_omega, double* g_K, double* g_theta0);
 
+/* One trajectory of a batch: its own graph (CSR as in kura_create), community
+ * labels, natural frequencies and coupling constant.  row_ptr == NULL denotes
+ * the complete graph without self-loops (the classical model, eq:Kuramoto):
+ * col and label are ignored and n_comm must be 1. */
+typedef struct {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* label;
+    int32_t n_comm;
+    const double* omega;
+    double K;
+} kura_graph_desc;
+
+/* Creates a batch handle: n_traj independent trajectories (uneven sizes,
+ * 1 <= n <= 16384 and n_comm <= 1024 each), integrated together by one
+ * persistent launch per kura_rk4_steps call.  Each trajectory is planned as
+ * in kura_create (eq:KuramotoGraphApproach with opts->tau, uniform scaling
+ * K/n); only KURA_PREC_MIXED is supported.  On a batch handle kura_rk4_steps
+ * takes the phases of all trajectories concatenated in trajectory order
+ * (user order within each); the other per-graph calls return KURA_ESTATE.
+ * Host arrays are copied.  Errors as for kura_create. */
+kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts,
+                              void* stream, kura_t* out);
+
+/* Sizes of a batch: total oscillators and stored corrections (nullable outputs). */
+kura_status kura_batch_stats(kura_t h, int64_t* n_total, int64_t* missing, int64_t* present);
+
 /* Replaces omega (nullable; n entries, user order, device or host) and/or
  * K (nullable). */
 kura_status kura_set_param(kura_t h, const double* omega, const double* K);

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "kura.h"
+#include "kura_batch.cuh"
 #include "kura_kernels.cuh"
 #include "plan.hpp"
 
@@ -67,8 +68,16 @@ int ceil_log2(int64_t v)
 
 }  // namespace
 
+// Device data of a batch handle (kura_batch_create).
+struct BatchData {
+    int32_t n_traj = 0;
+    int64_t n_total = 0, entries = 0, missing = 0, present = 0;
+    DevMem traj, order, comm_off, dptr, dcol, node_comm, row_off, row_nm, entries_d, queue, stash;
+};
+
 struct kura_ctx {
     std::string err;
+    std::unique_ptr<BatchData> batch;    // non-null for a batch handle
     int device = 0;
     kura_opts opts{};
     int64_t n = 0;
@@ -344,6 +353,15 @@ kura_status check_handle(kura_t h)
     return KURA_OK;
 }
 
+// Calls that need a single-graph handle.
+kura_status check_single(kura_t h)
+{
+    if (!h) return KURA_EINVAL;
+    if (h->batch) return h->fail(KURA_ESTATE, "not available on a batch handle");
+    cudaSetDevice(h->device);
+    return KURA_OK;
+}
+
 // Latched device conditions -> status (clears them).
 kura_status read_flags(kura_t h)
 {
@@ -499,7 +517,7 @@ kura_status kura_get_stats(kura_t h, kura_block_stats* s)
 
 kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (tau >= 0) {
         if (tau > 1.0) return h->fail(KURA_EINVAL, "tau must be in [0, 1]");
         if (h->h_col.empty() && h->nnz > 0)
@@ -538,7 +556,7 @@ kura_status kura_sync(kura_t h)
 
 kura_status kura_rhs(kura_t h, const double* theta, double* dtheta)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
     const double* th_dev;
     bool host_in;
@@ -566,12 +584,15 @@ kura_status kura_rhs(kura_t h, const double* theta, double* dtheta)
     return KURA_OK;
 }
 
+static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps);
+
 kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
 {
     if (check_handle(h)) return KURA_EINVAL;
     if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
     if (!(step > 0) || !std::isfinite(step)) return h->fail(KURA_EINVAL, "step must be positive and finite");
     if (n_steps < 0) return h->fail(KURA_EINVAL, "n_steps must be >= 0");
+    if (h->batch) return batch_rk4_steps(h, theta, step, n_steps);
     const double* th_dev;
     bool host;
     if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
@@ -619,7 +640,7 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
 kura_status kura_order_params(kura_t h, const double* theta, double* r, double* psi, double* r_comm,
                               double* psi_comm)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !r || !psi) return h->fail(KURA_EINVAL, "NULL argument");
     const double* th_dev;
     bool host;
@@ -649,7 +670,7 @@ kura_status kura_order_params(kura_t h, const double* theta, double* r, double* 
 
 kura_status kura_set_param(kura_t h, const double* omega, const double* K)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (K) {
         if (!std::isfinite(*K)) return h->fail(KURA_EINVAL, "K is not finite");
         h->K = *K;
@@ -713,7 +734,7 @@ static void launch_direct(kura_t h, const double* th_user, double* out_user, int
 
 kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32_t precision)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
     if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
     if (kura_status st = ensure_direct(h)) return st;
@@ -733,7 +754,7 @@ kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32
 
 kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps, int32_t precision)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
     if (!(step > 0) || !std::isfinite(step) || n_steps < 0) return h->fail(KURA_EINVAL, "bad step or n_steps");
     if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
@@ -822,7 +843,7 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                          int32_t loss_kind, const double* target, double* loss, double* g_omega, double* g_K,
                          double* g_theta0)
 {
-    if (check_handle(h)) return KURA_EINVAL;
+    if (kura_status st0 = check_single(h)) return st0;
     if (!theta0 || !loss || !g_omega || !g_K || !g_theta0) return h->fail(KURA_EINVAL, "NULL argument");
     if (!(step > 0) || !std::isfinite(step) || n_steps < 1 || ckpt_every < 1)
         return h->fail(KURA_EINVAL, "step > 0, n_steps >= 1 and ckpt_every >= 1 are required");
@@ -971,6 +992,225 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         for (double v : part) lsum += v;
         *loss = lsum;
     }
+    return KURA_OK;
+}
+
+// ---------------------------------------------------------------- batched ensembles
+static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
+{
+    BatchData& B = *h->batch;
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    double* io = host ? h->user.as<double>() : theta;
+    cudaStream_t s = h->stream;
+    const unsigned nb = blocks_for(h->n, 256);
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), io, h->y.as<double>());
+    KCHECK(h, cudaMemsetAsync(B.queue.p, 0, 16, s), "reset the trajectory queue");
+    BatchDev bd{};
+    bd.traj = B.traj.as<BatchTraj>();
+    bd.order = B.order.as<int32_t>();
+    bd.n_traj = B.n_traj;
+    bd.comm_off = B.comm_off.as<int32_t>();
+    bd.dptr = B.dptr.as<int32_t>();
+    bd.dcol = B.dcol.as<int32_t>();
+    bd.node_comm = B.node_comm.as<uint16_t>();
+    bd.row_off = B.row_off.as<int32_t>();
+    bd.row_nm = B.row_nm.as<int32_t>();
+    bd.entries = B.entries_d.as<uint16_t>();
+    bd.omega = h->omega.as<double>();
+    bd.y = h->y.as<double>();
+    bd.Y = h->Y.as<double>();
+    bd.krk = h->krk.as<double>();
+    bd.stash = B.stash.as<float2>();
+    bd.queue = B.queue.as<unsigned int>();
+    bd.err = h->err_flags.as<int>();
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    const size_t smem = size_t(BATCH_MAX_N) * 8 + size_t(2 * BATCH_MAX_COMM) * 8 + size_t(BATCH_MAX_COMM) * 16;
+    static GraphEntry batch_events;   // unused placeholder keeps kernel_times semantics simple
+    (void)batch_events;
+    if (n_steps > 0) {
+        if (h->timing) {
+            if (!h->last_graph || h->last_graph->events.size() != 2) {
+                h->graphs.clear();
+                std::unique_ptr<GraphEntry> ge(new GraphEntry());
+                ge->events.resize(2);
+                for (auto& e : ge->events) KCHECK(h, cudaEventCreate(&e), "cudaEventCreate");
+                h->last_graph = ge.get();
+                h->graphs.emplace(std::make_pair(0.0, int64_t(0)), std::move(ge));
+            }
+            cudaEventRecord(h->last_graph->events[0], s);
+        }
+        k_batch_rk4<<<unsigned(std::min(nsm, B.n_traj)), BATCH_THREADS, smem, s>>>(bd, step, n_steps);
+        if (h->timing) cudaEventRecord(h->last_graph->events[1], s);
+    }
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->y.as<double>(), io);
+    KCHECK(h, cudaGetLastError(), "launching the batched integrator");
+    if (host) {
+        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
+    }
+    return KURA_OK;
+}
+
+kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, void* stream,
+                              kura_t* out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
+    *out = nullptr;
+    if (n_traj <= 0 || !graphs) { g_create_error = "n_traj must be positive and graphs non-NULL"; return KURA_EINVAL; }
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != KURA_PREC_MIXED) { g_create_error = "batches run in KURA_PREC_MIXED"; return KURA_EINVAL; }
+    if (o.scaling != KURA_SCALING_UNIFORM) { g_create_error = "batches use uniform scaling"; return KURA_EINVAL; }
+    std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
+    if (!h) return KURA_ENOMEM;
+    h->batch.reset(new BatchData());
+    BatchData& B = *h->batch;
+    B.n_traj = n_traj;
+    std::vector<BatchTraj> traj(static_cast<size_t>(n_traj));
+    std::vector<int32_t> comm_off, dptr, dcol, row_off, row_nm, perm_g;
+    std::vector<uint16_t> node_comm, entries;
+    std::vector<double> om;
+    std::vector<double> cost(static_cast<size_t>(n_traj));
+    int64_t node_off = 0;
+    for (int32_t t = 0; t < n_traj; t++) {
+        const kura_graph_desc& gd = graphs[t];
+        if (gd.n < 1 || gd.n > BATCH_MAX_N || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega ||
+            !std::isfinite(gd.K)) {
+            g_create_error = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(BATCH_MAX_N) +
+                             ", 1 <= n_comm <= " + std::to_string(BATCH_MAX_COMM) + ", omega and finite K";
+            return KURA_EINVAL;
+        }
+        Plan p;
+        const bool complete = gd.row_ptr == nullptr;    // all-to-all: one dense community, nothing stored
+        if (complete) {
+            if (gd.n_comm != 1) { g_create_error = "a complete-graph trajectory has n_comm = 1"; return KURA_EINVAL; }
+            p.n = gd.n;
+            p.n_comm = 1;
+            p.perm.resize(size_t(gd.n));
+            for (int64_t v = 0; v < gd.n; v++) p.perm[size_t(v)] = int32_t(v);
+            p.comm_off = {0, gd.n};
+            p.node_comm.assign(size_t(gd.n), 0);
+            p.dptr = {0, 1};
+            p.dcol = {0};
+            p.row_sub0.assign(size_t(gd.n) + 1, 0);      // no sub-rows: no stored corrections
+        } else {
+            PlanInput in;
+            in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
+            in.tau = o.tau;
+            in.tile_max_rows = TILE_MAX_ROWS;
+            in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
+            in.slot_ints = slot_ints_for(MODE_MIXED);
+            std::string err;
+            int rc = build_plan(in, p, err);
+            if (rc) { g_create_error = "trajectory " + std::to_string(t) + ": " + err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+        }
+        BatchTraj& tr = traj[size_t(t)];
+        tr.node_off = node_off;
+        tr.entry_off = int64_t(entries.size());
+        tr.n = int32_t(gd.n);
+        tr.n_comm = gd.n_comm;
+        tr.comm_base = int32_t(comm_off.size());
+        tr.dense_base = int32_t(dptr.size());
+        tr.scale = gd.K / double(gd.n);
+        int k = 0;
+        while ((int64_t(1) << k) < std::max<int64_t>(gd.n, 2)) k++;
+        tr.q_bits = 61 - k;
+        for (int64_t v : p.comm_off) comm_off.push_back(int32_t(v));
+        const int32_t dbase = int32_t(dcol.size());
+        for (int64_t v : p.dptr) dptr.push_back(int32_t(v) + dbase);
+        for (int32_t v : p.dcol) dcol.push_back(v);
+        for (int64_t v = 0; v < gd.n; v++) {
+            node_comm.push_back(uint16_t(p.node_comm[size_t(v)]));
+            perm_g.push_back(int32_t(node_off + p.perm[size_t(v)]));
+            om.push_back(gd.omega[p.perm[size_t(v)]]);
+        }
+        // per row: [missing | present] local indices
+        int32_t pos = 0;
+        for (int64_t v = 0; v < gd.n; v++) {
+            row_off.push_back(pos);
+            int32_t nm = 0;
+            std::vector<int32_t> pres;
+            for (int32_t sg = p.row_sub0[size_t(v)]; sg < p.row_sub0[size_t(v) + 1]; sg++) {
+                const int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
+                for (int32_t q = 0; q < hdr[1]; q++) { entries.push_back(uint16_t(p.gstream[size_t(p.sub_mpos[size_t(sg)] + q)])); nm++; }
+                for (int32_t q = 0; q < hdr[3]; q++) pres.push_back(p.gstream[size_t(p.sub_ppos[size_t(sg)] + q)]);
+            }
+            for (int32_t c : pres) entries.push_back(uint16_t(c));
+            row_nm.push_back(nm);
+            pos += nm + int32_t(pres.size());
+            B.missing += nm;
+            B.present += int64_t(pres.size());
+        }
+        row_off.push_back(pos);
+        cost[size_t(t)] = double(gd.n) * 24.0 + double(pos);
+        node_off += gd.n;
+    }
+    B.n_total = node_off;
+    B.entries = int64_t(entries.size());
+    std::vector<int32_t> order(static_cast<size_t>(n_traj));
+    for (int32_t t = 0; t < n_traj; t++) order[size_t(t)] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[size_t(a)] > cost[size_t(b)]; });
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+        return KURA_ECUDA;
+    }
+    cudaGetDevice(&h->device);
+    h->opts = o;
+    h->n = node_off;
+    h->n_comm = 0;
+    h->stream = static_cast<cudaStream_t>(stream);
+    const size_t smem = size_t(BATCH_MAX_N) * 8 + size_t(2 * BATCH_MAX_COMM) * 8 + size_t(BATCH_MAX_COMM) * 16;
+    cudaStream_t s = h->stream;
+    kura_ctx* hc = h.get();
+#define BCHECK(call, what)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            g_create_error = std::string(what) + ": " + cudaGetErrorString(e_);         \
+            return e_ == cudaErrorMemoryAllocation ? KURA_ENOMEM : KURA_ECUDA;          \
+        }                                                                               \
+    } while (0)
+    BCHECK(cudaFuncSetAttribute((const void*)k_batch_rk4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+           "shared memory size");
+    BCHECK(upload(B.traj, traj, s), "upload trajectories");
+    BCHECK(upload(B.order, order, s), "upload order");
+    BCHECK(upload(B.comm_off, comm_off, s), "upload community offsets");
+    BCHECK(upload(B.dptr, dptr, s), "upload dense pointers");
+    BCHECK(upload(B.dcol, dcol, s), "upload dense blocks");
+    BCHECK(upload(B.node_comm, node_comm, s), "upload node communities");
+    BCHECK(upload(B.row_off, row_off, s), "upload row offsets");
+    BCHECK(upload(B.row_nm, row_nm, s), "upload row missing counts");
+    BCHECK(upload(B.entries_d, entries, s), "upload corrections");
+    BCHECK(upload(hc->omega, om, s), "upload omega");
+    BCHECK(upload(hc->perm, perm_g, s), "upload permutation");
+    BCHECK(B.queue.alloc(16), "alloc queue");
+    BCHECK(B.stash.alloc(8 * size_t(node_off)), "alloc stash");
+    for (DevMem* d : {&hc->y, &hc->Y, &hc->krk, &hc->user}) BCHECK(d->alloc(8 * size_t(node_off)), "alloc state");
+    BCHECK(hc->err_flags.alloc(16), "alloc error flags");
+    BCHECK(cudaMemsetAsync(hc->err_flags.p, 0, 16, s), "memset error flags");
+    BCHECK(cudaStreamCreateWithFlags(&hc->cap, cudaStreamNonBlocking), "stream");
+    BCHECK(cudaStreamSynchronize(s), "upload");
+#undef BCHECK
+    *out = h.release();
+    return KURA_OK;
+}
+
+kura_status kura_batch_stats(kura_t h, int64_t* n_total, int64_t* missing, int64_t* present)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!h->batch) return h->fail(KURA_ESTATE, "not a batch handle");
+    if (n_total) *n_total = h->batch->n_total;
+    if (missing) *missing = h->batch->missing;
+    if (present) *present = h->batch->present;
     return KURA_OK;
 }
 

@@ -213,3 +213,32 @@ def workload_sbm_large(n: int = 1 << 20, n_comm: int = 1024, min_size: int = 256
     g = sbm(seed, sizes, p_in, p_out)
     return Workload(f"sbm-{n}", g, cauchy(seed, 0, n, 0.0, 0.5, 10.0), uniform(seed, 1, n, 0.0, 2 * np.pi),
                     3.0, 0.01, 500)
+
+
+def workload_batch(n_traj: int = 2048, seed: int = 0, n_min: int = 256, n_max: int = 16384):
+    """Ensemble of independent trajectories: sizes log-uniform in [n_min, n_max], even-indexed complete
+    graphs (returned as None: the all-to-all graph needs no adjacency) and odd-indexed SBMs (8-32
+    communities, p_in 0.9, p_out 0.005, Dirichlet(2) sizes with a floor of min(16, n / (2 C))); per
+    trajectory omega ~ N(0,1), theta0 ~ U[0, 2pi), K ~ U[0.5, 5].  Returns a list of (graph or None, n,
+    omega, theta0, K)."""
+    u = uniform(seed, 11, n_traj)
+    sizes_n = np.floor(np.exp(np.log(n_min) + u * (np.log(n_max) - np.log(n_min)))).astype(np.int64)
+    Ks = uniform(seed, 12, n_traj, 0.5, 5.0)
+    ncs = np.floor(8 + uniform(seed, 13, n_traj) * 25).astype(np.int64)        # 8..32
+    out = []
+    for t in range(n_traj):
+        n = int(sizes_n[t])
+        if t % 2 == 0:
+            g = None
+        else:
+            c = int(min(ncs[t], max(1, n // 16)))
+            mn = int(min(16, n // (2 * c)))
+            g = sbm(seed + 1000 + t, dirichlet_sizes(seed + 1000 + t, n, c, 2, mn, 0), 0.9, 0.005)
+        out.append((g, n, normal(seed + t, 21, n), uniform(seed + t, 22, n, 0.0, 2 * np.pi), float(Ks[t])))
+    return out
+
+
+def batch_graphs(ens):
+    """(row_ptr, col, label, n_comm, omega, K) tuples of an ensemble for the batch API."""
+    return [((None, None, None, 1, om, K) if g is None else (g.row_ptr, g.col, g.label, g.n_comm, om, K))
+            for (g, n, om, th, K) in ens]

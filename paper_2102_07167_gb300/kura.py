@@ -59,6 +59,11 @@ class KuraBlockStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class KuraGraphDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("label", C.c_void_p),
+                ("n_comm", C.c_int32), ("omega", C.c_void_p), ("K", C.c_double)]
+
+
 def header_functions() -> list:
     """Names of the functions declared in include/kura.h."""
     txt = open(HEADER).read()
@@ -98,6 +103,8 @@ def load() -> C.CDLL:
             "kura_destroy": (None, [P]),
             "kura_order_params_static": (S, [I64, P, P, I32, P, P]),
             "kura_plan_build": (S, [I64, P, P, P, I32, C.POINTER(KuraOpts), C.POINTER(P)]),
+            "kura_batch_create": (S, [I32, C.POINTER(KuraGraphDesc), C.POINTER(KuraOpts), P, C.POINTER(P)]),
+            "kura_batch_stats": (S, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
             "kura_plan_perm": (S, [P, P, P]),
             "kura_plan_row": (S, [P, I64, P, C.POINTER(I64), P, C.POINTER(I64), I64]),
@@ -179,6 +186,39 @@ def kura_create(n, row_ptr, col, label, n_comm, omega, K, opts: Optional[KuraOpt
                             C.byref(opts) if opts is not None else None, s or None, C.byref(h))
     _check(rc, None)
     return h
+
+
+def kura_batch_create(graphs, opts: Optional[KuraOpts] = None, stream=None):
+    """graphs: sequence of (row_ptr, col, label, n_comm, omega, K).  Returns (handle, node offsets)."""
+    keep, descs, offs = [], [], [0]
+    for (row_ptr, col, label, n_comm, omega, K) in graphs:
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        n = om.size
+        keep.append(om)
+        if row_ptr is None:                      # complete graph: no adjacency passed
+            descs.append(KuraGraphDesc(n, None, None, None, 1, om.ctypes.data, float(K)))
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            lb = np.ascontiguousarray(label, dtype=np.int32)
+            keep += [rp, cl, lb]
+            descs.append(KuraGraphDesc(n, rp.ctypes.data, cl.ctypes.data if cl.size else None, lb.ctypes.data,
+                                       int(n_comm), om.ctypes.data, float(K)))
+        offs.append(offs[-1] + n)
+    arr = (KuraGraphDesc * len(descs))(*descs)
+    h = C.c_void_p()
+    if opts is None:
+        opts = kura_default_opts()
+        opts.precision = PREC_MIXED
+    s = _current_stream() if stream is None else int(stream)
+    _check(load().kura_batch_create(len(descs), arr, C.byref(opts), s or None, C.byref(h)), None)
+    return h, np.array(offs, dtype=np.int64)
+
+
+def kura_batch_stats(h):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().kura_batch_stats(h, C.byref(a), C.byref(b), C.byref(c)), h)
+    return {"n_total": a.value, "missing_entries": b.value, "sparse_entries": c.value}
 
 
 def kura_classify_blocks(h, tau: float = -1.0) -> dict:
@@ -396,6 +436,49 @@ class Kuramoto:
         kura_set_timing(self.h, on)
 
     def kernel_times(self, cap=4096):
+        return kura_kernel_times(self.h, cap)
+
+    def sync(self):
+        kura_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kura_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KuramotoBatch:
+    """A batch handle: independent trajectories (own graph, omega, K) integrated by one persistent launch.
+    Phases are passed concatenated in trajectory order; `offsets[t]:offsets[t+1]` is trajectory t."""
+
+    def __init__(self, graphs, tau=0.5, stream=None):
+        o = kura_default_opts()
+        o.precision, o.tau = PREC_MIXED, float(tau)
+        self.h, self.offsets = kura_batch_create(graphs, o, stream)
+        self.n = int(self.offsets[-1])
+
+    def rk4_steps(self, theta, step, n_steps):
+        kura_rk4_steps(self.h, theta, step, n_steps, self.n)
+
+    def stats(self):
+        return kura_batch_stats(self.h)
+
+    def set_timing(self, on=True):
+        kura_set_timing(self.h, on)
+
+    def kernel_times(self, cap=16):
         return kura_kernel_times(self.h, cap)
 
     def sync(self):
