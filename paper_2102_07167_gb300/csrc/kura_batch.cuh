@@ -74,21 +74,54 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch_rk4(BatchDev b, doub
         __syncthreads();
         for (int64_t step = 0; step < n_steps; step++) {
             for (int st = 1; st <= 4; st++) {
-                // ---- (sin, cos) table and fixed-point block sums
+                // ---- (sin, cos) table and fixed-point block sums: lane 0 of each warp keeps a running
+                // sum of its community run (communities are contiguous) and flushes it with one atomic
                 const double* th_in = (st == 1) ? b.y + o : b.Y + o;
-                for (int i = tid; i < n; i += BATCH_THREADS) {
-                    const double th = th_in[i];
-                    if (!isfinite(th)) atomicOr(b.err, 1);
-                    const double kk = rint(th * 0.15915494309189533577);
-                    double r = fma(-kk, 6.283185307179586232, th);
-                    r = fma(-kk, 2.4492935982947064e-16, r);
-                    float s, c;
-                    sincosf(static_cast<float>(r), &s, &c);
-                    tab[i] = make_float2(s, c);
-                    const int J = b.node_comm[o + i];
-                    const float fq = static_cast<float>(sq);
-                    atomicAdd(&S[2 * J], static_cast<unsigned long long>(__float2ll_rn(s * fq)));
-                    atomicAdd(&S[2 * J + 1], static_cast<unsigned long long>(__float2ll_rn(c * fq)));
+                const float fq = static_cast<float>(sq);
+                long long run_s = 0, run_c = 0;
+                int run_J = -1;
+                for (int base = warp * 32; base < n; base += BATCH_THREADS) {
+                    const int i = base + lane;
+                    long long sf = 0, cf = 0;
+                    int J = -1;
+                    if (i < n) {
+                        const double th = th_in[i];
+                        if (!isfinite(th)) atomicOr(b.err, 1);
+                        const double kk = rint(th * 0.15915494309189533577);
+                        double r = fma(-kk, 6.283185307179586232, th);
+                        r = fma(-kk, 2.4492935982947064e-16, r);
+                        float s, c;
+                        sincosf(static_cast<float>(r), &s, &c);
+                        tab[i] = make_float2(s, c);
+                        J = b.node_comm[o + i];
+                        sf = __float2ll_rn(s * fq);
+                        cf = __float2ll_rn(c * fq);
+                    }
+                    const int J0 = __shfl_sync(0xffffffffu, J, 0);
+                    if (__all_sync(0xffffffffu, J == J0 || J < 0)) {
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) {
+                            sf += __shfl_xor_sync(0xffffffffu, sf, off);
+                            cf += __shfl_xor_sync(0xffffffffu, cf, off);
+                        }
+                        if (lane == 0) {
+                            if (J0 != run_J && run_J >= 0) {
+                                atomicAdd(&S[2 * run_J], static_cast<unsigned long long>(run_s));
+                                atomicAdd(&S[2 * run_J + 1], static_cast<unsigned long long>(run_c));
+                                run_s = run_c = 0;
+                            }
+                            run_J = J0;
+                            run_s += sf;
+                            run_c += cf;
+                        }
+                    } else if (J >= 0) {
+                        atomicAdd(&S[2 * J], static_cast<unsigned long long>(sf));
+                        atomicAdd(&S[2 * J + 1], static_cast<unsigned long long>(cf));
+                    }
+                }
+                if (lane == 0 && run_J >= 0) {
+                    atomicAdd(&S[2 * run_J], static_cast<unsigned long long>(run_s));
+                    atomicAdd(&S[2 * run_J + 1], static_cast<unsigned long long>(run_c));
                 }
                 __syncthreads();
                 for (int I = tid; I < nc; I += BATCH_THREADS) {
@@ -105,13 +138,24 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch_rk4(BatchDev b, doub
                 // ---- rows: a warp per row gathers its corrections from the shared table
                 const int32_t* roff = b.row_off + o + cur;            // n + 1 offsets per trajectory
                 for (int r = warp; r < n; r += NW) {
-                    const int beg = roff[r], end = roff[r + 1], nm = b.row_nm[o + r];
+                    const int beg = __ldg(roff + r), end = __ldg(roff + r + 1), nm = __ldg(b.row_nm + o + r);
                     float as = 0.f, ac = 0.f;
                     const uint16_t* e = b.entries + tr.entry_off;
-                    for (int k = beg + lane; k < end; k += 32) {
-                        const float2 v = tab[e[k]];
-                        if (k - beg < nm) { as -= v.x; ac -= v.y; }
-                        else              { as += v.x; ac += v.y; }
+                    for (int k0 = beg; k0 < end; k0 += 128) {      // up to 128 index loads in flight per row
+                        int idx[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int k = k0 + 32 * q + lane;
+                            idx[q] = (k < end) ? int(__ldg(e + k)) : -1;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            if (idx[q] >= 0) {
+                                const float2 v = tab[idx[q]];
+                                if (k0 + 32 * q + lane - beg < nm) { as -= v.x; ac -= v.y; }
+                                else                               { as += v.x; ac += v.y; }
+                            }
+                        }
                     }
 #pragma unroll
                     for (int off = 16; off; off >>= 1) {
