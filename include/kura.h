@@ -74,10 +74,17 @@ typedef struct {
     /* keep a host copy of the CSR (needed by kura_classify_blocks with a new
      * tau and by the direct-summation baseline); default 1 */
     int32_t keep_host_csr;
-    int32_t reserved0;
-    /* index encoding of a community's dense-block zeros: a bitmap over the
-     * staged window when their fraction exceeds this, else an index list;
-     * negative (default): always index lists */
+    /* tensor-core encoding of a community's dense-block zeros: a 0/1 mask over
+     * 128-column blocks multiplied on the tensor cores (tcgen05, FP8 operands)
+     * by the base-16 digits of the fixed-point (sin, cos) of those columns, so
+     * that the subtracted sums are exact in fixed point.  Requires that the
+     * community's dense columns span at most 4096 columns.  0: never; 1
+     * (default): when the mask takes fewer bytes than the index lists; 2:
+     * whenever possible. */
+    int32_t tensor_cores;
+    /* index encoding of a community's dense-block zeros (when not on the
+     * tensor cores): a bitmap over the staged window when their fraction
+     * exceeds this, else an index list; negative (default): index lists */
     double bitmap_zmin;
     int32_t reserved[4];
 } kura_opts;
@@ -97,9 +104,12 @@ typedef struct {
      * stage; node_bytes_trig = per-node traffic of the trig/block-sum kernel. */
     int64_t stream_bytes, node_bytes_row, node_bytes_trig;
     int64_t direct_edges;            /* edges summed by the direct baseline */
+    int64_t tc_tiles, tc_rows;       /* tiles (and their rows) whose zeros are a tensor-core mask */
+    int64_t tc_mask_bits;            /* mask bits of those tiles (128 x 128 blocks) */
 } kura_block_stats;
 
-/* Fills *opts with the defaults (FP64, uniform scaling, tau 0.5, host CSR kept). */
+/* Fills *opts with the defaults (FP64, uniform scaling, tau 0.5, host CSR kept,
+ * tensor cores when smaller). */
 void kura_default_opts(kura_opts* opts);
 
 /* Library version (major*10000 + minor*100 + patch). */

@@ -91,12 +91,15 @@ struct kura_ctx {
     std::vector<double> h_omega;        // user order
     Plan plan;                          // host plan (streams released after upload)
     int64_t miss_total = 0, pres_total = 0, nnz = 0, stream_bytes = 0, bitmap_rows = 0;
+    int64_t tc_tiles = 0, tc_rows = 0, tc_mask_bits = 0;
+    bool has_tc = false;                // some tile runs on the tensor cores (digit image kept up to date)
+    int32_t bm_stash_off = 0;
     // device buffers
-    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off;
+    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig;
     DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
-        ad_tgt, ad_scratch;
+        ad_tgt, ad_scratch, ad_absmax;
     int64_t ad_M = 0, ad_nck = 0;
     int sym = -1;   // host CSR symmetric? (-1 unknown)
     DevMem y, Y, krk, fbuf, user, red, order_out;
@@ -177,6 +180,8 @@ DevGraph dev_graph(kura_ctx* h)
     g.tiles = h->tiles.as<Tile>();
     g.row_sub0 = h->row_sub0.as<int32_t>();
     g.bitmap = h->bitmap.as<uint32_t>();
+    g.dig = h->has_tc ? h->dig.as<uint8_t>() : nullptr;
+    g.bm_stash_off = h->bm_stash_off;
     g.dptr = h->dptr.as<int64_t>();
     g.dcol = h->dcol.as<int32_t>();
     g.comm_off = h->comm_off.as<int64_t>();
@@ -263,14 +268,19 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
 }
 
 // Bytes of the correction data one right-hand side reads: the listed indices
-// (4 B each), the sub-row headers (16 B each) and the row bitmaps.
+// (4 B each), the sub-row headers (16 B each), the row bitmaps, and for
+// tensor-core tiles their mask bits and the digit blocks of their K-blocks.
 int64_t plan_stream_bytes(const Plan& p)
 {
     int64_t listed = 0;
     for (const Group& G : p.groups) listed += G.len - 4 * int64_t(G.nsub);   // includes segment padding
     int64_t bm = 0;
-    for (const Tile& t : p.tiles)
+    for (const Tile& t : p.tiles) {
         if (t.flags & TILE_BITMAP) bm += int64_t(t.r1 - t.r0) * t.nsw * 128;
+        if (t.flags & TILE_TC)
+            bm += int64_t((t.r1 - t.r0 + TC_MBLOCK - 1) / TC_MBLOCK) * t.nsw * TC_MBLOCK * 16 +
+                  int64_t(t.nsw) * TC_BBYTES;
+    }
     return 4 * listed + 16 * int64_t(p.row_sub0.empty() ? 0 : p.row_sub0.back()) + bm;
 }
 
@@ -284,12 +294,21 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     h->miss_total = p.miss_total;
     h->pres_total = p.pres_total;
     h->bitmap_rows = p.bitmap_rows;
+    h->tc_tiles = p.tc_tiles;
+    h->tc_rows = p.tc_rows;
+    h->tc_mask_bits = p.tc_mask_bits;
+    h->has_tc = p.tc_tiles > 0;
     h->stream_bytes = plan_stream_bytes(p);
     h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2));
+    const int mode = h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
     const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
-    const int slot = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
-    const int nslots = slots_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
-    h->row_smem = size_t(nslots) * size_t(slot) * 4 + 16 + size_t(std::max(p.max_wlen, 2)) * esize;
+    // dynamic shared memory: the ring, then either [16 B | window | bitmap-pass
+    // stash] or the tensor-core operand stages
+    const size_t win_end = size_t(ring_bytes_for(mode)) + 16 + ((size_t(std::max(p.max_wlen, 2)) * esize + 15) & ~size_t(15));
+    h->bm_stash_off = int32_t(win_end);
+    size_t need = p.bitmap_rows > 0 ? win_end + size_t(TILE_MAX_ROWS) * 2 * (esize / 2) : win_end;
+    if (h->has_tc) need = std::max(need, size_t(ring_bytes_for(mode)) + size_t(TC_SMEM));
+    h->row_smem = need;
     KCHECK(h, (h->opts.precision == KURA_PREC_MIXED ? set_row_attrs<MODE_MIXED>(h->row_smem)
                                                     : set_row_attrs<MODE_FP64>(h->row_smem)),
            "setting the row kernel's shared-memory size");
@@ -324,6 +343,13 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     const size_t n = size_t(h->n), nc = size_t(h->n_comm);
     KCHECK(h, h->table.alloc(esize * (n + 2)), "alloc table");
     KCHECK(h, cudaMemsetAsync(h->table.p, 0, h->table.bytes, s), "memset table");
+    if (h->has_tc) {
+        // digit image: one 4 KB block per 128 nodes; columns past n stay zero
+        KCHECK(h, h->dig.alloc(size_t((h->n + TC_KBLOCK - 1) / TC_KBLOCK) * TC_BBYTES), "alloc digit image");
+        KCHECK(h, cudaMemsetAsync(h->dig.p, 0, h->dig.bytes, s), "memset digit image");
+    } else {
+        h->dig.release();
+    }
     KCHECK(h, h->bsum.alloc(16 * nc), "alloc bsum");
     KCHECK(h, cudaMemsetAsync(h->bsum.p, 0, h->bsum.bytes, s), "memset bsum");
     KCHECK(h, h->bsum_out.alloc(16 * nc), "alloc bsum_out");
@@ -403,6 +429,7 @@ void kura_default_opts(kura_opts* o)
     o->scaling = KURA_SCALING_UNIFORM;
     o->tau = 0.5;
     o->keep_host_csr = 1;
+    o->tensor_cores = 1;
     o->bitmap_zmin = -1.0;
 }
 
@@ -448,6 +475,7 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
     in.slot_ints = slot_ints_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     in.entry_bytes = o.precision == KURA_PREC_MIXED ? 8 : 16;
     in.bitmap_zmin = o.bitmap_zmin;
+    in.tensor_cores = o.tensor_cores;
     Plan plan;
     std::string err;
     int rc = build_plan(in, plan, err);
@@ -512,6 +540,9 @@ kura_status kura_get_stats(kura_t h, kura_block_stats* s)
     // trig kernel per node: theta read, table write, community id
     s->node_bytes_trig = (8 + esize + 4) * h->n;
     s->direct_edges = h->nnz - p.self_loops;
+    s->tc_tiles = h->tc_tiles;
+    s->tc_rows = h->tc_rows;
+    s->tc_mask_bits = h->tc_mask_bits;
     return KURA_OK;
 }
 
@@ -530,6 +561,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         in.slot_ints = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
         in.entry_bytes = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
         in.bitmap_zmin = h->opts.bitmap_zmin;
+        in.tensor_cores = h->opts.tensor_cores;
         Plan plan;
         std::string err;
         int rc = build_plan(in, plan, err);
@@ -873,6 +905,7 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         KCHECK(h, h->ad_bs.alloc(16 * size_t(h->n_comm)), "alloc block sums");
         KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(h->n_tiles, 1))), "alloc dK accumulators");
         KCHECK(h, h->ad_part.alloc(8 * ((n + 255) / 256)), "alloc loss partials");
+        KCHECK(h, h->ad_absmax.alloc(16), "alloc table maximum");
         h->ad_M = M;
         h->ad_nck = nck;
     }
@@ -939,9 +972,12 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
             for (int st = 4; st >= 1; st--) {
                 double* a_next = (st < 4) ? ((st % 2 == 1) ? h->ad_a0.as<double>() : h->ad_a1.as<double>()) : nullptr;
                 double* a_out = (st % 2 == 0) ? h->ad_a0.as<double>() : h->ad_a1.as<double>();
+                unsigned int* absmax = h->has_tc ? h->ad_absmax.as<unsigned int>() : nullptr;
+                if (absmax) KCHECK(h, cudaMemsetAsync(absmax, 0, sizeof(unsigned int), s), "zero the table maximum");
                 k_adj_prep<<<nb, 256, 0, s>>>(g, Ybuf + size_t(4 * t + st - 1) * n, lam, a_next, cl[st], ca[st],
                                               h->ad_w.as<double>(), h->ad_nu.as<double>(), h->ad_sc.as<float2>(),
-                                              h->ad_gom.as<double>());
+                                              h->ad_gom.as<double>(), absmax);
+                if (absmax) k_adj_digits<<<nb, 256, 0, s>>>(g, absmax);
                 k_adj_blocksum<<<unsigned(std::max(h->n_comm, 1)), 256, 0, s>>>(g, h->ad_bs.as<double2>());
                 k_adj_T<<<blocks_for(std::max(h->n_comm, 1), 256), 256, 0, s>>>(g, h->ad_bs.as<double2>());
                 AdjArgs adj{};
@@ -953,6 +989,7 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                 adj.asum = h->ad_asum.as<double>();
                 adj.lam = lam;
                 adj.gk_acc = h->ad_gk.as<double>();
+                adj.absmax = absmax;
                 adj.stage = st;
                 RkArgs rk{};
                 launch_row<MODE_MIXED, ST_ADJ>(h, g, rk, s, adj);
@@ -1105,6 +1142,7 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             in.tile_max_rows = TILE_MAX_ROWS;
             in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
             in.slot_ints = slot_ints_for(MODE_MIXED);
+            in.tensor_cores = 0;          // the batch kernel reads index lists
             std::string err;
             int rc = build_plan(in, p, err);
             if (rc) { g_create_error = "trajectory " + std::to_string(t) + ": " + err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
@@ -1261,6 +1299,7 @@ kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* co
     in.slot_ints = slot_ints_for(mode);
     in.entry_bytes = mode == MODE_MIXED ? 8 : 16;
     in.bitmap_zmin = o.bitmap_zmin;
+    in.tensor_cores = o.tensor_cores;
     std::string err;
     int rc = build_plan(in, p->p, err);
     if (rc) { g_create_error = err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
@@ -1291,6 +1330,9 @@ kura_status kura_plan_stats(kura_plan_t pl, kura_block_stats* s)
     s->node_bytes_row = (8 + 8 + 16 + 8 + 16) * p.n;
     s->node_bytes_trig = (8 + 16 + 4) * p.n;
     s->direct_edges = p.nnz_in - p.self_loops;
+    s->tc_tiles = p.tc_tiles;
+    s->tc_rows = p.tc_rows;
+    s->tc_mask_bits = p.tc_mask_bits;
     return KURA_OK;
 }
 
@@ -1319,6 +1361,17 @@ kura_status kura_plan_row(kura_plan_t pl, int64_t row, int32_t* missing, int64_t
                 if (missing && km < cap) missing[km] = int32_t(T.wbeg + k);
                 km++;
             }
+    }
+    if (T.flags & TILE_TC) {
+        const int64_t lr = row - T.r0, nM = (T.r1 - T.r0 + TC_MBLOCK - 1) / TC_MBLOCK;
+        for (int64_t kb = 0; kb < T.nsw; kb++) {
+            const uint32_t* w = p.bitmap.data() + T.bm_off + ((kb * nM + lr / TC_MBLOCK) * TC_MBLOCK + lr % TC_MBLOCK) * 4;
+            for (int64_t c = 0; c < TC_KBLOCK; c++)
+                if ((w[c >> 5] >> (c & 31)) & 1u) {
+                    if (missing && km < cap) missing[km] = int32_t(T.wbeg + kb * TC_KBLOCK + c);
+                    km++;
+                }
+        }
     }
     for (int32_t sg = p.row_sub0[size_t(row)]; sg < p.row_sub0[size_t(row) + 1]; sg++) {
         const int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];

@@ -10,6 +10,7 @@
 //                    and the RK4 stage update, fused
 #pragma once
 #include <cstdint>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "plan.hpp"
@@ -17,16 +18,38 @@
 namespace kura {
 
 constexpr int ROW_CONSUMERS = 16;                       // consumer warps of the row kernel
-constexpr int ROW_THREADS = (ROW_CONSUMERS + 1) * 32;   // + one producer warp
+constexpr int ROW_THREADS = (ROW_CONSUMERS + 2) * 32;   // + a producer warp and a tensor-core warp
 constexpr int TILE_MAX_ROWS = 512;      // rows per tile (the planner's bound)
 constexpr int BM_ROWS = 4;              // rows per warp in the bitmap pass
 constexpr int TRIG_THREADS = 256;
 // slot capacity (int32 units) per precision mode: keeps two CTAs resident per SM
 // Per precision mode (FP64 entries are 16 bytes, mixed 8): ring slots, slot
 // capacity (int32 units) and sub-rows per tile -- two CTAs stay resident per SM.
-__host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 4096; }
+__host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 3072; }
 __host__ __device__ constexpr int slots_for(int mode) { return mode == 0 ? 3 : 4; }
 __host__ __device__ constexpr int tile_max_sub_for(int mode) { return mode == 0 ? 512 : 768; }
+__host__ __device__ constexpr int ring_bytes_for(int mode) { return slots_for(mode) * slot_ints_for(mode) * 4; }
+
+// Tensor-core tiles (TILE_TC): A = 0/1 mask, 128 rows x 128 columns in FP8
+// (E4M3), B = 32 digit rows x 128 columns in FP8: rows 0-15 the balanced
+// base-16 digits of the fixed-point sin of each column, rows 16-31 those of
+// the cosine.  Both K-major with the 128-byte swizzle; D = 128 x 32 FP32 in
+// tensor memory per M-block (exact: every product is a small integer and
+// every partial sum stays below 2^24).
+constexpr int TC_NA = 2;                                  // mask stages (one per team of 8 warps)
+constexpr int TC_NB = 2;                                  // digit stages
+constexpr int TC_NDIG = 16;                               // digits per value
+constexpr int TC_ABYTES = TC_MBLOCK * TC_KBLOCK;          // 16384
+constexpr int TC_BBYTES = 2 * TC_NDIG * TC_KBLOCK;        // 4096: one 128-column block of the digit image
+constexpr int TC_SMEM = 1024 + TC_NA * TC_ABYTES + TC_NB * TC_BBYTES;   // + slack for 1024-byte alignment
+constexpr int TC_TMEM_COLS = 4 * 2 * TC_NDIG;             // 4 M-blocks x 32 columns
+// instruction descriptor of tcgen05.mma.kind::f8f6f4: D F32 (bits 4-5 = 1),
+// A and B E4M3 (bits 7-9, 10-12 = 0), both K-major, N = 32 (bits 17-22 = N/8),
+// M = 128 (bits 24-28 = M/16)
+constexpr uint32_t TC_IDESC = (1u << 4) | (uint32_t(2 * TC_NDIG / 8) << 17) | (uint32_t(TC_MBLOCK / 16) << 24);
+// byte of digit row d, column c (0..127) in a 4096-byte block of the digit
+// image: the 128-byte swizzle permutes the 16-byte chunks of row d by d mod 8
+__host__ __device__ constexpr int tc_digit_offset(int d, int c) { return d * 128 + ((((c >> 4) ^ (d & 7)) << 4) | (c & 15)); }
 
 enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
 enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4, ST_ADJ = 5 };
@@ -57,7 +80,9 @@ struct DevGraph {
     const Group* groups;
     const Tile* tiles;
     const int32_t* row_sub0;                // [n+1] first sub-row of each row
-    const uint32_t* bitmap;                 // row bitmaps of TILE_BITMAP tiles
+    const uint32_t* bitmap;                 // row bitmaps of TILE_BITMAP tiles, masks of TILE_TC tiles
+    uint8_t* dig;                           // digit image of the table (TILE_TC tiles; else null)
+    int32_t bm_stash_off;                   // byte offset of the bitmap-pass stash in dynamic shared memory
     const int64_t* dptr;                    // [n_comm+1]
     const int32_t* dcol;
     const int64_t* comm_off;                // [n_comm+1]
@@ -92,6 +117,7 @@ struct AdjArgs {
     double* asum;           // a_4 + a_3 + a_2 accumulated over the step
     double* lam;            // lambda; stage 1 adds a_1 + asum and clears asum
     double* gk_acc;         // per-CTA accumulators of dL/dK
+    const unsigned int* absmax;   // bits of max |table entry| (fixes the digit scale of TILE_TC tiles)
     int stage;
 };
 
@@ -139,6 +165,84 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// ---- tensor cores (tcgen05) and tensor memory
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor cores
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// whole warp: allocate ncols tensor-memory columns, address written to *dst
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride field), descriptor version 1
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr)
+{
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+// D[tmem] (+)= A[a] B[b]^T, issued by one thread
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive once on the mbarrier when every earlier tcgen05.mma of this thread has completed
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// whole warp: 16 consecutive 32-bit columns of the warp's 32 lanes
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+// sum_k D_k 16^k of exact-integer FP32 digit sums, in two's complement
+__device__ __forceinline__ long long tc_combine(const uint32_t (&d)[16])
+{
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int k = TC_NDIG - 1; k >= 0; k--)
+        acc = (acc << 4) + static_cast<unsigned long long>(__float2ll_rn(__uint_as_float(d[k])));
+    return static_cast<long long>(acc);
+}
+// balanced base-16 digits of the fixed-point (v_s, v_c) of node i into the digit image
+__device__ __forceinline__ void tc_write_digits(uint8_t* dig, int64_t i, long long vs, long long vc)
+{
+    uint8_t* blk = dig + (i >> 7) * TC_BBYTES;
+    const int c = int(i & 127);
+#pragma unroll
+    for (int k = 0; k < TC_NDIG; k++) {
+        const int ds = int((vs + 8) & 15) - 8, dc = int((vc + 8) & 15) - 8;
+        vs = (vs - ds) >> 4;
+        vc = (vc - dc) >> 4;
+        blk[tc_digit_offset(k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(ds), __NV_SATFINITE, __NV_E4M3);
+        blk[tc_digit_offset(TC_NDIG + k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(dc), __NV_SATFINITE, __NV_E4M3);
+    }
+}
+// digit scale 2^e of the adjoint table: |entry| 2^e < 2^42
+__device__ __forceinline__ int adj_digit_exp(unsigned int absmax_bits)
+{
+    const float m = __uint_as_float(absmax_bits);
+    return m > 0.0f ? 41 - ilogbf(m) : 0;
+}
+
 // Waits for the barrier phase with a time limit; false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
 {
@@ -184,6 +288,7 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
             if (WHAT & TB_TABLE) reinterpret_cast<float2*>(g.table)[i] = make_float2(s, c);
         }
         J = g.node_comm[i];
+        if ((WHAT & TB_TABLE) && g.dig) tc_write_digits(g.dig, i, sf, cf);
     }
     const unsigned full = 0xffffffffu;
     const int J0 = __shfl_sync(full, J, 0);
@@ -285,6 +390,15 @@ struct Acc2 {
 // The per-sub-row sums go to a stash; at the end every thread takes rows for
 // the FP64 epilogue: f = omega + scale (cos th acc_s - sin th acc_c), T_I
 // added, and the RK4 stage update.
+//
+// TILE_TC tiles list only present entries.  Their missing entries are a 0/1
+// mask: between row groups (and after the last) every consumer warp expands
+// its 8 rows of the next 128 x 128 mask block into an FP8 operand tile in
+// shared memory whenever a stage is free; warp ROW_CONSUMERS + 1 (one lane)
+// loads the matching digit blocks with TMA and issues tcgen05.mma into tensor
+// memory, one 128 x 32 accumulator per M-block of 128 rows.  The epilogue
+// reads the accumulators back and forms the exact fixed-point sum over the
+// missing entries of every row.
 template <int MODE, int STAGE>
 __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk, AdjArgs adj)
 {
@@ -292,22 +406,35 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     using A = typename EntryT<MODE>::A;
     constexpr int SLOT = slot_ints_for(MODE);
     constexpr int ROW_SLOTS = slots_for(MODE);
+    constexpr int RING_BYTES = ring_bytes_for(MODE);
+    constexpr int TC_WARP = ROW_CONSUMERS + 1;
     constexpr uint64_t LIMIT_NS = 1000000000ull;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[ROW_SLOTS], empty_bar[ROW_SLOTS], win_bar;
+    __shared__ __align__(8) uint64_t a_full[TC_NA], a_empty[TC_NA], b_full[TC_NB], b_empty[TC_NB], d_full;
     __shared__ Acc2<MODE> stash[tile_max_sub_for(MODE)];
-    __shared__ Acc2<MODE> bm_stash[TILE_MAX_ROWS];
     __shared__ int abort_flag;
-    __shared__ int issued[ROW_SLOTS];
+    __shared__ int issued[ROW_SLOTS], b_issued[TC_NB];
+    __shared__ int2 slot_meta[ROW_SLOTS];        // (first sub-row relative to the tile, sub-rows) of the slot's group
+    __shared__ uint32_t tmem_base;
 
     int32_t* ring = reinterpret_cast<int32_t*>(smem_raw);
     // window at win[0, wlen), preceded by 16 bytes holding a zero entry at win[-1]
-    E* win = reinterpret_cast<E*>(smem_raw + size_t(ROW_SLOTS) * SLOT * sizeof(int32_t) + 16);
+    E* win = reinterpret_cast<E*>(smem_raw + RING_BYTES + 16);
+    Acc2<MODE>* bm_stash = reinterpret_cast<Acc2<MODE>*>(smem_raw + g.bm_stash_off);
     const Tile t = g.tiles[blockIdx.x];
     const E* table = reinterpret_cast<const E*>(g.table);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ngroups = t.g1 - t.g0;
+    const int nrows = t.r1 - t.r0;
     const int zidx = int(g.n);                                // the table's zero entry
+    const bool tc = (t.flags & TILE_TC) != 0;
+    // tensor-core operand stages (TILE_TC tiles), 1024-byte aligned, after the ring
+    const uint32_t sbase = smem_u32(smem_raw);
+    const uint32_t tc_a = (sbase + uint32_t(RING_BYTES) + 1023u) & ~1023u;
+    const uint32_t tc_b = tc_a + uint32_t(TC_NA * TC_ABYTES);
+    unsigned char* tcA = smem_raw + (tc_a - sbase);
+    unsigned char* tcB = smem_raw + (tc_b - sbase);
 
     if (tid == 0) {
         abort_flag = 0;
@@ -321,8 +448,22 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             issued[sl] = 0;
         }
         mbar_init(&win_bar, 1);
+        for (int q = 0; q < TC_NA; q++) {
+            mbar_init(&a_full[q], ROW_CONSUMERS);   // one arrival per consumer warp
+            mbar_init(&a_empty[q], 1);              // tcgen05.commit
+        }
+        for (int q = 0; q < TC_NB; q++) {
+            mbar_init(&b_full[q], 1);
+            mbar_init(&b_empty[q], 1);
+            b_issued[q] = 0;
+        }
+        mbar_init(&d_full, 1);
     }
+    if (tc && warp == TC_WARP) tc_alloc(&tmem_base, TC_TMEM_COLS);
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tc ? tmem_base : 0u;
 
     if (warp == ROW_CONSUMERS) {
         // ---------------- producer
@@ -332,18 +473,63 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 mbar_arrive_expect_tx(&win_bar, bytes);
                 bulk_g2s(win, table + t.wbeg, bytes, &win_bar);
             }
+            Group Gn = ngroups > 0 ? g.groups[t.g0] : Group{};
             for (int gi = 0; gi < ngroups; gi++) {
                 const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
+                const Group G = Gn;
+                if (gi + 1 < ngroups) Gn = g.groups[t.g0 + gi + 1];      // next descriptor, loaded ahead
                 if (fill > 0 && !mbar_wait_bounded(&empty_bar[sl], uint32_t(fill - 1) & 1u, LIMIT_NS)) {
                     atomicOr(g.err, ERR_TIMEOUT);
                     atomicExch(&abort_flag, 1);
                     break;
                 }
-                const Group G = g.groups[t.g0 + gi];
+                // the group's placement travels with the slot (published by the arrive below)
+                slot_meta[sl] = make_int2(G.sub0 - t.sub0, G.nsub);
                 const uint32_t bytes = uint32_t(G.len) * 4u;
                 mbar_arrive_expect_tx(&full_bar[sl], bytes);
                 bulk_g2s(ring + size_t(sl) * SLOT, g.gstream + G.off, bytes, &full_bar[sl]);
                 issued[sl] = fill + 1;
+            }
+        }
+    } else if (warp == TC_WARP) {
+        // ---------------- tensor cores: lane 0 loads the digit blocks with TMA and
+        // issues the MMAs of mask block tt = kb * nM + m (stage tt mod TC_NA) once
+        // every consumer warp has expanded its 8 rows of it
+        if (tc && lane == 0) {
+            const int nM = (nrows + TC_MBLOCK - 1) / TC_MBLOCK, nkb = t.nsw, nT = nkb * nM;
+            const uint8_t* dsrc = g.dig + size_t(t.wbeg / TC_KBLOCK) * TC_BBYTES;
+            bool fail = false;
+            for (int kb = 0; kb < TC_NB && kb < nkb; kb++) {
+                mbar_arrive_expect_tx(&b_full[kb], TC_BBYTES);
+                bulk_g2s(tcB + kb * TC_BBYTES, dsrc + size_t(kb) * TC_BBYTES, TC_BBYTES, &b_full[kb]);
+                b_issued[kb] = 1;
+            }
+            for (int tt = 0; tt < nT && !fail; tt++) {
+                const int kb = tt / nM, m = tt % nM, st = tt % TC_NA, sb = kb % TC_NB;
+                if (m == 0 && !mbar_wait_bounded(&b_full[sb], uint32_t(kb / TC_NB) & 1u, LIMIT_NS)) { fail = true; break; }
+                if (!mbar_wait_bounded(&a_full[st], uint32_t(tt / TC_NA) & 1u, LIMIT_NS)) { fail = true; break; }
+                tc_fence_after();
+                const uint64_t da = tc_sdesc(tc_a + uint32_t(st * TC_ABYTES));
+                const uint64_t db = tc_sdesc(tc_b + uint32_t(sb * TC_BBYTES));
+#pragma unroll
+                for (int k = 0; k < TC_KBLOCK / 32; k++)       // K = 32 FP8 per MMA: 32 bytes along the row
+                    tc_mma(tmem + uint32_t(m * 2 * TC_NDIG), da + uint64_t(2 * k), db + uint64_t(2 * k), TC_IDESC,
+                           (kb | k) != 0 ? 1u : 0u);
+                tc_commit(&a_empty[st]);
+                if (m == nM - 1) tc_commit(&b_empty[sb]);
+                // refill the stage of block kb - 1 with block kb + 1 once its MMAs are done
+                if (m == 0 && kb >= 1 && kb + 1 < nkb) {
+                    const int pb = (kb - 1) % TC_NB;
+                    if (!mbar_wait_bounded(&b_empty[pb], uint32_t((kb - 1) / TC_NB) & 1u, LIMIT_NS)) { fail = true; break; }
+                    mbar_arrive_expect_tx(&b_full[pb], TC_BBYTES);
+                    bulk_g2s(tcB + pb * TC_BBYTES, dsrc + size_t(kb + 1) * TC_BBYTES, TC_BBYTES, &b_full[pb]);
+                    b_issued[pb] = (kb + 1) / TC_NB + 1;
+                }
+            }
+            tc_commit(&d_full);          // arrives once every MMA above has completed
+            if (fail) {
+                atomicOr(g.err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
             }
         }
     } else {
@@ -402,18 +588,96 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 }
             }
         }
+        // TILE_TC: warp w expands rows 8 w .. 8 w + 7 of every mask block; lane l
+        // takes row 8 w + l / 4, columns 32 (l mod 4) .. + 31 (one mask word, two
+        // 16-byte chunks of FP8 1.0 = 0x38 or 0 in the 128-byte swizzle).
+        const int nT = tc ? t.nsw * ((nrows + TC_MBLOCK - 1) / TC_MBLOCK) : 0;
+        int tc_next = 0;
+        const uint32_t* tc_bits = g.bitmap + t.bm_off + (8 * warp + (lane >> 2)) * 4 + (lane & 3);
+        // mask words of parts tc_next and tc_next + 1, loaded ahead
+        uint32_t pf0 = nT > 0 ? __ldg(tc_bits) : 0u, pf1 = nT > 1 ? __ldg(tc_bits + TC_MBLOCK * 4) : 0u;
+        auto expand_part = [&](int tt) {
+            const uint32_t w = pf0;
+            pf0 = pf1;
+            pf1 = tt + 2 < nT ? __ldg(tc_bits + size_t(tt + 2) * TC_MBLOCK * 4) : 0u;
+            const int r = 8 * warp + (lane >> 2);
+            unsigned char* row = tcA + (tt % TC_NA) * TC_ABYTES + r * TC_KBLOCK;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t b16 = (w >> (16 * h)) & 0xFFFFu;
+                uint32_t q[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) q[i] = ((((b16 >> (4 * i)) & 0xFu) * 0x00204081u) & 0x01010101u) * 0x38u;
+                const int c = 2 * (lane & 3) + h;
+                *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(q[0], q[1], q[2], q[3]);
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[tt % TC_NA]);
+        };
+        // non-blocking: expand the next parts while their stages are free
+        auto expand_ready = [&](int max_parts) {
+            for (int e = 0; e < max_parts && tc_next < nT; e++) {
+                const int use = tc_next / TC_NA;
+                int free_ = 1;
+                if (use > 0 && lane == 0) free_ = mbar_try_wait(&a_empty[tc_next % TC_NA], uint32_t(use - 1) & 1u) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, free_, 0)) break;
+                expand_part(tc_next++);
+            }
+        };
         for (int gi = 0; gi < ngroups && ok; gi++) {
+            if (tc) expand_ready(2);
             const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
             if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
                 atomicOr(g.err, ERR_TIMEOUT);
                 atomicExch(&abort_flag, 1);
                 break;
             }
-            const Group G = g.groups[t.g0 + gi];
-            const int rel0 = G.sub0 - t.sub0;
+            const int2 meta = slot_meta[sl];
+            const int rel0 = meta.x;
             const int j = ((warp - rel0) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
-            const bool have = j < G.nsub;                       // warp-uniform
             const int32_t* slot = ring + size_t(sl) * SLOT;
+            if constexpr (MODE == MODE_MIXED) if (meta.y > ROW_CONSUMERS) {
+                // ---- group of short sub-rows (mixed precision only): this warp takes j and
+                // j + ROW_CONSUMERS (one int4 of indices per lane each) and gathers both
+                // before summing
+                const bool hb = j + ROW_CONSUMERS < meta.y;       // warp-uniform; j < meta.y always
+                const int4 ha_ = reinterpret_cast<const int4*>(slot)[j];
+                const int4 hb_ = hb ? reinterpret_cast<const int4*>(slot)[j + ROW_CONSUMERS] : make_int4(0, 0, 0, 0);
+                const int ma = (ha_.y + 3) >> 2, ta = ma + ((ha_.w + 3) >> 2);
+                const int mb = (hb_.y + 3) >> 2, tb = mb + ((hb_.w + 3) >> 2);
+                const int4 z4 = make_int4(zidx, zidx, zidx, zidx);
+                const int4 va = lane < ta ? reinterpret_cast<const int4*>(slot + ha_.x)[lane] : z4;
+                const int4 vb = lane < tb ? reinterpret_cast<const int4*>(slot + hb_.x)[lane] : z4;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty_bar[sl]);      // indices are in registers: release the slot
+                const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
+                const bool mia = lane < ma, mib = lane < mb;
+                auto fetch = [&](int idx, bool missing) -> E {
+                    if (missing) return miss_fast ? win[idx - t.wbeg] : gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx);
+                    return pres_check ? gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx) : __ldg(table + idx);
+                };
+                const E a0 = fetch(va.x, mia), a1 = fetch(va.y, mia), a2 = fetch(va.z, mia), a3 = fetch(va.w, mia);
+                const E b0 = fetch(vb.x, mib), b1 = fetch(vb.y, mib), b2 = fetch(vb.z, mib), b3 = fetch(vb.w, mib);
+                A sa = (a0.x + a1.x) + (a2.x + a3.x), ca = (a0.y + a1.y) + (a2.y + a3.y);
+                A sb = (b0.x + b1.x) + (b2.x + b3.x), cb = (b0.y + b1.y) + (b2.y + b3.y);
+                if (mia) { sa = -sa; ca = -ca; }
+                if (mib) { sb = -sb; cb = -cb; }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                    ca += __shfl_xor_sync(0xffffffffu, ca, o);
+                    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+                    cb += __shfl_xor_sync(0xffffffffu, cb, o);
+                }
+                if (lane == 0) {
+                    stash[rel0 + j] = Acc2<MODE>{sa, ca};
+                    if (hb) stash[rel0 + j + ROW_CONSUMERS] = Acc2<MODE>{sb, cb};
+                }
+                if (*(volatile int*)&abort_flag) break;
+                continue;
+            }
+            const bool have = j < meta.y;                       // warp-uniform
             int4 v[4];
             int m4 = 0, tot4 = 0;
             if (have) {
@@ -463,21 +727,52 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             }
             if (*(volatile int*)&abort_flag) break;
         }
+        // the remaining mask parts, waiting for free stages
+        while (ok && tc_next < nT) {
+            const int use = tc_next / TC_NA;
+            if (use > 0 && !mbar_wait_bounded(&a_empty[tc_next % TC_NA], uint32_t(use - 1) & 1u, LIMIT_NS)) {
+                atomicOr(g.err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            expand_part(tc_next++);
+        }
     }
     __syncthreads();
     if (abort_flag) {
-        // let the copies in flight land (bounded) before the CTA leaves
+        // let the copies and MMAs in flight land (bounded) before the CTA leaves
         if (tid == 0) {
             for (int sl = 0; sl < ROW_SLOTS; sl++)
                 if (issued[sl] > 0) mbar_wait_bounded(&full_bar[sl], uint32_t(issued[sl] - 1) & 1u, LIMIT_NS);
             if (t.wlen > 0) mbar_wait_bounded(&win_bar, 0u, LIMIT_NS);
+            if (tc) {
+                for (int q = 0; q < TC_NB; q++)
+                    if (b_issued[q] > 0) mbar_wait_bounded(&b_full[q], uint32_t(b_issued[q] - 1) & 1u, LIMIT_NS);
+                mbar_wait_bounded(&d_full, 0u, LIMIT_NS);
+            }
         }
+        tc_fence_before();
         __syncthreads();
+        if (tc && warp == TC_WARP) tc_dealloc(tmem, TC_TMEM_COLS);
         return;
     }
 
     // ---------------- epilogue: one thread per row, FP64
-    const int nrows = t.r1 - t.r0;
+    // TILE_TC: thread 32 w + l owns tile row 32 w + l = tensor-memory lane
+    // 32 (w mod 4) + l of M-block w / 4; its missing-entry sums (fixed point)
+    long long ms_s = 0, ms_c = 0;
+    if (tc && warp < ROW_CONSUMERS && 32 * warp < nrows) {
+        if (!mbar_wait_bounded(&d_full, 0u, LIMIT_NS)) atomicOr(g.err, ERR_TIMEOUT);
+        tc_fence_after();
+        const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t((warp >> 2) * 2 * TC_NDIG);
+        uint32_t d[16];
+        tc_ld16(ta, d);
+        ms_s = tc_combine(d);
+        tc_ld16(ta + TC_NDIG, d);
+        ms_c = tc_combine(d);
+    }
+    // scale of the digits: 2^-q (the table's fixed point), or the adjoint table's own
+    const double dig_inv = (STAGE == ST_ADJ && tc) ? ldexp(1.0, -adj_digit_exp(*adj.absmax)) : g.inv_scale_q;
     double gk_local = 0.0;
     for (int k = tid; k < nrows; k += ROW_THREADS) {
         const int64_t row = int64_t(t.r0) + k;
@@ -495,14 +790,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         double acc_s, acc_c, si, ci;
         if (MODE == MODE_FP64) {
             const longlong2 T = reinterpret_cast<const longlong2*>(g.T)[t.comm];
-            acc_s = static_cast<double>(T.x + static_cast<long long>(sa)) * g.inv_scale_q;
-            acc_c = static_cast<double>(T.y + static_cast<long long>(sc_)) * g.inv_scale_q;
+            acc_s = static_cast<double>(T.x + static_cast<long long>(sa) - ms_s) * g.inv_scale_q;
+            acc_c = static_cast<double>(T.y + static_cast<long long>(sc_) - ms_c) * g.inv_scale_q;
             si = static_cast<double>(own.x) * g.inv_scale_q;
             ci = static_cast<double>(own.y) * g.inv_scale_q;
         } else {
             const double2 T = reinterpret_cast<const double2*>(g.T)[t.comm];
-            acc_s = T.x + static_cast<double>(sa);
-            acc_c = T.y + static_cast<double>(sc_);
+            acc_s = T.x + static_cast<double>(sa) - static_cast<double>(ms_s) * dig_inv;
+            acc_c = T.y + static_cast<double>(sc_) - static_cast<double>(ms_c) * dig_inv;
             si = static_cast<double>(own.x);
             ci = static_cast<double>(own.y);
         }
@@ -556,6 +851,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             adj.gk_acc[blockIdx.x] += v;
         }
     }
+    if (tc) {
+        tc_fence_before();
+        __syncthreads();
+        if (warp == TC_WARP) tc_dealloc(tmem, TC_TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------------- adjoint helpers
@@ -564,25 +864,47 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
 // entry (nu sin, nu cos), and dL/domega += w.
 __global__ void k_adj_prep(DevGraph g, const double* __restrict__ Ys, const double* __restrict__ lam,
                            const double* __restrict__ a_next, double c_lam, double c_a, double* __restrict__ w,
-                           double* __restrict__ nu, float2* __restrict__ sc, double* __restrict__ g_omega)
+                           double* __restrict__ nu, float2* __restrict__ sc, double* __restrict__ g_omega,
+                           unsigned int* __restrict__ absmax)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    float amax = 0.0f;
+    if (i < g.n) {
+        const double wi = c_lam * lam[i] + (a_next ? c_a * a_next[i] : 0.0);
+        const double scale = g.rscale ? g.rscale[i] : g.scale;
+        const double nui = wi * scale;
+        const double th = Ys[i];
+        const double k = rint(th * KURA_INV_TWO_PI);
+        double r = fma(-k, KURA_TWO_PI_HI, th);
+        r = fma(-k, KURA_TWO_PI_LO, r);
+        float s, c;
+        sincosf(static_cast<float>(r), &s, &c);
+        w[i] = wi;
+        nu[i] = nui;
+        sc[i] = make_float2(s, c);
+        const float2 e = make_float2(static_cast<float>(nui * static_cast<double>(s)),
+                                     static_cast<float>(nui * static_cast<double>(c)));
+        reinterpret_cast<float2*>(g.table)[i] = e;
+        g_omega[i] += wi;
+        amax = fmaxf(fabsf(e.x), fabsf(e.y));
+    }
+    if (absmax) {
+        // non-negative floats order like their bit patterns
+        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(absmax, m);
+    }
+}
+
+// Digit image of the adjoint table for TILE_TC tiles: fixed point with the
+// scale 2^e that keeps every |entry| 2^e below 2^42 (exact products: the
+// entries are FP32).
+__global__ void k_adj_digits(DevGraph g, const unsigned int* __restrict__ absmax)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
-    const double wi = c_lam * lam[i] + (a_next ? c_a * a_next[i] : 0.0);
-    const double scale = g.rscale ? g.rscale[i] : g.scale;
-    const double nui = wi * scale;
-    const double th = Ys[i];
-    const double k = rint(th * KURA_INV_TWO_PI);
-    double r = fma(-k, KURA_TWO_PI_HI, th);
-    r = fma(-k, KURA_TWO_PI_LO, r);
-    float s, c;
-    sincosf(static_cast<float>(r), &s, &c);
-    w[i] = wi;
-    nu[i] = nui;
-    sc[i] = make_float2(s, c);
-    reinterpret_cast<float2*>(g.table)[i] =
-        make_float2(static_cast<float>(nui * static_cast<double>(s)), static_cast<float>(nui * static_cast<double>(c)));
-    g_omega[i] += wi;
+    const double sc = ldexp(1.0, adj_digit_exp(*absmax));
+    const float2 e = reinterpret_cast<const float2*>(g.table)[i];
+    tc_write_digits(g.dig, i, __double2ll_rn(static_cast<double>(e.x) * sc), __double2ll_rn(static_cast<double>(e.y) * sc));
 }
 
 // One CTA per community: FP64 sums of the (nu sin, nu cos) table over the

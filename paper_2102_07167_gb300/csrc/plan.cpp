@@ -223,11 +223,14 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
 
         // ---- staged window of every community: its own columns joined with
         // its dense column blocks when that span fits the cap, else its own
-        // columns (aligned to an even start and length for 16-byte copies);
-        // bitmap encoding when every dense column is inside the window and
+        // columns (aligned to an even start and length for 16-byte copies).
+        // When every dense column is inside the window, the missing entries
+        // become a tensor-core mask (TILE_TC) if that is smaller than their
+        // index lists (tensor_cores = 1) or always (2), else row bitmaps if
         // the zero fraction over the dense columns exceeds bitmap_zmin.
         std::vector<int32_t> c_wbeg(size_t(nc), 0), c_wlen(size_t(nc), 0), c_nsw(size_t(nc), 0);
-        std::vector<uint8_t> c_bitmap(size_t(nc), 0), c_inwin(size_t(nc), 0);
+        std::vector<int32_t> c_kb0(size_t(nc), 0), c_nkb(size_t(nc), 0);
+        std::vector<uint8_t> c_bitmap(size_t(nc), 0), c_inwin(size_t(nc), 0), c_tc(size_t(nc), 0);
         std::vector<int32_t> c_mpad(static_cast<size_t>(nc), static_cast<int32_t>(n));
         for (int32_t I = 0; I < nc; I++) {
             int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
@@ -249,6 +252,19 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 c_mpad[size_t(I)] = wbeg - 1;
             }
             p.max_wlen = std::max(p.max_wlen, wlen);
+            if (covers && in.tensor_cores > 0 && p.dptr[I + 1] > p.dptr[I]) {
+                // tensor-core mask over the K-blocks spanning the dense columns [lo, hi)
+                const int64_t kb0 = lo / TC_KBLOCK, kb1 = (hi + TC_KBLOCK - 1) / TC_KBLOCK;
+                int64_t zeros = 0;
+                for (int64_t v = rb; v < re; v++) zeros += p.miss_cnt[size_t(v)];
+                const int64_t bits_bytes = (re - rb + TC_MBLOCK - 1) / TC_MBLOCK * TC_MBLOCK * (kb1 - kb0) * 16;
+                if (zeros > 0 && (in.tensor_cores >= 2 || bits_bytes < 4 * zeros)) {
+                    c_tc[size_t(I)] = 1;
+                    c_kb0[size_t(I)] = int32_t(kb0);
+                    c_nkb[size_t(I)] = int32_t(kb1 - kb0);
+                    continue;
+                }
+            }
             if (covers && wlen > 0 && in.bitmap_zmin >= 0 && p.dptr[I + 1] > p.dptr[I]) {
                 double zeros = 0, entries = 0;
                 for (int64_t v = rb; v < re; v++) zeros += p.miss_cnt[size_t(v)];
@@ -263,7 +279,8 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         }
         // missing entries given as index lists (not in a bitmap)
         auto listed_miss = [&](int64_t v) -> int64_t {
-            return c_bitmap[size_t(p.node_comm[size_t(v)])] ? 0 : p.miss_cnt[size_t(v)];
+            const size_t I = size_t(p.node_comm[size_t(v)]);
+            return (c_bitmap[I] || c_tc[I]) ? 0 : p.miss_cnt[size_t(v)];
         };
 
         // ---- sub-rows: each row is cut into ceil((nm + np) / SUBROW_MAX)
@@ -322,15 +339,30 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 int64_t w = 0, s = r;
                 while (r < re && (r == s || (w < target && r - s < in.tile_max_rows &&
                                              p.row_sub0[size_t(r) + 1] - p.row_sub0[size_t(s)] <= in.tile_max_sub))) {
-                    w += (c_bitmap[size_t(I)] ? 8 * c_nsw[size_t(I)] : p.miss_cnt[size_t(r)]) + p.pres_cnt[size_t(r)] + 8;
+                    w += (c_tc[size_t(I)] ? 4 * c_nkb[size_t(I)]
+                                          : c_bitmap[size_t(I)] ? 8 * c_nsw[size_t(I)] : p.miss_cnt[size_t(r)]) +
+                         p.pres_cnt[size_t(r)] + 8;
                     r++;
                 }
                 Tile t{};
                 t.r0 = int32_t(s); t.r1 = int32_t(r); t.comm = I; t.wbeg = wbeg; t.wlen = wlen;
                 t.sub0 = p.row_sub0[size_t(s)];
-                if (c_inwin[size_t(I)]) t.flags |= TILE_MISS_IN_WINDOW;
-                if (!std::binary_search(p.dcol.begin() + p.dptr[I], p.dcol.begin() + p.dptr[I + 1], I))
-                    t.flags |= TILE_PRES_CHECK;
+                if (c_tc[size_t(I)]) {
+                    const int64_t nM = (r - s + TC_MBLOCK - 1) / TC_MBLOCK;
+                    t.flags |= TILE_TC;
+                    t.wbeg = c_kb0[size_t(I)] * TC_KBLOCK;
+                    t.wlen = 0;
+                    t.nsw = c_nkb[size_t(I)];
+                    t.bm_off = bm_words;
+                    bm_words += nM * int64_t(t.nsw) * TC_MBLOCK * 4;
+                    p.tc_tiles++;
+                    p.tc_rows += r - s;
+                    p.tc_mask_bits += nM * TC_MBLOCK * int64_t(t.nsw) * TC_KBLOCK;
+                } else {
+                    if (c_inwin[size_t(I)]) t.flags |= TILE_MISS_IN_WINDOW;
+                    if (!std::binary_search(p.dcol.begin() + p.dptr[I], p.dcol.begin() + p.dptr[I + 1], I))
+                        t.flags |= TILE_PRES_CHECK;
+                }
                 if (c_bitmap[size_t(I)]) {
                     t.flags |= TILE_BITMAP;
                     t.nsw = c_nsw[size_t(I)];
@@ -347,10 +379,16 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     G.sub0 = p.row_sub0[size_t(v)] + int32_t(k);
                     int64_t size = 0;
                     std::vector<std::pair<int64_t, int64_t>> members;
-                    while (v < r && int64_t(members.size()) < GROUP_MAX_SUB) {
+                    bool all_short = true;        // every member fits one int4 per lane
+                    while (v < r) {
                         const int64_t si = sub_ints(v, k);
+                        const bool short_ = si - 4 <= SHORT_SUB_INTS;
+                        const int64_t cap = (all_short && short_ && in.entry_bytes == 8) ? GROUP_MAX_SUB_SHORT
+                                                                                           : GROUP_MAX_SUB;
+                        if (int64_t(members.size()) >= cap) break;
                         if (!members.empty() && size + si > in.slot_ints) break;
                         members.emplace_back(v, k);
+                        all_short = all_short && short_;
                         size += si;
                         if (++k == p.row_sub0[size_t(v) + 1] - p.row_sub0[size_t(v)]) { k = 0; v++; }
                     }
@@ -422,6 +460,18 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     if (c == o) continue;
                     int32_t w = p.inv_perm[size_t(c)];
                     bits[size_t(w) >> 6] = 0;
+                }
+                // tensor-core rows: the missing entries become mask bits
+                if (c_tc[size_t(I)]) {
+                    const Tile& T = p.tiles[size_t(p.row_tile[size_t(v)])];
+                    const int64_t lr = v - T.r0, nM = (T.r1 - T.r0 + TC_MBLOCK - 1) / TC_MBLOCK;
+                    const int64_t m = lr / TC_MBLOCK, rr = lr % TC_MBLOCK;
+                    for (int32_t c : ms) {
+                        const int64_t k = int64_t(c) - T.wbeg, kb = k / TC_KBLOCK, kc = k % TC_KBLOCK;
+                        p.bitmap[size_t(T.bm_off + ((kb * nM + m) * TC_MBLOCK + rr) * 4 + (kc >> 5))] |=
+                            uint32_t(1) << (kc & 31);
+                    }
+                    ms.clear();
                 }
                 // bitmap rows: the missing entries become bits over the window
                 if (c_bitmap[size_t(I)]) {

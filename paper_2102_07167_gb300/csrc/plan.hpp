@@ -38,6 +38,17 @@ constexpr int32_t TILE_MISS_IN_WINDOW = 2;
 // range-checked (otherwise they are gathered from the global table directly)
 constexpr int32_t TILE_PRES_CHECK = 4;
 constexpr int32_t BITMAP_MAX_SW = 5;
+// Tensor-core tile: the missing entries of the tile's dense blocks form a 0/1
+// mask over K-blocks of 128 permuted columns, [wbeg, wbeg + 128 nsw) with wbeg
+// a multiple of 128 (wlen = 0: no staged window).  The row kernel multiplies
+// the mask by the base-16 digits of the fixed-point (sin, cos) of those
+// columns on the tensor cores.  Bits at bitmap[bm_off ...] in blocks of
+// 128 rows x 128 columns, block (kb, m) at (kb * nM + m) * 512 words with
+// nM = ceil((r1 - r0) / 128); row r of the block is 4 words, bit c & 31 of
+// word c >> 5 for column wbeg + 128 kb + c, tile row 128 m + r.
+constexpr int32_t TILE_TC = 8;
+constexpr int32_t TC_KBLOCK = 128;      // columns per K-block
+constexpr int32_t TC_MBLOCK = 128;      // rows per M-block (tensor-core tile height)
 
 // Rows are cut into sub-rows of at most SUBROW_MAX entries (missing entries
 // first, then present entries, in the row's order), so that one warp holds a
@@ -54,6 +65,12 @@ constexpr int32_t SUBROW_MAX = 508;
 //   n for present parts; for missing parts wbeg - 1 in TILE_MISS_IN_WINDOW
 //   tiles, else n.
 constexpr int32_t GROUP_MAX_SUB = 16;
+// With 8-byte table entries (mixed precision), a group of short sub-rows (each
+// at most SHORT_SUB_INTS stream ints: one int4 per lane) may hold up to
+// GROUP_MAX_SUB_SHORT of them: then every consumer warp takes two (j and
+// j + GROUP_MAX_SUB) and gathers both at once.
+constexpr int32_t GROUP_MAX_SUB_SHORT = 32;
+constexpr int32_t SHORT_SUB_INTS = 128;
 struct Group {
     int64_t off;
     int32_t len;
@@ -78,6 +95,10 @@ struct PlanInput {
     // there exceeds this (and the window holds every dense column); < 0: never
     double bitmap_zmin = -1.0;
     int32_t entry_bytes = 8;            // (sin, cos) table entry size of the row kernel: 8 or 16
+    // tensor-core mask encoding of a community's dense blocks (TILE_TC):
+    // 0 never, 1 when its mask bits take fewer bytes than its index lists,
+    // 2 whenever the window holds every dense column
+    int32_t tensor_cores = 1;
 };
 
 struct Plan {
@@ -100,9 +121,10 @@ struct Plan {
     std::vector<Tile> tiles;
     std::vector<int64_t> sub_hdr;       // [n_sub] position of each sub-row's header in gstream
     std::vector<int64_t> sub_mpos, sub_ppos;   // [n_sub] positions of its missing / present segments
-    std::vector<uint32_t> bitmap;              // row bitmaps of TILE_BITMAP tiles
+    std::vector<uint32_t> bitmap;              // row bitmaps of TILE_BITMAP tiles, mask bits of TILE_TC tiles
     std::vector<int32_t> row_tile;             // [n] tile of each row
     int64_t bitmap_rows = 0;
+    int64_t tc_tiles = 0, tc_rows = 0, tc_mask_bits = 0;   // tensor-core tiles, their rows and mask bits
     int32_t max_wlen = 0;
     // statistics
     int64_t dense_blocks = 0, sparse_blocks = 0, nonempty_blocks = 0;

@@ -42,7 +42,7 @@ class KuraError(RuntimeError):
 
 class KuraOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scaling", C.c_int32), ("tau", C.c_double),
-                ("keep_host_csr", C.c_int32), ("reserved0", C.c_int32), ("bitmap_zmin", C.c_double),
+                ("keep_host_csr", C.c_int32), ("tensor_cores", C.c_int32), ("bitmap_zmin", C.c_double),
                 ("reserved", C.c_int32 * 4)]
 
 
@@ -53,7 +53,8 @@ class KuraBlockStats(C.Structure):
                 ("missing_entries", C.c_int64), ("sparse_entries", C.c_int64), ("max_row_entries", C.c_int64),
                 ("tiles", C.c_int64), ("max_window", C.c_int64),
                 ("stream_bytes", C.c_int64), ("node_bytes_row", C.c_int64), ("node_bytes_trig", C.c_int64),
-                ("direct_edges", C.c_int64)]
+                ("direct_edges", C.c_int64), ("tc_tiles", C.c_int64), ("tc_rows", C.c_int64),
+                ("tc_mask_bits", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -313,13 +314,15 @@ def kura_destroy(h):
     load().kura_destroy(h)
 
 
-def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5, precision=PREC_MIXED, bitmap_zmin=-1.0):
+def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5, precision=PREC_MIXED, bitmap_zmin=-1.0,
+                    tensor_cores=1):
     p = C.c_void_p()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     label = np.ascontiguousarray(label, dtype=np.int32)
     o = kura_default_opts()
     o.tau, o.precision, o.bitmap_zmin = float(tau), int(precision), float(bitmap_zmin)
+    o.tensor_cores = int(tensor_cores)
     rc = load().kura_plan_build(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
                                 label.ctypes.data, int(n_comm), C.byref(o), C.byref(p))
     _check(rc, None)
@@ -361,6 +364,9 @@ TILE_DTYPE = np.dtype([("r0", np.int32), ("r1", np.int32), ("comm", np.int32), (
                        ("wlen", np.int32), ("g0", np.int32), ("g1", np.int32), ("sub0", np.int32),
                        ("bm_off", np.int64), ("nsw", np.int32), ("flags", np.int32)])
 TILE_BITMAP = 1
+TILE_TC = 8
+TC_KBLOCK = 128
+TC_MBLOCK = 128
 
 
 def kura_plan_export(p, n):
@@ -388,13 +394,16 @@ class Kuramoto:
     """A libkura handle: the graph, omega and K resident on the GPU."""
 
     def __init__(self, row_ptr, col, label, n_comm, omega, K, precision=PREC_FP64,
-                 scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None, bitmap_zmin=None):
+                 scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None, bitmap_zmin=None,
+                 tensor_cores=None):
         self.n = int(np.asarray(row_ptr).shape[0] - 1)
         self.n_comm = int(n_comm)
         o = kura_default_opts()
         o.precision, o.scaling, o.tau, o.keep_host_csr = int(precision), int(scaling), float(tau), int(keep_host_csr)
         if bitmap_zmin is not None:
             o.bitmap_zmin = float(bitmap_zmin)
+        if tensor_cores is not None:
+            o.tensor_cores = int(tensor_cores)
         self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
 
     def rhs(self, theta, out):

@@ -54,9 +54,9 @@ def test_invalid_input_is_rejected(bad):
     assert kura.kura_last_error(None)
 
 
-def _reconstruct_and_check(g, tau, bitmap_zmin=-1.0, precision=1):
+def _reconstruct_and_check(g, tau, bitmap_zmin=-1.0, precision=1, tensor_cores=1):
     n, nc = g.n, g.n_comm
-    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin)
+    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin, tensor_cores)
     try:
         perm, off = kura.kura_plan_perm(p, n, nc)
         st = kura.kura_plan_stats(p)
@@ -125,14 +125,16 @@ def test_plan_reconstructs_random_graphs(seed):
         np.fill_diagonal(A, 1)           # self-loops must be dropped
     g = G.from_dense(A, lab, nc)
     for tau in (0.0, 0.25, 0.5, 0.75, 1.0):
-        for zmin, prec in ((-1.0, 1), (0.0, 1), (-1.0, 0)):
-            _reconstruct_and_check(g, tau, zmin, prec)
+        for zmin, prec, tcm in ((-1.0, 1, 0), (0.0, 1, 0), (-1.0, 0, 0), (-1.0, 1, 1), (-1.0, 0, 2)):
+            _reconstruct_and_check(g, tau, zmin, prec, tcm)
 
 
 def test_plan_reconstructs_sbm_and_extremes():
     g = G.sbm(4, [40, 25, 60, 13], [0.9, 0.6, 0.95, 0.3], 0.04)
-    _reconstruct_and_check(g, 0.5, 0.0)
-    st = _reconstruct_and_check(g, 0.5)
+    _reconstruct_and_check(g, 0.5, 0.0, tensor_cores=0)
+    st2 = _reconstruct_and_check(g, 0.5, tensor_cores=2)
+    assert st2["tc_tiles"] >= 3 and st2["tc_rows"] == 40 + 25 + 60      # every dense community on the tensor cores
+    st = _reconstruct_and_check(g, 0.5, tensor_cores=0)
     assert st["dense_blocks"] == 3          # the p_in = 0.3 community stays sparse
     st0 = _reconstruct_and_check(g, 0.0)
     assert st0["dense_blocks"] == 0 and st0["missing_entries"] == 0 and st0["sparse_entries"] == g.nnz
@@ -164,17 +166,31 @@ def test_plan_splits_long_rows_into_subrows(tau, p_one):
     A = (rng.random((n, n)) < p_one).astype(np.uint8)
     np.fill_diagonal(A, 0)
     g = G.from_dense(A)
-    st = _reconstruct_and_check(g, tau)
-    _reconstruct_and_check(g, tau, 0.0)
+    st = _reconstruct_and_check(g, tau, tensor_cores=0)
+    _reconstruct_and_check(g, tau, 0.0, tensor_cores=0)
+    _reconstruct_and_check(g, tau, tensor_cores=2)
     assert st["max_row_entries"] > 508
 
 
-def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
+def _tc_digits(v):
+    """Balanced base-16 digits (16 of them, each in [-8, 7]) of integers v, as the trig kernel writes them."""
+    v = np.asarray(v, dtype=np.int64).copy()
+    out = np.empty((16,) + v.shape, np.int64)
+    for k in range(16):
+        d = ((v + 8) & 15) - 8
+        out[k] = d
+        v = (v - d) >> 4
+    assert np.all(v == 0)
+    return out
+
+
+def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1, tensor_cores=1):
     """Consumes the packed stream exactly as the row kernel does (groups -> sub-row headers -> padded int4
-    segments -> window-or-table gathers, padding resolving to zero entries), in float64, and returns f in
-    user order."""
+    segments -> window-or-table gathers, padding resolving to zero entries; tensor-core tiles: 128 x 128 mask
+    blocks times the base-16 digits of the fixed-point table, summed as exact integers), in float64, and
+    returns f in user order."""
     n, nc = g.n, g.n_comm
-    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin)
+    p = kura.kura_plan_build(n, g.row_ptr, g.col, g.label, nc, tau, precision, bitmap_zmin, tensor_cores)
     try:
         perm, off = kura.kura_plan_perm(p, n, nc)
         gstream, groups, tiles, row_sub0, bitmap = kura.kura_plan_export(p, n)
@@ -186,6 +202,14 @@ def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
     c_tab = np.append(np.cos(th), [0.0, 0.0])
     S = np.array([s_tab[off[J]:off[J + 1]].sum() for J in range(nc)])
     C = np.array([c_tab[off[J]:off[J + 1]].sum() for J in range(nc)])
+    # fixed point with q = 61 - ceil(log2 n) fraction bits, and its digits per column (padded to 128)
+    qb = 61 - int(np.ceil(np.log2(max(n, 2))))
+    npad = (n + 127) // 128 * 128
+    sf = np.zeros(npad, np.int64)
+    cf = np.zeros(npad, np.int64)
+    sf[:n] = np.rint(s_tab[:n] * 2.0 ** qb).astype(np.int64)
+    cf[:n] = np.rint(c_tab[:n] * 2.0 ** qb).astype(np.int64)
+    dsf, dcf = _tc_digits(sf), _tc_digits(cf)
     f = np.empty(n)
     for t in tiles:
         wbeg, wlen = int(t["wbeg"]), int(t["wlen"])
@@ -221,6 +245,23 @@ def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
                 cols = wbeg + k[bits == 1]
                 a_s -= s_tab[cols].sum()
                 a_c -= c_tab[cols].sum()
+            if t["flags"] & kura.TILE_TC:
+                # block (kb, m) of 128 x 128 bits; D_k = mask . digit_k, sum_k D_k 16^k in integers
+                lr, nM = r - t["r0"], (t["r1"] - t["r0"] + 127) // 128
+                ms = mc = 0
+                for kb in range(int(t["nsw"])):
+                    w = bitmap[int(t["bm_off"]) + ((kb * nM + lr // 128) * 128 + lr % 128) * 4:][:4]
+                    c = np.arange(128)
+                    bits = ((w[c >> 5] >> (c & 31).astype(np.uint32)) & 1).astype(np.int64)
+                    cols = wbeg + 128 * kb + c
+                    assert np.all(cols[bits == 1] < n)
+                    Ds = dsf[:, cols] @ bits
+                    Dc = dcf[:, cols] @ bits
+                    assert np.all(np.abs(Ds) < 2 ** 24) and np.all(np.abs(Dc) < 2 ** 24)   # exact in FP32
+                    ms += sum(int(Ds[k]) << (4 * k) for k in range(16))
+                    mc += sum(int(Dc[k]) << (4 * k) for k in range(16))
+                a_s -= ms * 2.0 ** -qb
+                a_c -= mc * 2.0 ** -qb
             I = t["comm"]
             Ts, Tc = S[dense[I]].sum(), C[dense[I]].sum()
             f[r] = omega[perm[r]] + (K / n) * (c_tab[r] * (Ts + a_s) - s_tab[r] * (Tc + a_c))
@@ -229,9 +270,9 @@ def _emulate_row_kernel(g, tau, omega, theta, K, bitmap_zmin=-1.0, precision=1):
     return out
 
 
-@pytest.mark.parametrize("zmin,prec", [(-1.0, 1), (0.05, 1), (-1.0, 0)])
+@pytest.mark.parametrize("zmin,prec,tcm", [(-1.0, 1, 0), (0.05, 1, 0), (-1.0, 0, 0), (-1.0, 1, 1), (-1.0, 0, 2)])
 @pytest.mark.parametrize("case", ["sbm", "long_rows_sparse", "long_rows_dense", "big_community"])
-def test_packed_stream_emulation_matches_oracle(case, zmin, prec):
+def test_packed_stream_emulation_matches_oracle(case, zmin, prec, tcm):
     """The packed stream (headers, padding, windows, sub-rows) read the way the row kernel reads it gives
     the right-hand side of the FP64 oracle."""
     import oracle
@@ -247,7 +288,7 @@ def test_packed_stream_emulation_matches_oracle(case, zmin, prec):
         g = G.from_dense(A)
         tau = 0.0 if case == "long_rows_sparse" else 1.0
     omega, theta = rng.normal(size=g.n), rng.uniform(-30, 30, g.n)
-    f = _emulate_row_kernel(g, tau, omega, theta, 2.0, zmin, prec)
+    f = _emulate_row_kernel(g, tau, omega, theta, 2.0, zmin, prec, tcm)
     ref = oracle.rhs_csr(g.row_ptr, g.col, omega, theta, 2.0)
     np.testing.assert_allclose(f, ref, rtol=0, atol=1e-10)
 
@@ -258,7 +299,7 @@ def test_missing_entries_are_bank_balanced(prec):
     memory bank group about equally: on average at most 2.5 (of 32) entries per group of 128 / entry-size
     bytes (the ideal is 32 / groups = 2 or 4); only a row's tail can be lopsided."""
     g = G.sbm(2, [900, 700, 1200], [0.6, 0.7, 0.8], 0.01)
-    p = kura.kura_plan_build(g.n, g.row_ptr, g.col, g.label, g.n_comm, 0.5, prec)
+    p = kura.kura_plan_build(g.n, g.row_ptr, g.col, g.label, g.n_comm, 0.5, prec, tensor_cores=0)
     try:
         gstream, groups, tiles, row_sub0, _ = kura.kura_plan_export(p, g.n)
     finally:
