@@ -321,7 +321,11 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "kernel": "k_row_stage",
                 "algorithmic_bytes_per_launch": alg_bytes, "row_kernel_ms": row_ms,
-                "launches_timed": int(launch_ms.size)}
+                "launches_timed": int(launch_ms.size),
+                # the kernel's actual limiter: random L2 gathers of the present (sparse-block) entries
+                "present_gathers_per_launch": int(st["sparse_entries"]),
+                "present_gather_rate_per_s": (st["sparse_entries"] / (row_ms * 1e-3)) if row_ms else None,
+                "tensor_core_tiles": int(st["tc_tiles"]), "tiles": int(st["tiles"])}
 
     # ---- e2e: the public call with pinned HOST phases, copies inside every step
     e2e = None
