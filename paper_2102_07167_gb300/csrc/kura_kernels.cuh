@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             }
         };
         for (int gi = 0; gi < ngroups && ok; gi++) {
-            if (tc) expand_ready(2);
+            if (tc) expand_ready(4);
             const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
             if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
                 atomicOr(g.err, ERR_TIMEOUT);

@@ -329,6 +329,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         sub_ppos.resize(size_t(n_sub));
         int64_t goff = 0;
         int64_t bm_words = 0;
+        std::vector<int64_t> tile_work;       // work estimate of each tile (entries + per-row overhead)
         p.row_tile.resize(size_t(n));
         for (int32_t I = 0; I < nc; I++) {
             int64_t rb = p.comm_off[I], re = p.comm_off[I + 1];
@@ -410,6 +411,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 }
                 t.g1 = int32_t(p.groups.size());
                 p.tiles.push_back(t);
+                tile_work.push_back(w);
             }
         }
         p.gstream.assign(size_t(std::max<int64_t>(goff, 4)), 0);
@@ -508,6 +510,22 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 hdr[0] = int32_t(sub_mpos[size_t(G.sub0 + m)] - G.off);
                 hdr[2] = int32_t(sub_ppos[size_t(G.sub0 + m)] - G.off);
             }
+        // launch order: longest tiles first (CTAs start in index order, so the
+        // last wave holds the shortest tiles); ties keep community order
+        {
+            std::vector<int32_t> order(p.tiles.size());
+            for (size_t q = 0; q < order.size(); q++) order[q] = int32_t(q);
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t a, int32_t b) { return tile_work[size_t(a)] > tile_work[size_t(b)]; });
+            std::vector<Tile> sorted(p.tiles.size());
+            std::vector<int32_t> new_index(p.tiles.size());
+            for (size_t q = 0; q < order.size(); q++) {
+                sorted[q] = p.tiles[size_t(order[q])];
+                new_index[size_t(order[q])] = int32_t(q);
+            }
+            p.tiles.swap(sorted);
+            for (int64_t v = 0; v < n; v++) p.row_tile[size_t(v)] = new_index[size_t(p.row_tile[size_t(v)])];
+        }
     } catch (const std::bad_alloc&) {
         err = "out of host memory while building the block plan";
         return 2;
