@@ -233,6 +233,29 @@ kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t 
 kura_status kura_set_timing(kura_t h, int32_t on);
 kura_status kura_kernel_times(kura_t h, float* ms, int32_t cap, int32_t* count);
 
+/* Result of kura_autotune. */
+typedef struct {
+    double tau;              /* chosen dense/sparse threshold */
+    int32_t tensor_cores;    /* chosen encoding of dense-block zeros (as kura_opts.tensor_cores) */
+    int32_t candidates;      /* plans built and timed (the handle's own plan included) */
+    int64_t tile_work;       /* chosen work target per tile (stored entries + per-row overhead) */
+    double rhs_ms;           /* median time of one right-hand side with the chosen plan */
+    double initial_rhs_ms;   /* the same with the plan the handle had on entry */
+    double seconds;          /* wall time spent tuning */
+} kura_tune_result;
+
+/* Autotuner of the block plan (not in the paper: its tau = 0.5 is a cost
+ * argument, Sec. 1 and 3).  Every plan computes the same right-hand side up
+ * to rounding; only speed differs.  Times kura_rhs at theta (host or device,
+ * user order, n values) for candidate plans, one parameter at a time
+ * starting from the handle's own: the encoding of dense-block zeros
+ * (tensor-core mask or index lists), the work per tile (x0.6, x1.6) and the
+ * threshold tau (0.35, 0.65), within about budget_s seconds of wall time
+ * (plan builds included).  The fastest plan is kept on the handle (cached
+ * step graphs are dropped).  Needs the host CSR (keep_host_csr = 1), else
+ * KURA_ESTATE.  Synchronous.  Not available on batch handles. */
+kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out);
+
 /* Switches the handle to another stream (cached graphs stay valid). */
 kura_status kura_set_stream(kura_t h, void* stream);
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -93,6 +94,7 @@ struct kura_ctx {
     int64_t miss_total = 0, pres_total = 0, nnz = 0, stream_bytes = 0, bitmap_rows = 0;
     int64_t tc_tiles = 0, tc_rows = 0, tc_mask_bits = 0;
     bool has_tc = false;                // some tile runs on the tensor cores (digit image kept up to date)
+    int64_t tile_work = 0;              // planner work target per tile (0: automatic); set by kura_autotune
     int32_t bm_stash_off = 0;
     // device buffers
     DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig;
@@ -562,6 +564,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         in.entry_bytes = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
         in.bitmap_zmin = h->opts.bitmap_zmin;
         in.tensor_cores = h->opts.tensor_cores;
+        in.tile_work = h->tile_work;
         Plan plan;
         std::string err;
         int rc = build_plan(in, plan, err);
@@ -571,6 +574,126 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         if (st) return st;
     }
     return stats ? kura_get_stats(h, stats) : KURA_OK;
+}
+
+namespace {
+
+// Plan of the handle's host CSR with the given parameters, uploaded.
+kura_status rebuild_plan(kura_t h, double tau, int32_t tensor_cores, int64_t tile_work)
+{
+    PlanInput in;
+    in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
+    in.n_comm = h->n_comm; in.tau = tau;
+    const int mode = h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
+    in.tile_max_rows = TILE_MAX_ROWS;
+    in.tile_max_sub = tile_max_sub_for(mode);
+    in.slot_ints = slot_ints_for(mode);
+    in.entry_bytes = mode == MODE_MIXED ? 8 : 16;
+    in.bitmap_zmin = h->opts.bitmap_zmin;
+    in.tensor_cores = tensor_cores;
+    in.tile_work = tile_work;
+    Plan plan;
+    std::string err;
+    int rc = build_plan(in, plan, err);
+    if (rc) return h->fail(rc == 2 ? KURA_ENOMEM : KURA_EINVAL, "%s", err.c_str());
+    KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise before re-planning");
+    kura_status st = build_device(h, std::move(plan));
+    if (st) return st;
+    h->opts.tau = tau;
+    h->opts.tensor_cores = tensor_cores;
+    h->tile_work = tile_work;
+    return KURA_OK;
+}
+
+// Median of `reps` timed right-hand sides (after two untimed ones).
+kura_status time_rhs(kura_t h, const double* theta, double* out, int reps, double* ms)
+{
+    cudaEvent_t e0, e1;
+    KCHECK(h, cudaEventCreate(&e0), "event");
+    KCHECK(h, cudaEventCreate(&e1), "event");
+    std::vector<float> t;
+    kura_status st = KURA_OK;
+    for (int r = 0; r < reps + 2 && st == KURA_OK; r++) {
+        cudaEventRecord(e0, h->stream);
+        st = kura_rhs(h, theta, out);
+        cudaEventRecord(e1, h->stream);
+        if (st == KURA_OK && cudaEventSynchronize(e1) != cudaSuccess) st = h->fail(KURA_ECUDA, "timing the right-hand side");
+        float v = 0.0f;
+        cudaEventElapsedTime(&v, e0, e1);
+        if (r >= 2) t.push_back(v);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == KURA_OK) st = read_flags(h);
+    if (st) return st;
+    std::sort(t.begin(), t.end());
+    *ms = double(t[t.size() / 2]);
+    return KURA_OK;
+}
+
+}  // namespace
+
+kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out)
+{
+    if (kura_status st0 = check_single(h)) return st0;
+    if (!theta || !out) return h->fail(KURA_EINVAL, "theta or out is NULL");
+    if (h->h_col.empty() && h->nnz > 0)
+        return h->fail(KURA_ESTATE, "the autotuner rebuilds plans from the host CSR copy (keep_host_csr = 1)");
+    const auto t_start = std::chrono::steady_clock::now();
+    auto elapsed = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    std::memset(out, 0, sizeof *out);
+    DevMem scratch;
+    KCHECK(h, scratch.alloc(size_t(h->n) * 8), "alloc tuning output");
+    double* f = scratch.as<double>();
+    const int reps = 5;
+    double best_ms = 0.0;
+    if (kura_status st = time_rhs(h, theta, f, reps, &best_ms)) return st;
+    out->initial_rhs_ms = best_ms;
+    int32_t cand = 1;
+    double best_tau = h->opts.tau;
+    int32_t best_tc = h->opts.tensor_cores;
+    // the automatic work target, as the planner computes it
+    int64_t total = 0;
+    for (int64_t v = 0; v < h->n; v++) total += h->plan.miss_cnt[size_t(v)] + h->plan.pres_cnt[size_t(v)] + 8;
+    const int64_t auto_work = std::max<int64_t>(2048, total / (152 * 12));
+    int64_t best_work = h->tile_work > 0 ? h->tile_work : auto_work;
+    auto try_plan = [&](double tau, int32_t tc, int64_t work) -> kura_status {
+        if (elapsed() > budget_s) return KURA_OK;
+        if (kura_status st = rebuild_plan(h, tau, tc, work)) return st;
+        double ms = 0.0;
+        if (kura_status st = time_rhs(h, theta, f, reps, &ms)) return st;
+        cand++;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_tau = tau;
+            best_tc = tc;
+            best_work = work;
+        }
+        return KURA_OK;
+    };
+    // one parameter at a time, each from the best so far
+    for (int32_t tc : {1, 0})
+        if (tc != best_tc)
+            if (kura_status st = try_plan(best_tau, tc, best_work)) return st;
+    for (double sc : {0.6, 1.6}) {
+        const int64_t w = std::max<int64_t>(1024, int64_t(double(best_work) * sc));
+        if (kura_status st = try_plan(best_tau, best_tc, w)) return st;
+    }
+    for (double tau : {0.35, 0.65})
+        if (tau != best_tau)
+            if (kura_status st = try_plan(tau, best_tc, best_work)) return st;
+    // keep the winner on the handle
+    if (h->opts.tau != best_tau || h->opts.tensor_cores != best_tc || h->tile_work != best_work)
+        if (kura_status st = rebuild_plan(h, best_tau, best_tc, best_work)) return st;
+    out->tau = best_tau;
+    out->tensor_cores = best_tc;
+    out->tile_work = best_work;
+    out->rhs_ms = best_ms;
+    out->candidates = cand;
+    out->seconds = elapsed();
+    return KURA_OK;
 }
 
 kura_status kura_set_stream(kura_t h, void* stream)

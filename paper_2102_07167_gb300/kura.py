@@ -60,6 +60,15 @@ class KuraBlockStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class KuraTuneResult(C.Structure):
+    _fields_ = [("tau", C.c_double), ("tensor_cores", C.c_int32), ("candidates", C.c_int32),
+                ("tile_work", C.c_int64), ("rhs_ms", C.c_double), ("initial_rhs_ms", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class KuraGraphDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("label", C.c_void_p),
                 ("n_comm", C.c_int32), ("omega", C.c_void_p), ("K", C.c_double)]
@@ -97,6 +106,7 @@ def load() -> C.CDLL:
             "kura_direct_rhs": (S, [P, P, P, I32]),
             "kura_direct_rk4_steps": (S, [P, P, D, I64, I32]),
             "kura_set_timing": (S, [P, I32]),
+            "kura_autotune": (S, [P, P, D, C.POINTER(KuraTuneResult)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
             "kura_sync": (S, [P]),
@@ -310,6 +320,12 @@ def kura_last_error(h=None) -> str:
     return (load().kura_last_error(h) or b"").decode()
 
 
+def kura_autotune(h, theta, n, budget_s=30.0) -> dict:
+    r = KuraTuneResult()
+    _check(load().kura_autotune(h, _ptr(theta, n=n), float(budget_s), C.byref(r)), h)
+    return r.as_dict()
+
+
 def kura_destroy(h):
     load().kura_destroy(h)
 
@@ -423,6 +439,10 @@ class Kuramoto:
 
     def stats(self):
         return kura_get_stats(self.h)
+
+    def autotune(self, theta, budget_s=30.0):
+        """Times the right-hand side at theta for candidate plans and keeps the fastest (see kura_autotune)."""
+        return kura_autotune(self.h, theta, self.n, budget_s)
 
     def adjoint(self, theta0, step, n_steps, ckpt_every=64, loss_kind=0, target=None, g_omega=None, g_theta0=None):
         """Loss and gradients (loss, g_omega, g_K, g_theta0) of the RK4 trajectory from theta0."""

@@ -154,3 +154,19 @@ def test_adjoint_tensor_cores_vs_index_lists(ragged, loss_kind):
         assert rel(gom, gom_ref) < 2e-4 and rel(gth, gth_ref) < 2e-4, (tcm, rel(gom, gom_ref), rel(gth, gth_ref))
         assert abs(gK - gK_ref) <= 2e-4 * max(abs(gK_ref), 1e-12), (tcm, gK, gK_ref)
     assert rel(out[2][1], out[0][1]) < 2e-4 and rel(out[2][3], out[0][3]) < 2e-4
+
+
+def test_autotune_keeps_the_right_hand_side(sbm_small):
+    """The autotuner times candidate plans (encoding, tile work, tau) and keeps the fastest; the right-hand
+    side stays within the FP64 parity tolerance of the oracle (every plan computes the same sums)."""
+    w = sbm_small
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_FP64) as k:
+        res = k.autotune(_dev(w.theta0), budget_s=60.0)
+        assert res["candidates"] >= 4 and res["rhs_ms"] <= res["initial_rhs_ms"] + 1e-9
+        assert res["tau"] in (0.35, 0.5, 0.65) and res["tensor_cores"] in (0, 1)
+        f = _rhs(k, w.theta0)
+        st = k.stats()
+        assert abs(st["tau"] - res["tau"]) < 1e-12
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
+    assert np.all(np.abs(f - ref) <= 1e-11 * (1 + np.diff(g.row_ptr)))
