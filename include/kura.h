@@ -233,6 +233,28 @@ kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t 
 kura_status kura_set_timing(kura_t h, int32_t on);
 kura_status kura_kernel_times(kura_t h, float* ms, int32_t cap, int32_t* count);
 
+/* Ensemble of n_traj trajectories that share one graph (not in the paper:
+ * its batched form).  n_traj must be a multiple of 16; the trajectories are
+ * processed in groups of 16.
+ *   omega   host, n_traj x n (trajectory-major, user order)
+ *   K       host, n_traj (uniform scaling K / N per trajectory)
+ * The graph arguments and opts->tau are as in kura_create; opts->tensor_cores
+ * = 0 keeps index lists, any other value puts every dense community whose
+ * dense columns span <= 4096 columns on the tensor cores.  The dense-block
+ * product A_IJ [sin, cos] of eq:KuramotoGraphApproach is then a real matrix
+ * product over the 16 trajectories of a group: the 0/1 mask (BF16, exact)
+ * times the split BF16 hi + lo (sin, cos) of every trajectory, 64 columns,
+ * FP32 accumulation in tensor memory (tcgen05.mma.kind::f16); listed entries
+ * are gathered for all 16 trajectories at once.  FP32 sin/cos of phases
+ * reduced mod 2 pi in FP64, FP64 block sums, epilogue and state.
+ * kura_rhs and kura_rk4_steps then take theta (and dtheta) as n_traj x n
+ * arrays, host or device; kura_get_stats, kura_sync, kura_set_stream,
+ * kura_last_error and kura_destroy work as for single handles, every other
+ * call returns KURA_ESTATE. */
+kura_status kura_ensemble_create(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
+                                 int32_t n_comm, int32_t n_traj, const double* omega, const double* K,
+                                 const kura_opts* opts, void* stream, kura_t* out);
+
 /* Result of kura_autotune. */
 typedef struct {
     double tau;              /* chosen dense/sparse threshold */

@@ -15,6 +15,7 @@
 
 #include "kura.h"
 #include "kura_batch.cuh"
+#include "kura_ensemble.cuh"
 #include "kura_kernels.cuh"
 #include "plan.hpp"
 
@@ -76,9 +77,19 @@ struct BatchData {
     DevMem traj, order, comm_off, dptr, dcol, node_comm, row_off, row_nm, entries_d, queue, stash;
 };
 
+// Device data of an ensemble handle (kura_ensemble_create): trajectories in
+// groups of ENS_B sharing one graph, node-major per group.
+struct EnsData {
+    int32_t groups = 0;
+    int64_t nblk64 = 0;
+    DevMem comm_off, dptr, dcol, tiles, row_sub0, sub_hdr, sub_mpos, sub_ppos, gstream, bitmap, node_comm;
+    DevMem table, image, bsum, T, omega, scale, y, Y, krk, f, user;
+};
+
 struct kura_ctx {
     std::string err;
     std::unique_ptr<BatchData> batch;    // non-null for a batch handle
+    std::unique_ptr<EnsData> ens;        // non-null for an ensemble handle
     int device = 0;
     kura_opts opts{};
     int64_t n = 0;
@@ -269,6 +280,73 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
     }
 }
 
+EnsArgs ens_args(kura_ctx* h)
+{
+    EnsData& e = *h->ens;
+    EnsArgs a{};
+    a.n = h->n;
+    a.n_comm = h->n_comm;
+    a.groups = e.groups;
+    a.node_comm = e.node_comm.as<int32_t>();
+    a.comm_off = e.comm_off.as<int64_t>();
+    a.dptr = e.dptr.as<int64_t>();
+    a.dcol = e.dcol.as<int32_t>();
+    a.tiles = e.tiles.as<Tile>();
+    a.row_sub0 = e.row_sub0.as<int32_t>();
+    a.sub_hdr = e.sub_hdr.as<int64_t>();
+    a.sub_mpos = e.sub_mpos.as<int64_t>();
+    a.sub_ppos = e.sub_ppos.as<int64_t>();
+    a.gstream = e.gstream.as<int32_t>();
+    a.bitmap = e.bitmap.as<uint32_t>();
+    a.table = e.table.as<float2>();
+    a.image = e.image.as<__nv_bfloat16>();
+    a.nblk64 = e.nblk64;
+    a.bsum = e.bsum.as<double2>();
+    a.T = e.T.as<double2>();
+    a.omega = e.omega.as<double>();
+    a.scale = e.scale.as<double>();
+    a.err = h->err_flags.as<int>();
+    return a;
+}
+
+// One right-hand-side evaluation of every trajectory (stage `stage`), on stream s.
+void enqueue_ens_stage(kura_ctx* h, const EnsArgs& a, const double* in, const RkArgs& rk, int stage, cudaStream_t s)
+{
+    const unsigned G = unsigned(a.groups);
+    k_ens_trig<<<dim3(blocks_for(h->n, 256), G), 256, 0, s>>>(a, in);
+    k_ens_bsum<<<dim3(unsigned(h->n_comm), G), 256, 0, s>>>(a);
+    k_ens_T<<<dim3(blocks_for(int64_t(h->n_comm) * ENS_B, 256), G), 256, 0, s>>>(a);
+    const dim3 grid(unsigned(h->n_tiles), G);
+    switch (stage) {
+    case ST_RHS: k_ens_row<ST_RHS><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
+    case ST_1: k_ens_row<ST_1><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
+    case ST_2: k_ens_row<ST_2><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
+    case ST_3: k_ens_row<ST_3><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
+    default: k_ens_row<ST_4><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
+    }
+}
+
+RkArgs ens_rk_args(kura_ctx* h, double step)
+{
+    EnsData& e = *h->ens;
+    RkArgs rk{};
+    rk.y = e.y.as<double>();
+    rk.y_out = e.y.as<double>();
+    rk.Y = e.Y.as<double>();
+    rk.krk = e.krk.as<double>();
+    rk.out = e.f.as<double>();
+    rk.h = step;
+    return rk;
+}
+
+void enqueue_ens_step(kura_ctx* h, double step, cudaStream_t s)
+{
+    const EnsArgs a = ens_args(h);
+    const RkArgs rk = ens_rk_args(h, step);
+    for (int st = ST_1; st <= ST_4; st++)
+        enqueue_ens_stage(h, a, st == ST_1 ? rk.y : rk.Y, rk, st, s);
+}
+
 // Bytes of the correction data one right-hand side reads: the listed indices
 // (4 B each), the sub-row headers (16 B each), the row bitmaps, and for
 // tensor-core tiles their mask bits and the digit blocks of their K-blocks.
@@ -386,6 +464,7 @@ kura_status check_single(kura_t h)
 {
     if (!h) return KURA_EINVAL;
     if (h->batch) return h->fail(KURA_ESTATE, "not available on a batch handle");
+    if (h->ens) return h->fail(KURA_ESTATE, "not available on an ensemble handle");
     cudaSetDevice(h->device);
     return KURA_OK;
 }
@@ -709,8 +788,15 @@ kura_status kura_sync(kura_t h)
     return read_flags(h);
 }
 
+static kura_status ens_rhs(kura_t h, const double* theta, double* dtheta);
+static kura_status ens_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps);
+
 kura_status kura_rhs(kura_t h, const double* theta, double* dtheta)
 {
+    if (h && h->ens) {
+        cudaSetDevice(h->device);
+        return ens_rhs(h, theta, dtheta);
+    }
     if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
     const double* th_dev;
@@ -748,6 +834,7 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
     if (!(step > 0) || !std::isfinite(step)) return h->fail(KURA_EINVAL, "step must be positive and finite");
     if (n_steps < 0) return h->fail(KURA_EINVAL, "n_steps must be >= 0");
     if (h->batch) return batch_rk4_steps(h, theta, step, n_steps);
+    if (h->ens) return ens_rk4_steps(h, theta, step, n_steps);
     const double* th_dev;
     bool host;
     if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
@@ -770,8 +857,10 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
             }
             cudaGraph_t graph = nullptr;
             KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            for (int64_t k = 0; k < c; k++)
-                enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            for (int64_t k = 0; k < c; k++) {
+                if (h->ens) enqueue_ens_step(h, step, h->cap);
+                else enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            }
             cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
             if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
             ec = cudaGraphInstantiate(&ge->exec, graph, 0);
@@ -978,8 +1067,10 @@ static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps)
             }
             cudaGraph_t graph = nullptr;
             KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            for (int64_t k = 0; k < c; k++)
-                enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            for (int64_t k = 0; k < c; k++) {
+                if (h->ens) enqueue_ens_step(h, step, h->cap);
+                else enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            }
             cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
             if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
             ec = cudaGraphInstantiate(&ge->exec, graph, 0);
@@ -991,6 +1082,180 @@ static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps)
         h->last_graph = it->second.get();
         left -= c;
     }
+    return KURA_OK;
+}
+
+// ---------------------------------------------------------------- ensembles sharing one graph
+// theta: n_traj x n (trajectory-major, user order), host or device
+static kura_status ens_stage_in(kura_t h, const double* src, const double** dev, bool* host)
+{
+    EnsData& e = *h->ens;
+    const size_t bytes = size_t(e.groups) * ENS_B * size_t(h->n) * 8;
+    *host = !is_device_ptr(src);
+    if (*host) {
+        KCHECK(h, cudaMemcpyAsync(e.user.p, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
+        *dev = e.user.as<double>();
+    } else {
+        *dev = src;
+    }
+    return KURA_OK;
+}
+
+static kura_status ens_rhs(kura_t h, const double* theta, double* dtheta)
+{
+    if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
+    EnsData& e = *h->ens;
+    const double* th;
+    bool host_in;
+    if (kura_status st = ens_stage_in(h, theta, &th, &host_in)) return st;
+    const bool host_out = !is_device_ptr(dtheta);
+    cudaStream_t s = h->stream;
+    const int64_t tot = int64_t(e.groups) * ENS_B * h->n;
+    const unsigned nb = blocks_for(tot, 256);
+    k_ens_gather<<<nb, 256, 0, s>>>(h->n, e.groups, h->perm.as<int32_t>(), th, e.Y.as<double>());
+    const EnsArgs a = ens_args(h);
+    const RkArgs rk = ens_rk_args(h, 0.0);
+    enqueue_ens_stage(h, a, rk.Y, rk, ST_RHS, s);
+    double* out = host_out ? e.user.as<double>() : dtheta;
+    k_ens_scatter<<<nb, 256, 0, s>>>(h->n, e.groups, h->perm.as<int32_t>(), e.f.as<double>(), out);
+    KCHECK(h, cudaGetLastError(), "launching the ensemble right-hand side");
+    if (host_out) {
+        KCHECK(h, cudaMemcpyAsync(dtheta, out, size_t(tot) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
+    }
+    return KURA_OK;
+}
+
+static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps);
+
+static kura_status ens_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
+{
+    EnsData& e = *h->ens;
+    const double* th;
+    bool host;
+    if (kura_status st = ens_stage_in(h, theta, &th, &host)) return st;
+    double* io = host ? e.user.as<double>() : theta;
+    cudaStream_t s = h->stream;
+    const int64_t tot = int64_t(e.groups) * ENS_B * h->n;
+    const unsigned nb = blocks_for(tot, 256);
+    k_ens_gather<<<nb, 256, 0, s>>>(h->n, e.groups, h->perm.as<int32_t>(), io, e.y.as<double>());
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    if (kura_status st = run_steps_perm(h, step, n_steps)) return st;
+    k_ens_scatter<<<nb, 256, 0, s>>>(h->n, e.groups, h->perm.as<int32_t>(), e.y.as<double>(), io);
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    if (host) {
+        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(tot) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
+    }
+    return KURA_OK;
+}
+
+kura_status kura_ensemble_create(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
+                                 int32_t n_comm, int32_t n_traj, const double* omega, const double* K,
+                                 const kura_opts* opts, void* stream, kura_t* out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
+    *out = nullptr;
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
+    if (n_traj <= 0 || n_traj % ENS_B) { g_create_error = "n_traj must be a positive multiple of 16"; return KURA_EINVAL; }
+    if (o.scaling != KURA_SCALING_UNIFORM) { g_create_error = "ensembles use uniform scaling"; return KURA_EINVAL; }
+    if (!omega || !K) { g_create_error = "omega or K is NULL"; return KURA_EINVAL; }
+    for (int64_t q = 0; q < int64_t(n_traj) * n; q++)
+        if (!std::isfinite(omega[q])) { g_create_error = "omega has a non-finite entry"; return KURA_EINVAL; }
+    for (int32_t b = 0; b < n_traj; b++)
+        if (!std::isfinite(K[b])) { g_create_error = "K has a non-finite entry"; return KURA_EINVAL; }
+    PlanInput in;
+    in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
+    in.tile_max_rows = TC_MBLOCK;                  // one M-block per CTA
+    in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
+    in.slot_ints = slot_ints_for(MODE_MIXED);
+    in.tensor_cores = o.tensor_cores > 0 ? 2 : 0;  // the mask product serves every trajectory of a group
+    Plan plan;
+    std::string err;
+    int rc = build_plan(in, plan, err);
+    if (rc) { g_create_error = err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(ce);
+        return KURA_ECUDA;
+    }
+    std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
+    if (!h) { g_create_error = "out of host memory"; return KURA_ENOMEM; }
+    cudaGetDevice(&h->device);
+    o.precision = KURA_PREC_MIXED;
+    h->opts = o;
+    h->n = n;
+    h->n_comm = n_comm;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->nnz = row_ptr[n];
+    h->ens.reset(new EnsData());
+    EnsData& e = *h->ens;
+    e.groups = n_traj / ENS_B;
+    auto fail = [&](cudaError_t c, const char* what) {
+        g_create_error = std::string(what) + ": " + cudaGetErrorString(c);
+        return c == cudaErrorMemoryAllocation ? KURA_ENOMEM : KURA_ECUDA;
+    };
+#define ECHECK(call, what) do { cudaError_t c_ = (call); if (c_ != cudaSuccess) return fail(c_, what); } while (0)
+    ECHECK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaStream_t s = h->stream;
+    const Plan& p = plan;
+    ECHECK(upload(h->perm, p.perm, s), "upload perm");
+    ECHECK(upload(e.node_comm, p.node_comm, s), "upload node_comm");
+    ECHECK(upload(e.comm_off, p.comm_off, s), "upload comm_off");
+    ECHECK(upload(e.dptr, p.dptr, s), "upload dptr");
+    ECHECK(upload(e.dcol, p.dcol, s), "upload dcol");
+    ECHECK(upload(e.tiles, p.tiles, s), "upload tiles");
+    ECHECK(upload(e.row_sub0, p.row_sub0, s), "upload row_sub0");
+    ECHECK(upload(e.sub_hdr, p.sub_hdr, s), "upload sub-row headers");
+    ECHECK(upload(e.sub_mpos, p.sub_mpos, s), "upload sub-row segments");
+    ECHECK(upload(e.sub_ppos, p.sub_ppos, s), "upload sub-row segments");
+    ECHECK(upload(e.gstream, p.gstream, s), "upload the correction stream");
+    ECHECK(upload(e.bitmap, p.bitmap, s), "upload masks");
+    const size_t G = size_t(e.groups), N = size_t(n), B = ENS_B;
+    {
+        std::vector<double> om(G * N * B), sc(G * B);
+        for (size_t g = 0; g < G; g++)
+            for (size_t i = 0; i < N; i++)
+                for (size_t b = 0; b < B; b++)
+                    om[(g * N + i) * B + b] = omega[(g * B + b) * N + size_t(p.perm[i])];
+        for (size_t q = 0; q < G * B; q++) sc[q] = K[q] / double(n);
+        ECHECK(upload(e.omega, om, s), "upload omega");
+        ECHECK(upload(e.scale, sc, s), "upload K");
+    }
+    e.nblk64 = 2 * ((int64_t(n) + TC_KBLOCK - 1) / TC_KBLOCK);
+    ECHECK(e.table.alloc(G * (N + 2) * B * sizeof(float2)), "alloc table");
+    ECHECK(cudaMemsetAsync(e.table.p, 0, e.table.bytes, s), "memset table");
+    ECHECK(e.image.alloc(G * size_t(e.nblk64) * ENS_BBYTES), "alloc image");
+    ECHECK(cudaMemsetAsync(e.image.p, 0, e.image.bytes, s), "memset image");
+    ECHECK(e.bsum.alloc(G * size_t(n_comm) * B * 16), "alloc block sums");
+    ECHECK(e.T.alloc(G * size_t(n_comm) * B * 16), "alloc T");
+    for (DevMem* d : {&e.y, &e.Y, &e.krk, &e.f, &e.user}) ECHECK(d->alloc(G * N * B * 8), "alloc state");
+    ECHECK(h->err_flags.alloc(16), "alloc error flags");
+    ECHECK(cudaMemsetAsync(h->err_flags.p, 0, 16, s), "memset error flags");
+    const void* fns[] = {(const void*)k_ens_row<ST_RHS>, (const void*)k_ens_row<ST_1>, (const void*)k_ens_row<ST_2>,
+                         (const void*)k_ens_row<ST_3>, (const void*)k_ens_row<ST_4>};
+    for (const void* fn : fns) ECHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ENS_SMEM),
+                                      "setting the ensemble kernel's shared-memory size");
+    ECHECK(cudaStreamSynchronize(s), "upload");
+#undef ECHECK
+    h->n_tiles = int32_t(p.tiles.size());
+    h->miss_total = p.miss_total;
+    h->pres_total = p.pres_total;
+    h->tc_tiles = p.tc_tiles;
+    h->tc_rows = p.tc_rows;
+    h->tc_mask_bits = p.tc_mask_bits;
+    h->has_tc = p.tc_tiles > 0;
+    h->stream_bytes = plan_stream_bytes(p);
+    h->q_bits = 61 - ceil_log2(std::max<int64_t>(n, 2));
+    h->plan = std::move(plan);
+    std::vector<int32_t>().swap(h->plan.gstream);
+    std::vector<uint32_t>().swap(h->plan.bitmap);
+    *out = h.release();
     return KURA_OK;
 }
 

@@ -196,6 +196,15 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// the same with BF16 (or F16) operands: tcgen05.mma.kind::f16
+__device__ __forceinline__ void tc_mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // arrive once on the mbarrier when every earlier tcgen05.mma of this thread has completed
 __device__ __forceinline__ void tc_commit(uint64_t* bar)
 {

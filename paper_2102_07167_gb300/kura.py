@@ -107,6 +107,7 @@ def load() -> C.CDLL:
             "kura_direct_rk4_steps": (S, [P, P, D, I64, I32]),
             "kura_set_timing": (S, [P, I32]),
             "kura_autotune": (S, [P, P, D, C.POINTER(KuraTuneResult)]),
+            "kura_ensemble_create": (S, [I64, P, P, P, I32, I32, P, P, C.POINTER(KuraOpts), P, C.POINTER(P)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
             "kura_sync": (S, [P]),
@@ -466,6 +467,64 @@ class Kuramoto:
 
     def kernel_times(self, cap=4096):
         return kura_kernel_times(self.h, cap)
+
+    def sync(self):
+        kura_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kura_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kura_ensemble_create(n, row_ptr, col, label, n_comm, omega, K, opts: Optional[KuraOpts] = None, stream=None):
+    """omega: (n_traj, n) array, K: (n_traj,) array; n_traj a multiple of 16."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    n_traj = int(K.shape[0])
+    if omega.shape != (n_traj, int(n)):
+        raise ValueError("omega must have shape (n_traj, n)")
+    h = C.c_void_p()
+    rc = load().kura_ensemble_create(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                     label.ctypes.data, int(n_comm), n_traj, omega.ctypes.data, K.ctypes.data,
+                                     C.byref(opts) if opts is not None else None, stream or None, C.byref(h))
+    _check(rc, None)
+    return h
+
+
+class KuramotoEnsemble:
+    """Trajectories sharing one graph (own omega and K each): phases are (n_traj, n) arrays or tensors."""
+
+    def __init__(self, row_ptr, col, label, n_comm, omega, K, tau=0.5, tensor_cores=1, stream=None):
+        self.n = int(np.asarray(row_ptr).shape[0] - 1)
+        self.n_traj = int(np.asarray(K).shape[0])
+        o = kura_default_opts()
+        o.precision, o.tau, o.tensor_cores = PREC_MIXED, float(tau), int(tensor_cores)
+        self.h = kura_ensemble_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
+
+    def rhs(self, theta, out):
+        kura_rhs(self.h, theta, out, self.n * self.n_traj)
+
+    def rk4_steps(self, theta, step, n_steps):
+        kura_rk4_steps(self.h, theta, step, n_steps, self.n * self.n_traj)
+
+    def stats(self):
+        return kura_get_stats(self.h)
 
     def sync(self):
         kura_sync(self.h)
