@@ -234,6 +234,62 @@ def bench_batch(dev, steps: int = 1000):
             "precision": "mixed (FP32 sin/cos and corrections, exact fixed-point block sums, FP64 epilogue/state)"}
 
 
+def bench_ensemble(dev, n_traj: int = 64, steps: int = 200):
+    """64 trajectories sharing the 65536-node SBM (64 communities, p_in 0.95, p_out 0.001): own omega ~ N(0,1),
+    K ~ U[0.5, 5] and theta0 ~ U[0, 2 pi) each; the dense-block product is a BF16 tensor-core GEMM over the
+    trajectories; h = 0.005. Next to it, one single-trajectory mixed-precision handle on the same graph."""
+    import torch
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_sbm_small()
+    g = w.graph
+    rng = np.random.default_rng(0)
+    omega = rng.normal(size=(n_traj, g.n))
+    K = rng.uniform(0.5, 5.0, n_traj)
+    theta = rng.uniform(0.0, 2 * np.pi, (n_traj, g.n))
+
+    def timed(obj, th, h):
+        obj.rk4_steps(th, h, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        obj.rk4_steps(th, h, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    with kura.KuramotoEnsemble(g.row_ptr, g.col, g.label, g.n_comm, omega, K) as e:
+        t_create = time.perf_counter() - t0
+        st = e.stats()
+        ms = timed(e, torch.tensor(theta, device=dev), 0.005)
+        # error of one right-hand side against the library's FP64 mode, a few trajectories
+        th = torch.tensor(theta, device=dev)
+        out = torch.empty_like(th)
+        e.rhs(th, out)
+        f = out.cpu().numpy()
+    errs = []
+    for b in (0, n_traj // 2, n_traj - 1):
+        with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, omega[b], K[b], precision=kura.PREC_FP64) as k64:
+            t64 = torch.tensor(theta[b], device=dev)
+            o64 = torch.empty_like(t64)
+            k64.rhs(t64, o64)
+            ref = o64.cpu().numpy()
+        errs.append(float(np.max(np.abs(f[b] - ref) / (1 + np.diff(g.row_ptr)))))
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, omega[0], K[0], precision=kura.PREC_MIXED) as k:
+        ms1 = timed(k, torch.tensor(theta[0], device=dev), 0.005)
+    v = g.n * n_traj * steps / (ms / 1e3)
+    v1 = g.n * steps / (ms1 / 1e3)
+    return {"workload": f"{n_traj} trajectories sharing the SBM N=65536 (64 communities, p_in 0.95, p_out 0.001); "
+                        "own omega, K ~ U[0.5, 5], theta0; h = 0.005",
+            "steps": steps, "ms": ms, "value": v, "unit": UNIT, "create_s": t_create,
+            "tensor_core_tiles": int(st["tc_tiles"]), "tiles": int(st["tiles"]),
+            "gemm": "per 128-row tile and 16 trajectories: BF16 0/1 mask x split BF16 (sin_hi, sin_lo, cos_hi, cos_lo), "
+                    "N = 64, FP32 accumulation (tcgen05.mma.kind::f16)",
+            "rhs_max_abs_err_over_1_plus_deg_vs_fp64_mode": max(errs),
+            "single_trajectory_handle": {"value": v1, "ms_per_step": ms1 / steps},
+            "speedup_per_oscillator_vs_single": v / v1}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -396,6 +452,8 @@ def run_ours(args):
         extra["adjoint"] = bench_adjoint(dev)
     if not args.quick and rank == 0 and not args.no_batch:
         extra["batch"] = bench_batch(dev)
+    if not args.quick and rank == 0 and not args.no_ensemble:
+        extra["ensemble_shared_graph"] = bench_ensemble(dev)
 
     cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds) if (rank == 0 and world == 1 and not args.quick) \
         else None
@@ -427,6 +485,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -82,7 +82,7 @@ struct BatchData {
 struct EnsData {
     int32_t groups = 0;
     int64_t nblk64 = 0;
-    DevMem comm_off, dptr, dcol, tiles, row_sub0, sub_hdr, sub_mpos, sub_ppos, gstream, bitmap, node_comm;
+    DevMem comm_off, dptr, dcol, tiles, lptr, lidx, bitmap, node_comm;
     DevMem table, image, bsum, T, omega, scale, y, Y, krk, f, user;
 };
 
@@ -292,11 +292,8 @@ EnsArgs ens_args(kura_ctx* h)
     a.dptr = e.dptr.as<int64_t>();
     a.dcol = e.dcol.as<int32_t>();
     a.tiles = e.tiles.as<Tile>();
-    a.row_sub0 = e.row_sub0.as<int32_t>();
-    a.sub_hdr = e.sub_hdr.as<int64_t>();
-    a.sub_mpos = e.sub_mpos.as<int64_t>();
-    a.sub_ppos = e.sub_ppos.as<int64_t>();
-    a.gstream = e.gstream.as<int32_t>();
+    a.lptr = e.lptr.as<int64_t>();
+    a.lidx = e.lidx.as<int32_t>();
     a.bitmap = e.bitmap.as<uint32_t>();
     a.table = e.table.as<float2>();
     a.image = e.image.as<__nv_bfloat16>();
@@ -1210,11 +1207,22 @@ kura_status kura_ensemble_create(int64_t n, const int64_t* row_ptr, const int32_
     ECHECK(upload(e.dptr, p.dptr, s), "upload dptr");
     ECHECK(upload(e.dcol, p.dcol, s), "upload dcol");
     ECHECK(upload(e.tiles, p.tiles, s), "upload tiles");
-    ECHECK(upload(e.row_sub0, p.row_sub0, s), "upload row_sub0");
-    ECHECK(upload(e.sub_hdr, p.sub_hdr, s), "upload sub-row headers");
-    ECHECK(upload(e.sub_mpos, p.sub_mpos, s), "upload sub-row segments");
-    ECHECK(upload(e.sub_ppos, p.sub_ppos, s), "upload sub-row segments");
-    ECHECK(upload(e.gstream, p.gstream, s), "upload the correction stream");
+    {
+        // per row, its listed entries in one run: present as the column, missing as ~column
+        std::vector<int64_t> lptr(size_t(n) + 1, 0);
+        std::vector<int32_t> lidx;
+        lidx.reserve(size_t(p.miss_total + p.pres_total));
+        for (int64_t v = 0; v < n; v++) {
+            for (int32_t sg = p.row_sub0[size_t(v)]; sg < p.row_sub0[size_t(v) + 1]; sg++) {
+                const int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
+                for (int32_t k = 0; k < hdr[1]; k++) lidx.push_back(~p.gstream[size_t(p.sub_mpos[size_t(sg)] + k)]);
+                for (int32_t k = 0; k < hdr[3]; k++) lidx.push_back(p.gstream[size_t(p.sub_ppos[size_t(sg)] + k)]);
+            }
+            lptr[size_t(v) + 1] = int64_t(lidx.size());
+        }
+        ECHECK(upload(e.lptr, lptr, s), "upload listed-entry offsets");
+        ECHECK(upload(e.lidx, lidx, s), "upload listed entries");
+    }
     ECHECK(upload(e.bitmap, p.bitmap, s), "upload masks");
     const size_t G = size_t(e.groups), N = size_t(n), B = ENS_B;
     {

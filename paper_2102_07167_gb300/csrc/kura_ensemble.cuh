@@ -11,7 +11,8 @@
 // Per stage of one group of ENS_B trajectories (blockIdx.y = group):
 //   k_ens_trig   FP32 (sin, cos) of the FP64-reduced phases -> node-major table
 //                and the split BF16 image of the mask product's B operand
-//   k_ens_bsum   S_J, C_J per community and trajectory (FP64, fixed order)
+//   k_ens_bsum   S_J, C_J per community and trajectory (compensated FP32 per
+//                thread, FP64 across threads, fixed order)
 //   k_ens_T      T_I = sum_{J in D(I)} (S_J, C_J)
 //   k_ens_row    mask product + listed gathers + FP64 epilogue and RK4 update
 #pragma once
@@ -50,11 +51,8 @@ struct EnsArgs {
     const int64_t* dptr;                      // [n_comm+1]
     const int32_t* dcol;
     const Tile* tiles;
-    const int32_t* row_sub0;                  // [n+1]
-    const int64_t* sub_hdr;                   // [n_sub] header position of each sub-row in gstream
-    const int64_t* sub_mpos;                  // [n_sub] its missing segment
-    const int64_t* sub_ppos;                  // [n_sub] its present segment
-    const int32_t* gstream;
+    const int64_t* lptr;                      // [n+1] listed entries of each row in lidx
+    const int32_t* lidx;                      // column (present: added) or ~column (missing: subtracted)
     const uint32_t* bitmap;                   // mask blocks of TILE_TC tiles
     float2* table;                            // [groups][n + 2][ENS_B]
     __nv_bfloat16* image;                     // [groups][nblk64][ENS_N][64] (swizzled blocks)
@@ -99,23 +97,29 @@ __global__ void __launch_bounds__(256) k_ens_trig(EnsArgs a, const double* __res
     if (bad) atomicOr(a.err, ERR_NONFINITE);
 }
 
-// One CTA per (community, group): FP64 sums of the table over the
-// community's nodes in a fixed order, per trajectory.
+// One CTA per (community, group): sums of the table over the community's
+// nodes in a fixed order, per trajectory.
 __global__ void __launch_bounds__(256) k_ens_bsum(EnsArgs a)
 {
     const int J = blockIdx.x, grp = blockIdx.y;
     const int b = threadIdx.x % ENS_B, part = threadIdx.x / ENS_B;     // 16 node lanes per trajectory
     const int64_t lo = a.comm_off[J], hi = a.comm_off[J + 1];
     const float2* tab = a.table + size_t(grp) * (a.n + 2) * ENS_B;
-    double s = 0.0, c = 0.0;
+    // per thread: compensated (Kahan-Neumaier) FP32 sums, full-rate arithmetic;
+    // across threads: FP64 in a fixed order
+    float s = 0.0f, es = 0.0f, c = 0.0f, ec = 0.0f;
     for (int64_t i = lo + part; i < hi; i += 256 / ENS_B) {
         const float2 v = tab[i * ENS_B + b];
-        s += static_cast<double>(v.x);
-        c += static_cast<double>(v.y);
+        float t1 = s + v.x;
+        es += fabsf(s) >= fabsf(v.x) ? (s - t1) + v.x : (v.x - t1) + s;
+        s = t1;
+        t1 = c + v.y;
+        ec += fabsf(c) >= fabsf(v.y) ? (c - t1) + v.y : (v.y - t1) + c;
+        c = t1;
     }
     __shared__ double rs[256], rc[256];
-    rs[threadIdx.x] = s;
-    rc[threadIdx.x] = c;
+    rs[threadIdx.x] = double(s) + double(es);
+    rc[threadIdx.x] = double(c) + double(ec);
     __syncthreads();
     if (threadIdx.x < ENS_B) {
         double ts = 0.0, tc = 0.0;
@@ -187,15 +191,18 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
     if (tid < ENS_EXP_THREADS) {
         // ---- mask expansion: thread r writes row r of each 128 x 64 tile as BF16 1.0 / 0
         const int r = tid;
+        // words 2 h, 2 h + 1 of row r of 128-column block kb = q / 2 (h = q mod 2), loaded one tile ahead
+        const uint2* bits = reinterpret_cast<const uint2*>(a.bitmap + t.bm_off) + size_t(r) * 2;
+        uint2 nxt = nT > 0 ? __ldg(bits) : make_uint2(0u, 0u);
         for (int q = 0; q < nT; q++) {
             const int st = q & 1, use = q >> 1;
+            const uint2 w = nxt;
+            if (q + 1 < nT) nxt = __ldg(bits + size_t((q + 1) >> 1) * TC_MBLOCK * 2 + ((q + 1) & 1));
             if (use > 0 && !mbar_wait_bounded(&a_empty[st], uint32_t(use - 1) & 1u, LIMIT_NS)) {
                 atomicOr(a.err, ERR_TIMEOUT);
                 fail_flag = 1;
                 break;
             }
-            // words 2 h, 2 h + 1 of row r of 128-column block kb (h = q mod 2)
-            const uint2 w = __ldg(reinterpret_cast<const uint2*>(a.bitmap + t.bm_off) + (size_t(q >> 1) * TC_MBLOCK + r) * 2 + (q & 1));
             unsigned char* row = A_ + st * ENS_ABYTES + r * 128;
 #pragma unroll
             for (int c = 0; c < 8; c++) {              // 8 columns -> 16 bytes
@@ -250,36 +257,39 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
             }
         }
     } else {
-        // ---- listed entries: a warp per row; lane l holds trajectory l / 2, component l mod 2
+        // ---- listed entries: a warp per row; lane l holds trajectory l / 2, component l mod 2.
+        // The next row's range and each segment's next 32 indices are loaded ahead; all 32 row
+        // loads of a round are in flight before any is summed; lanes past the end read the
+        // table's zero entry n.
         const float* tabf = reinterpret_cast<const float*>(tab);
-        for (int r = warp - ENS_LIST_WARP0; r < nrows; r += 16 - ENS_LIST_WARP0) {
-            const int64_t row = int64_t(t.r0) + r;
+        constexpr int LW = 16 - ENS_LIST_WARP0;
+        int r = warp - ENS_LIST_WARP0;
+        int64_t beg = 0, end = 0;
+        if (r < nrows) { beg = a.lptr[t.r0 + r]; end = a.lptr[t.r0 + r + 1]; }
+        const int zero = int(a.n);
+        while (r < nrows) {
+            int64_t nbeg = 0, nend = 0;
+            if (r + LW < nrows) { nbeg = a.lptr[t.r0 + r + LW]; nend = a.lptr[t.r0 + r + LW + 1]; }
+            const int cnt = int(end - beg);
             float acc = 0.0f;
-            for (int s = a.row_sub0[row]; s < a.row_sub0[row + 1]; s++) {
-                const int4 hdr = *reinterpret_cast<const int4*>(a.gstream + a.sub_hdr[s]);
+            int nidx = lane < cnt ? a.lidx[beg + lane] : zero;
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int idx = nidx;
+                if (k0 + 32 < cnt) nidx = k0 + 32 + lane < cnt ? a.lidx[beg + k0 + 32 + lane] : zero;
+                float v[32];
 #pragma unroll
-                for (int part = 0; part < 2; part++) {
-                    const int64_t pos = part ? a.sub_ppos[s] : a.sub_mpos[s];
-                    const int cnt = part ? hdr.w : hdr.y;
-                    const float sgn = part ? 1.0f : -1.0f;
-                    for (int k0 = 0; k0 < cnt; k0 += 32) {
-                        const int m = min(32, cnt - k0);
-                        const int idx = lane < m ? a.gstream[pos + k0 + lane] : 0;
-                        float part_sum = 0.0f;
-                        int kk = 0;
-                        for (; kk + 8 <= m; kk += 8) {
-                            float v[8];
-#pragma unroll
-                            for (int u = 0; u < 8; u++) v[u] = __ldg(tabf + size_t(__shfl_sync(0xffffffffu, idx, kk + u)) * (2 * ENS_B) + lane);
-#pragma unroll
-                            for (int u = 0; u < 8; u++) part_sum += v[u];
-                        }
-                        for (; kk < m; kk++) part_sum += __ldg(tabf + size_t(__shfl_sync(0xffffffffu, idx, kk)) * (2 * ENS_B) + lane);
-                        acc += sgn * part_sum;
-                    }
+                for (int u = 0; u < 32; u++) {
+                    const int j = __shfl_sync(0xffffffffu, idx, u);
+                    const float e = __ldg(tabf + size_t(j >= 0 ? j : ~j) * (2 * ENS_B) + lane);
+                    v[u] = j >= 0 ? e : -e;
                 }
+#pragma unroll
+                for (int u = 0; u < 32; u++) acc += v[u];
             }
             stash[r][lane] = acc;
+            r += LW;
+            beg = nbeg;
+            end = nend;
         }
     }
     __syncthreads();
@@ -302,11 +312,13 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
 #pragma unroll
         for (int bb = 0; bb < 4; bb++) {
             const int b = b0 + bb;
-            const double ms = double(__uint_as_float(d[4 * bb])) + double(__uint_as_float(d[4 * bb + 1]));
-            const double mc = double(__uint_as_float(d[4 * bb + 2])) + double(__uint_as_float(d[4 * bb + 3]));
+            // corrections (FP32 sums of FP32 terms: missing from the mask product, hi + lo;
+            // listed from the gathers) in FP32, added to the FP64 block sums in FP64
+            const float cs = (__uint_as_float(d[4 * bb]) + __uint_as_float(d[4 * bb + 1])) - stash[r][2 * b];
+            const float cc = (__uint_as_float(d[4 * bb + 2]) + __uint_as_float(d[4 * bb + 3])) - stash[r][2 * b + 1];
             const double2 T = a.T[(size_t(grp) * a.n_comm + t.comm) * ENS_B + b];
-            const double acc_s = T.x - ms + double(stash[r][2 * b]);
-            const double acc_c = T.y - mc + double(stash[r][2 * b + 1]);
+            const double acc_s = T.x - double(cs);
+            const double acc_c = T.y - double(cc);
             const float2 own = tab[size_t(row) * ENS_B + b];
             const double f = a.omega[base + b] + a.scale[grp * ENS_B + b] *
                                                      (double(own.y) * acc_s - double(own.x) * acc_c);
