@@ -383,6 +383,17 @@ def run_ours(args):
                 "present_gather_rate_per_s": (st["sparse_entries"] / (row_ms * 1e-3)) if row_ms else None,
                 "tensor_core_tiles": int(st["tc_tiles"]), "tiles": int(st["tiles"])}
 
+    # ---- the bound the row kernel actually meets: random L2 gathers of its sparse-block entries,
+    # against the rate this device reaches on the same kind of gathers (measured now, same process)
+    gather_peak = kura.kura_measure_gather_rate(1 << 20, 1 << 28, 8 if args.precision == "mixed" else 16)
+    gather_rate = (st["sparse_entries"] / (row_ms * 1e-3)) if row_ms else None
+    gather_roofline = {"bound": "l2_random_gather", "achieved": gather_rate, "peak": gather_peak,
+                       "unit": "gathers/s", "frac": (gather_rate / gather_peak) if gather_rate else None,
+                       "peak_source": "measured in this run (kura_measure_gather_rate): 2^28 random "
+                                      f"{8 if args.precision == 'mixed' else 16}-byte gathers from an L2-resident "
+                                      "2^20-entry table, four per 16-byte index load, full occupancy, median of 3",
+                       "kernel": "k_row_stage"}
+
     # ---- e2e: the public call with pinned HOST phases, copies inside every step
     e2e = None
     if not args.no_e2e:
@@ -464,7 +475,7 @@ def run_ours(args):
                 "dtype": "f32+f64" if prec == kura.PREC_MIXED else "f64", "data": "synthetic",
                 "config": dict(_workload_desc(w, st), precision=args.precision,
                                parallelism="replicas" if world > 1 else "single-gpu"),
-                "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+                "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "gather_roofline": gather_roofline,
                 "cpu_baseline": cpu, "clocks": clk.summary()}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -278,6 +278,18 @@ typedef struct {
  * KURA_ESTATE.  Synchronous.  Not available on batch handles. */
 kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out);
 
+/* Measurement for rooflines (not part of the method): the median rate, in
+ * gathers per second, of random entry_bytes-byte (8 or 16) loads from a
+ * table of table_entries entries (<= 2^30), as the row kernel makes for the
+ * entries of sparse blocks.  Indices are counter-based hashes of the
+ * position, uniform over the table; the table is L2-resident when it is
+ * small enough.  gathers in [4096, 2^31] are made per run, four per 16-byte
+ * index load, at full occupancy; one warm-up run, median of three timed
+ * runs (CUDA events on stream).  Allocates and frees its own device memory;
+ * synchronous.  KURA_EINVAL for sizes out of range. */
+kura_status kura_measure_gather_rate(int64_t table_entries, int64_t gathers, int32_t entry_bytes, void* stream,
+                                     double* gathers_per_s);
+
 /* Switches the handle to another stream (cached graphs stay valid). */
 kura_status kura_set_stream(kura_t h, void* stream);
 

@@ -108,6 +108,7 @@ def load() -> C.CDLL:
             "kura_set_timing": (S, [P, I32]),
             "kura_autotune": (S, [P, P, D, C.POINTER(KuraTuneResult)]),
             "kura_ensemble_create": (S, [I64, P, P, P, I32, I32, P, P, C.POINTER(KuraOpts), P, C.POINTER(P)]),
+            "kura_measure_gather_rate": (S, [I64, I64, I32, P, C.POINTER(D)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
             "kura_sync": (S, [P]),
@@ -325,6 +326,15 @@ def kura_autotune(h, theta, n, budget_s=30.0) -> dict:
     r = KuraTuneResult()
     _check(load().kura_autotune(h, _ptr(theta, n=n), float(budget_s), C.byref(r)), h)
     return r.as_dict()
+
+
+def kura_measure_gather_rate(table_entries=1 << 20, gathers=1 << 28, entry_bytes=8, stream=None) -> float:
+    """Random-gather rate of this device (gathers/s) from an L2-resident table: the peak of the row kernel's
+    sparse-block gathers."""
+    r = C.c_double()
+    _check(load().kura_measure_gather_rate(int(table_entries), int(gathers), int(entry_bytes), stream or None,
+                                           C.byref(r)), None)
+    return r.value
 
 
 def kura_destroy(h):

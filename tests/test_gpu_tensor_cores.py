@@ -170,3 +170,10 @@ def test_autotune_keeps_the_right_hand_side(sbm_small):
         assert abs(st["tau"] - res["tau"]) < 1e-12
     ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
     assert np.all(np.abs(f - ref) <= 1e-11 * (1 + np.diff(g.row_ptr)))
+
+
+def test_gather_rate_probe():
+    """The roofline probe measures a plausible random-gather rate (between 10^10 and 10^13 per second)."""
+    r8 = kura.kura_measure_gather_rate(1 << 20, 1 << 24, 8)
+    r16 = kura.kura_measure_gather_rate(1 << 20, 1 << 24, 16)
+    assert 1e10 < r8 < 1e13 and 1e10 < r16 < 1e13

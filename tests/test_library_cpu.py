@@ -324,3 +324,13 @@ def test_missing_entries_are_bank_balanced(prec):
     maxima = np.array(maxima)
     assert maxima.size > 100 and maxima.mean() <= ideal + 0.5 and np.percentile(maxima, 99) <= ideal + 3, \
         (maxima.size, maxima.mean(), np.percentile(maxima, 99))
+
+
+def test_gather_rate_probe_rejects_bad_sizes():
+    """Argument checks of the roofline probe run before any CUDA call."""
+    import ctypes as C
+    L = kura.load()
+    r = C.c_double()
+    for args in ((0, 1 << 20, 8), (1 << 20, 100, 8), (1 << 20, 1 << 20, 12), (1 << 31, 1 << 20, 8)):
+        assert L.kura_measure_gather_rate(*args, None, C.byref(r)) == kura.KURA_EINVAL
+    assert L.kura_measure_gather_rate(1 << 20, 1 << 20, 8, None, None) == kura.KURA_EINVAL
