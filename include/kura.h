@@ -165,6 +165,24 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
 kura_status kura_order_params(kura_t h, const double* theta, double* r, double* psi,
                               double* r_comm, double* psi_comm);
 
+/* Graph potential of eq:ExtendedPotentialConservation at theta[n] (user
+ * order, device or host):
+ *   V = -sum_m omega_m theta_m + (K/2) sum_m (1/calM_m) sum_l A_{ml} (1 - cos(theta_l - theta_m)),
+ * rows without neighbours contributing no coupling term.  The inner sums use
+ * the cosine identity sum_l A_{ml} cos(theta_l - theta_m) = cos theta_m
+ * (A cos theta)_m + sin theta_m (A sin theta)_m, with the row sums of the
+ * block method (one right-hand-side pass) and FP64 sin/cos of theta_m; the
+ * reduction over m is FP64 in a fixed order (deterministic).  For symmetric
+ * A and uniform scaling the flow is a gradient flow of V, so V does not
+ * increase along trajectories.  *V: host.  Synchronises the stream. */
+kura_status kura_potential(kura_t h, const double* theta, double* V);
+
+/* eq:Means: (1/n) sum_m (theta_m(t) - theta_m(0) - t omega_m) of theta_t and
+ * theta_0 (user order, device or host); zero at all t for symmetric A with
+ * uniform scaling (the coupling terms cancel in pairs).  FP64, fixed-order
+ * reduction.  *out: host.  Synchronises the stream. */
+kura_status kura_mean_deviation(kura_t h, const double* theta_t, const double* theta_0, double t, double* out);
+
 /* Gradient of a terminal loss of an RK4 trajectory by the discrete adjoint
  * of the classical RK4 step (backward sweep over the stage Jacobians of
  * eq:KuramotoGraph; the paper's integrator section, Sec. 2, extended to a

@@ -116,6 +116,7 @@ struct kura_ctx {
     int64_t ad_M = 0, ad_nck = 0;
     int sym = -1;   // host CSR symmetric? (-1 unknown)
     DevMem y, Y, krk, fbuf, user, red, order_out;
+    DevMem deg, sums, diag;                   // diagnostics: degrees, row sums, partials (lazily)
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
     int q_bits = 0;
     int32_t n_tiles = 0, max_wlen = 0;
@@ -444,6 +445,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     // the correction stream now lives on the device
     std::vector<int32_t>().swap(p.gstream);
     std::vector<uint32_t>().swap(p.bitmap);
+    h->deg.release();
     h->graphs.clear();
     h->last_graph = nullptr;
     return KURA_OK;
@@ -875,6 +877,78 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
         KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
         return read_flags(h);
     }
+    return KURA_OK;
+}
+
+kura_status kura_potential(kura_t h, const double* theta, double* V)
+{
+    if (kura_status st0 = check_single(h)) return st0;
+    if (!theta || !V) return h->fail(KURA_EINVAL, "NULL argument");
+    const int64_t n = h->n;
+    const int64_t nb = (n + DIAG_THREADS - 1) / DIAG_THREADS;
+    if (!h->deg.p) {
+        // degree plus 1 where the row's own diagonal block is dense: its block sums then include the
+        // don't-care self term, which adds cos 0 = 1 to the row's cosine sum (and sin 0 = 0 elsewhere)
+        const Plan& p = h->plan;
+        std::vector<int32_t> degx(static_cast<size_t>(n));
+        for (int64_t v = 0; v < n; v++) {
+            const int32_t I = p.node_comm[size_t(v)];
+            const bool self = std::binary_search(p.dcol.begin() + p.dptr[size_t(I)], p.dcol.begin() + p.dptr[size_t(I) + 1], I);
+            degx[size_t(v)] = p.deg[size_t(v)] + (self ? 1 : 0);
+        }
+        KCHECK(h, upload(h->deg, degx, h->stream), "upload degrees");
+        KCHECK(h, cudaStreamSynchronize(h->stream), "upload degrees");
+    }
+    if (!h->sums.p) KCHECK(h, h->sums.alloc(size_t(n) * 16), "alloc row sums");
+    if (h->diag.bytes < size_t(nb + 1) * 8) KCHECK(h, h->diag.alloc(size_t(nb + 1) * 8), "alloc partials");
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    cudaStream_t s = h->stream;
+    const DevGraph g = dev_graph(h);
+    RkArgs rk = rk_args(h, 0.0);
+    rk.sums_out = h->sums.as<double2>();
+    k_gather_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, h->perm.as<int32_t>(), th_dev, h->Y.as<double>());
+    if (h->opts.precision == KURA_PREC_MIXED) {
+        launch_trig<MODE_MIXED>(h, g, h->Y.as<double>(), TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_MIXED>(h, g, rk, ST_RHS, s);
+    } else {
+        launch_trig<MODE_FP64>(h, g, h->Y.as<double>(), TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_FP64>(h, g, rk, ST_RHS, s);
+    }
+    double* part = h->diag.as<double>();
+    k_potential_terms<<<unsigned(nb), DIAG_THREADS, 0, s>>>(g, h->Y.as<double>(), h->sums.as<double2>(),
+                                                             h->deg.as<int32_t>(), h->K, part);
+    k_sum_partials<<<1, DIAG_THREADS, 0, s>>>(part, nb, part + nb);
+    KCHECK(h, cudaGetLastError(), "launching the potential");
+    KCHECK(h, cudaMemcpyAsync(V, part + nb, 8, cudaMemcpyDeviceToHost, s), "copy V");
+    return read_flags(h);
+}
+
+kura_status kura_mean_deviation(kura_t h, const double* theta_t, const double* theta_0, double t, double* out)
+{
+    if (kura_status st0 = check_single(h)) return st0;
+    if (!theta_t || !theta_0 || !out || !std::isfinite(t)) return h->fail(KURA_EINVAL, "NULL argument or non-finite t");
+    const int64_t n = h->n;
+    const int64_t nb = (n + DIAG_THREADS - 1) / DIAG_THREADS;
+    if (h->diag.bytes < size_t(nb + 1) * 8) KCHECK(h, h->diag.alloc(size_t(nb + 1) * 8), "alloc partials");
+    cudaStream_t s = h->stream;
+    const DevGraph g = dev_graph(h);
+    const double* dev;
+    bool host;
+    // theta_t -> Y, theta_0 -> krk (permuted); both staged through the user buffer when on the host
+    if (kura_status st = stage_in(h, theta_t, &dev, &host)) return st;
+    k_gather_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, h->perm.as<int32_t>(), dev, h->Y.as<double>());
+    if (kura_status st = stage_in(h, theta_0, &dev, &host)) return st;
+    k_gather_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, h->perm.as<int32_t>(), dev, h->krk.as<double>());
+    double* part = h->diag.as<double>();
+    k_meandev_terms<<<unsigned(nb), DIAG_THREADS, 0, s>>>(g, h->Y.as<double>(), h->krk.as<double>(), t, part);
+    k_sum_partials<<<1, DIAG_THREADS, 0, s>>>(part, nb, part + nb);
+    KCHECK(h, cudaGetLastError(), "launching the mean deviation");
+    double v = 0.0;
+    KCHECK(h, cudaMemcpyAsync(&v, part + nb, 8, cudaMemcpyDeviceToHost, s), "copy result");
+    if (kura_status st = read_flags(h)) return st;
+    *out = v / double(n);
     return KURA_OK;
 }
 

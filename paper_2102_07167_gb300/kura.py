@@ -109,6 +109,8 @@ def load() -> C.CDLL:
             "kura_autotune": (S, [P, P, D, C.POINTER(KuraTuneResult)]),
             "kura_ensemble_create": (S, [I64, P, P, P, I32, I32, P, P, C.POINTER(KuraOpts), P, C.POINTER(P)]),
             "kura_measure_gather_rate": (S, [I64, I64, I32, P, C.POINTER(D)]),
+            "kura_potential": (S, [P, P, C.POINTER(D)]),
+            "kura_mean_deviation": (S, [P, P, P, D, C.POINTER(D)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
             "kura_sync": (S, [P]),
@@ -337,6 +339,18 @@ def kura_measure_gather_rate(table_entries=1 << 20, gathers=1 << 28, entry_bytes
     return r.value
 
 
+def kura_potential(h, theta, n) -> float:
+    v = C.c_double()
+    _check(load().kura_potential(h, _ptr(theta, n=n), C.byref(v)), h)
+    return v.value
+
+
+def kura_mean_deviation(h, theta_t, theta_0, t, n) -> float:
+    v = C.c_double()
+    _check(load().kura_mean_deviation(h, _ptr(theta_t, n=n), _ptr(theta_0, n=n), float(t), C.byref(v)), h)
+    return v.value
+
+
 def kura_destroy(h):
     load().kura_destroy(h)
 
@@ -450,6 +464,14 @@ class Kuramoto:
 
     def stats(self):
         return kura_get_stats(self.h)
+
+    def potential(self, theta):
+        """Graph potential V (kura_potential)."""
+        return kura_potential(self.h, theta, self.n)
+
+    def mean_deviation(self, theta_t, theta_0, t):
+        """(1/n) sum (theta_t - theta_0 - t omega) (kura_mean_deviation)."""
+        return kura_mean_deviation(self.h, theta_t, theta_0, t, self.n)
 
     def autotune(self, theta, budget_s=30.0):
         """Times the right-hand side at theta for candidate plans and keeps the fastest (see kura_autotune)."""

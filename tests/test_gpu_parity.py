@@ -297,3 +297,38 @@ def test_nonfinite_state_is_reported(sbm_small):
             k.sync()
         assert e.value.status == kura.KURA_ENUMERIC
         k.sync()      # latched condition was cleared
+
+
+# ----------------------------------------------------------------------------- diagnostics (NEXT-2)
+@pytest.mark.parametrize("prec,scaling", [(0, 0), (1, 0), (0, 1)])
+def test_potential_vs_oracle(sbm_small, prec, scaling):
+    """V of eq:ExtendedPotentialConservation from the block method's row sums (cosine identity) against the
+    oracle's edge-by-edge sum."""
+    w = sbm_small
+    g = w.graph
+    ref = oracle.potential_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, scaling)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec, scaling=scaling) as k:
+        V = k.potential(_dev(w.theta0))
+        Vh = k.potential(np.ascontiguousarray(w.theta0))
+    assert V == Vh
+    tol = (1e-9 if prec == 0 else 1e-5) * max(1.0, abs(ref))
+    assert abs(V - ref) <= tol, (V, ref)
+
+
+def test_potential_decreases_and_mean_is_conserved(sbm_small):
+    """Symmetric A, uniform scaling: the flow is a gradient flow of V (V non-increasing along the RK4
+    trajectory, up to the integrator's error) and the mean deviation of eq:Means stays zero."""
+    w = sbm_small
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=0) as k:
+        th = _dev(w.theta0)
+        th0 = th.clone()
+        Vs = [k.potential(th)]
+        for _ in range(5):
+            k.rk4_steps(th, w.h, 10)
+            Vs.append(k.potential(th))
+        md = k.mean_deviation(th, th0, 50 * w.h)
+    assert all(b <= a + 1e-9 * max(1.0, abs(a)) for a, b in zip(Vs, Vs[1:])), Vs
+    assert abs(md) < 1e-10, md
+    ref_md = oracle.mean_deviation(th.cpu().numpy(), w.theta0, w.omega, 50 * w.h)
+    assert abs(md - ref_md) < 1e-12
