@@ -63,10 +63,11 @@ def _load():
         L.orc_mean_deviation.argtypes = [I64, _d, _d, _d, D, C.POINTER(D)]
         L.orc_adjoint_rk4_csr.argtypes = [I64, _i64, _i32, _d, D, C.c_int, _d, D, I64, C.c_int, C.c_void_p,
                                           C.POINTER(D), _d, C.POINTER(D), _d]
+        L.orc_rk2_csr.argtypes = [I64, _i64, _i32, _d, D, C.c_int, _d, D, I64, C.c_int, C.c_int]
         L.orc_trig_count.restype = C.c_int64
         for f in ("orc_rhs_dense", "orc_rhs_csr", "orc_rhs_csr_rows", "orc_rhs_complete_op",
                   "orc_rhs_block", "orc_rk4_csr", "orc_rk4_complete", "orc_order_params",
-                  "orc_potential_csr", "orc_mean_deviation", "orc_adjoint_rk4_csr"):
+                  "orc_potential_csr", "orc_mean_deviation", "orc_adjoint_rk4_csr", "orc_rk2_csr"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -143,6 +144,17 @@ def rk4_csr(row_ptr, col, omega, K, theta0, h, n_steps, scaling=0):
     th = _f64(theta0).copy()
     _check(_load().orc_rk4_csr(row_ptr.shape[0] - 1, row_ptr, np.ascontiguousarray(col, dtype=np.int32),
                                _f64(omega), float(K), int(scaling), th, float(h), int(n_steps)), "rk4_csr")
+    return th
+
+
+def rk2_csr(row_ptr, col, omega, K, theta0, h, n_steps, method=0, iters=4, scaling=0):
+    """Second-order integrators: method 0 explicit midpoint, 1 implicit midpoint (`iters` fixed-point
+    sweeps of the stage from the explicit predictor)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    th = _f64(theta0).copy()
+    _check(_load().orc_rk2_csr(row_ptr.shape[0] - 1, row_ptr, np.ascontiguousarray(col, dtype=np.int32),
+                               _f64(omega), float(K), int(scaling), th, float(h), int(n_steps), int(method),
+                               int(iters)), "rk2_csr")
     return th
 
 

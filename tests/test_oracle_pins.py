@@ -391,3 +391,46 @@ def test_adjoint_uncoupled_closed_form():
     np.testing.assert_allclose(g_th, resid, atol=1e-12, rtol=0)
     np.testing.assert_allclose(g_om, T * resid, atol=1e-12, rtol=0)
     assert abs(L - 0.5 * resid @ resid) < 1e-11
+
+
+# ----------------------------------------------------------------------------- second-order integrators (NEXT-3)
+@pytest.mark.parametrize("method", [0, 1])
+def test_rk2_free_rotation_when_uncoupled(method):
+    """K = 0: both second-order methods integrate theta' = omega exactly."""
+    w = G.workload_sbm_small(n=1000, n_comm=4, min_size=100)
+    th = oracle.rk2_csr(w.graph.row_ptr, w.graph.col, w.omega, 0.0, w.theta0, 0.01, 50, method, 3)
+    np.testing.assert_allclose(th, w.theta0 + 0.5 * w.omega, atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_rk2_two_oscillators_adler_second_order(method):
+    """M = 2 against the Adler closed form: the error shrinks ~4x when h halves (second order), and
+    theta_1 + theta_2 advances exactly as (omega_1 + omega_2) t (linear invariant, eq:5c)."""
+    K, T, dw = 2.0, 1.0, 0.5
+    omega = np.array([0.3, 0.3 + dw])
+    th0 = np.array([0.2, 0.9])
+    g = G.complete(2)
+    phi_ex = _adler_phi(th0[1] - th0[0], dw, K, T)
+    errs = []
+    for nst in (40, 80, 160, 320):
+        th = oracle.rk2_csr(g.row_ptr, g.col, omega, K, th0, T / nst, nst, method, 12)
+        assert abs((th[0] + th[1]) - (th0.sum() + omega.sum() * T)) < 1e-13
+        errs.append(abs((th[1] - th[0]) - phi_ex))
+    ratios = [e1 / e2 for e1, e2 in zip(errs, errs[1:])]
+    assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
+
+
+def test_implicit_midpoint_solves_its_stage_equation_and_is_symmetric():
+    """Implicit midpoint: the step satisfies y' = y + h f((y + y')/2) (residual at rounding level after enough
+    sweeps), and a step with h followed by one with -h returns to y (a symmetric method); explicit midpoint
+    does not return."""
+    w = G.workload_sbm_small(n=800, n_comm=4, min_size=100)
+    g, h = w.graph, 0.02
+    y1 = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, h, 1, 1, 30)
+    f_mid = oracle.rhs_csr(g.row_ptr, g.col, w.omega, 0.5 * (w.theta0 + y1), w.K)
+    assert np.max(np.abs(y1 - w.theta0 - h * f_mid)) < 1e-13
+    back = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, y1, -h, 1, 1, 30)
+    assert np.max(np.abs(back - w.theta0)) < 1e-12
+    ye = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, h, 1, 0, 1)
+    backe = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, ye, -h, 1, 0, 1)
+    assert np.max(np.abs(backe - w.theta0)) > 1e-9
