@@ -157,6 +157,21 @@ kura_status kura_rhs(kura_t h, const double* theta, double* dtheta);
  * unwrapped (eq:5c). */
 kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps);
 
+enum { KURA_INT_RK4 = 0, KURA_INT_RK2 = 1, KURA_INT_IMPLICIT_MIDPOINT = 2 };
+
+/* n_steps steps of a chosen integrator on theta[n] in place (user order,
+ * device or host), with the block method as right-hand side:
+ *   KURA_INT_RK4                as kura_rk4_steps (iters ignored);
+ *   KURA_INT_RK2                explicit midpoint, Y = y + h/2 f(y), y' = y + h f(Y);
+ *   KURA_INT_IMPLICIT_MIDPOINT  y' = 2 Z - y where Z = y + h/2 f(Z), the stage
+ *                               found by `iters` (1..64) fixed-point sweeps from
+ *                               the predictor y + h/2 f(y); a symmetric,
+ *                               second-order geometric method.
+ * The paper compares a second-order explicit Runge-Kutta method with a
+ * second-order implicit one for the conserved quantity of eq:5c over long
+ * times (Sec. 2, numerical results).  Steps run as cached CUDA graphs. */
+kura_status kura_integrate(kura_t h, double* theta, double step, int64_t n_steps, int32_t method, int32_t iters);
+
 /* Order parameters (eq:OrderParameter): r e^{i psi} = (1/n) sum_m e^{i theta_m}
  * of theta[n] (user order, device or host); r, psi: host scalars.  When
  * r_comm / psi_comm (host, n_comm entries each, nullable) are given, the

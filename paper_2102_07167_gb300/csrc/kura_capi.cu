@@ -281,6 +281,41 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
     }
 }
 
+// f(X) -> fbuf for a permuted state X (trig + row kernel, right-hand-side stage)
+void enqueue_rhs_of(kura_ctx* h, const DevGraph& g, const double* X, cudaStream_t s)
+{
+    RkArgs rk = rk_args(h, 0.0);
+    if (h->opts.precision == KURA_PREC_MIXED) {
+        launch_trig<MODE_MIXED>(h, g, X, TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_MIXED>(h, g, rk, ST_RHS, s);
+    } else {
+        launch_trig<MODE_FP64>(h, g, X, TB_TABLE | TB_T, s);
+        launch_row_stage<MODE_FP64>(h, g, rk, ST_RHS, s);
+    }
+}
+
+// One step of explicit (method 1) or implicit (method 2, `iters` sweeps) midpoint on y; stage in Y.
+void enqueue_rk2_step(kura_ctx* h, double step, int method, int iters, cudaStream_t s)
+{
+    const DevGraph g = dev_graph(h);
+    const unsigned nb = blocks_for(h->n, 256);
+    double* y = h->y.as<double>();
+    double* Z = h->Y.as<double>();
+    double* f = h->fbuf.as<double>();
+    enqueue_rhs_of(h, g, y, s);
+    k_axpy<<<nb, 256, 0, s>>>(h->n, Z, y, 0.5 * step, f);
+    if (method == KURA_INT_RK2) {
+        enqueue_rhs_of(h, g, Z, s);
+        k_axpy<<<nb, 256, 0, s>>>(h->n, y, y, step, f);
+        return;
+    }
+    for (int it = 0; it < iters; it++) {
+        enqueue_rhs_of(h, g, Z, s);
+        k_axpy<<<nb, 256, 0, s>>>(h->n, Z, y, 0.5 * step, f);
+    }
+    k_midpoint_final<<<nb, 256, 0, s>>>(h->n, y, Z);
+}
+
 EnsArgs ens_args(kura_ctx* h)
 {
     EnsData& e = *h->ens;
@@ -1152,6 +1187,55 @@ static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps)
         KCHECK(h, cudaGraphLaunch(it->second->exec, h->stream), "graph launch");
         h->last_graph = it->second.get();
         left -= c;
+    }
+    return KURA_OK;
+}
+
+kura_status kura_integrate(kura_t h, double* theta, double step, int64_t n_steps, int32_t method, int32_t iters)
+{
+    if (method == KURA_INT_RK4) return kura_rk4_steps(h, theta, step, n_steps);
+    if (kura_status st0 = check_single(h)) return st0;
+    if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
+    if (!(step > 0) || !std::isfinite(step)) return h->fail(KURA_EINVAL, "step must be positive and finite");
+    if (n_steps < 0) return h->fail(KURA_EINVAL, "n_steps must be >= 0");
+    if (method != KURA_INT_RK2 && method != KURA_INT_IMPLICIT_MIDPOINT) return h->fail(KURA_EINVAL, "unknown method");
+    if (method == KURA_INT_IMPLICIT_MIDPOINT && (iters < 1 || iters > 64)) return h->fail(KURA_EINVAL, "iters in 1..64");
+    if (method == KURA_INT_RK2) iters = 0;
+    const double* th_dev;
+    bool host;
+    if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
+    double* io = host ? h->user.as<double>() : theta;
+    cudaStream_t s = h->stream;
+    const unsigned nb = blocks_for(h->n, 256);
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), io, h->y.as<double>());
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    const int64_t chunk_max = 8;
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int64_t c = std::min(left, chunk_max);
+        // cache key: step size and (method, iters, chunk) in one integer, disjoint from the RK4 keys
+        auto key = std::make_pair(step, int64_t(1) << 40 | int64_t(method) << 32 | int64_t(iters) << 16 | c);
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            std::unique_ptr<GraphEntry> ge(new GraphEntry());
+            cudaGraph_t graph = nullptr;
+            KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int64_t k = 0; k < c; k++) enqueue_rk2_step(h, step, method, iters, h->cap);
+            cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
+            ec = cudaGraphInstantiate(&ge->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate graph");
+            it = h->graphs.emplace(key, std::move(ge)).first;
+        }
+        KCHECK(h, cudaGraphLaunch(it->second->exec, s), "graph launch");
+        left -= c;
+    }
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->y.as<double>(), io);
+    KCHECK(h, cudaGetLastError(), "launching the permutation");
+    if (host) {
+        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+        return read_flags(h);
     }
     return KURA_OK;
 }

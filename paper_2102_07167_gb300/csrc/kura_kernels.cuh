@@ -867,6 +867,20 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     }
 }
 
+// ---------------------------------------------------------------- second-order integrators
+// out = x + alpha f (out may be x)
+__global__ void k_axpy(int64_t n, double* out, const double* x, double alpha, const double* __restrict__ f)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = x[i] + alpha * f[i];
+}
+// y = 2 Z - y (implicit midpoint: the step from its stage)
+__global__ void k_midpoint_final(int64_t n, double* __restrict__ y, const double* __restrict__ Z)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = 2.0 * Z[i] - y[i];
+}
+
 // ---------------------------------------------------------------- diagnostics
 constexpr int DIAG_THREADS = 256;
 // Fixed-order FP64 block reduction of v into part[blockIdx.x].

@@ -110,6 +110,7 @@ def load() -> C.CDLL:
             "kura_ensemble_create": (S, [I64, P, P, P, I32, I32, P, P, C.POINTER(KuraOpts), P, C.POINTER(P)]),
             "kura_measure_gather_rate": (S, [I64, I64, I32, P, C.POINTER(D)]),
             "kura_potential": (S, [P, P, C.POINTER(D)]),
+            "kura_integrate": (S, [P, P, D, I64, I32, I32]),
             "kura_mean_deviation": (S, [P, P, P, D, C.POINTER(D)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
@@ -339,6 +340,13 @@ def kura_measure_gather_rate(table_entries=1 << 20, gathers=1 << 28, entry_bytes
     return r.value
 
 
+INT_RK4, INT_RK2, INT_IMPLICIT_MIDPOINT = 0, 1, 2
+
+
+def kura_integrate(h, theta, step, n_steps, method, iters, n):
+    _check(load().kura_integrate(h, _ptr(theta, n=n), float(step), int(n_steps), int(method), int(iters)), h)
+
+
 def kura_potential(h, theta, n) -> float:
     v = C.c_double()
     _check(load().kura_potential(h, _ptr(theta, n=n), C.byref(v)), h)
@@ -464,6 +472,11 @@ class Kuramoto:
 
     def stats(self):
         return kura_get_stats(self.h)
+
+    def integrate(self, theta, step, n_steps, method=INT_RK4, iters=4):
+        """n_steps of RK4, explicit midpoint (INT_RK2) or implicit midpoint (INT_IMPLICIT_MIDPOINT, `iters`
+        fixed-point sweeps of the stage) on theta in place."""
+        kura_integrate(self.h, theta, step, n_steps, method, iters, self.n)
 
     def potential(self, theta):
         """Graph potential V (kura_potential)."""

@@ -332,3 +332,38 @@ def test_potential_decreases_and_mean_is_conserved(sbm_small):
     assert abs(md) < 1e-10, md
     ref_md = oracle.mean_deviation(th.cpu().numpy(), w.theta0, w.omega, 50 * w.h)
     assert abs(md - ref_md) < 1e-12
+
+
+# ----------------------------------------------------------------------------- second-order integrators (NEXT-3)
+@pytest.mark.parametrize("method", [1, 2])
+def test_second_order_integrators_vs_oracle(sbm_small, method):
+    """Explicit midpoint (1) and implicit midpoint (2, 4 sweeps) in FP64 against the oracle's."""
+    w = sbm_small
+    g = w.graph
+    steps = 30
+    ref = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps, method - 1, 4)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=0) as k:
+        th = _dev(w.theta0)
+        k.integrate(th, w.h, steps, method, 4)
+        k.sync()
+        out = th.cpu().numpy()
+        # host pointer path
+        thh = np.ascontiguousarray(w.theta0).copy()
+        k.integrate(thh, w.h, steps, method, 4)
+    assert np.abs(out - ref).max() < 1e-8
+    assert np.array_equal(out, thh)
+
+
+def test_long_horizon_mean_deviation_second_order():
+    """Classical all-to-all model (N = 512, K = 5, the paper's long-term setting shape): both second-order
+    methods keep the linear invariant of eq:5c to rounding over 20000 steps; the drift is measured."""
+    w = G.workload_complete(512)
+    g = w.graph
+    h, steps = 0.01, 20000
+    drift = {}
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, 5.0, precision=0) as k:
+        for method in (1, 2):
+            th = _dev(w.theta0)
+            k.integrate(th, h, steps, method, 4)
+            drift[method] = abs(k.mean_deviation(th, _dev(w.theta0), h * steps))
+    assert drift[1] < 1e-9 and drift[2] < 1e-9, drift
