@@ -64,10 +64,14 @@ def _load():
         L.orc_adjoint_rk4_csr.argtypes = [I64, _i64, _i32, _d, D, C.c_int, _d, D, I64, C.c_int, C.c_void_p,
                                           C.POINTER(D), _d, C.POINTER(D), _d]
         L.orc_rk2_csr.argtypes = [I64, _i64, _i32, _d, D, C.c_int, _d, D, I64, C.c_int, C.c_int]
+        L.orc_rhs_valued_csr.argtypes = [I64, _i64, _i32, _i32, _d, _d, D, _d]
+        L.orc_rhs_valued_dense.argtypes = [I64, _i32, _d, _d, D, _d]
+        L.orc_rhs_block_valued.argtypes = [I64, _i64, _i32, _i32, I32, _i32, I32, _d, _d, D, D, _d, C.c_void_p]
         L.orc_trig_count.restype = C.c_int64
         for f in ("orc_rhs_dense", "orc_rhs_csr", "orc_rhs_csr_rows", "orc_rhs_complete_op",
                   "orc_rhs_block", "orc_rk4_csr", "orc_rk4_complete", "orc_order_params",
-                  "orc_potential_csr", "orc_mean_deviation", "orc_adjoint_rk4_csr", "orc_rk2_csr"):
+                  "orc_potential_csr", "orc_mean_deviation", "orc_adjoint_rk4_csr", "orc_rk2_csr",
+                  "orc_rhs_valued_csr", "orc_rhs_valued_dense", "orc_rhs_block_valued"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -145,6 +149,37 @@ def rk4_csr(row_ptr, col, omega, K, theta0, h, n_steps, scaling=0):
     _check(_load().orc_rk4_csr(row_ptr.shape[0] - 1, row_ptr, np.ascontiguousarray(col, dtype=np.int32),
                                _f64(omega), float(K), int(scaling), th, float(h), int(n_steps)), "rk4_csr")
     return th
+
+
+def rhs_valued_csr(row_ptr, col, val, omega, theta, K):
+    """Finite-valued A (Sec. 1, Generalisations): omega + (K/n) sum_l A_ml sin(theta_l - theta_m)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = np.empty(row_ptr.shape[0] - 1)
+    _check(_load().orc_rhs_valued_csr(row_ptr.shape[0] - 1, row_ptr, np.ascontiguousarray(col, dtype=np.int32),
+                                      np.ascontiguousarray(val, dtype=np.int32), _f64(omega), _f64(theta),
+                                      float(K), out), "rhs_valued_csr")
+    return out
+
+
+def rhs_valued_dense(A, omega, theta, K):
+    """The same by brute force over a dense int32 matrix."""
+    A = np.ascontiguousarray(A, dtype=np.int32)
+    out = np.empty(A.shape[0])
+    _check(_load().orc_rhs_valued_dense(A.shape[0], A, _f64(omega), _f64(theta), float(K), out), "rhs_valued_dense")
+    return out
+
+
+def rhs_block_valued(row_ptr, col, val, max_val, label, n_comm, omega, theta, K, tau=0.5):
+    """Prevalent-value block rule for finite-valued A.  Returns (f, block values [n_comm, n_comm])."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    n = row_ptr.shape[0] - 1
+    out = np.empty(n)
+    bv = np.zeros((n_comm, n_comm), np.int32)
+    _check(_load().orc_rhs_block_valued(n, row_ptr, np.ascontiguousarray(col, dtype=np.int32),
+                                        np.ascontiguousarray(val, dtype=np.int32), int(max_val),
+                                        np.ascontiguousarray(label, dtype=np.int32), int(n_comm), _f64(omega),
+                                        _f64(theta), float(K), float(tau), out, bv.ctypes.data), "rhs_block_valued")
+    return out, bv
 
 
 def rk2_csr(row_ptr, col, omega, K, theta0, h, n_steps, method=0, iters=4, scaling=0):

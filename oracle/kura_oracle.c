@@ -136,6 +136,127 @@ int orc_rhs_complete_op(int64_t n, const double* omega, const double* theta,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Finite-valued adjacency (Sec. 1, "Generalisations": A_{ml} in {0, ..., J}),
+ * uniform scaling: f_m = omega_m + (K/n) sum_l A_{ml} sin(theta_l - theta_m).
+ * CSR form: val[e] is the value of edge e (values 0 are simply absent);
+ * dense form: brute force over an n x n int32 matrix.  Diagonal skipped. */
+int orc_rhs_valued_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                       const int32_t* val, const double* omega,
+                       const double* theta, double K, double* out)
+{
+    if (n <= 0 || !row_ptr || !val || !omega || !theta || !out) return -1;
+    for (int64_t m = 0; m < n; m++) {
+        acc_t sum = {0, 0};
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n) return -1;
+            if (col[e] == m) continue;
+            acc_add(&sum, (double)val[e] * counted_sin(theta[col[e]] - theta[m]));
+        }
+        out[m] = omega[m] + (K / (double)n) * acc_val(&sum);
+    }
+    return 0;
+}
+
+int orc_rhs_valued_dense(int64_t n, const int32_t* A, const double* omega,
+                         const double* theta, double K, double* out)
+{
+    if (n <= 0 || !A || !omega || !theta || !out) return -1;
+    for (int64_t m = 0; m < n; m++) {
+        acc_t sum = {0, 0};
+        for (int64_t l = 0; l < n; l++) {
+            if (l == m || !A[m * n + l]) continue;
+            acc_add(&sum, (double)A[m * n + l] * sin(theta[l] - theta[m]));
+        }
+        out[m] = omega[m] + (K / (double)n) * acc_val(&sum);
+    }
+    return 0;
+}
+
+/* Block rule for finite-valued A ("a single value is prevalent in each
+ * block"): per block (I, J) over its n_I n_J entries (n_I (n_I - 1) on the
+ * diagonal block, whose diagonal is don't-care) the value v* of largest
+ * count among the nonzero values (ties: the smaller value); the block is
+ * dense with value v* when the fraction of its entries different from v* is
+ * below tau, else sparse (value 0).  Row m of community I then sums, per
+ * column block J, v_IJ (S_J, C_J) plus (A_{ml} - v_IJ)(sin, cos) theta_l over
+ * the l in J with A_{ml} != v_IJ (l != m), and
+ * f_m = omega_m + (K/n)(cos theta_m acc_s - sin theta_m acc_c).  For 0/1
+ * values this is eq:KuramotoGraphApproach (v* = 1: missing entries
+ * subtracted).  max_val bounds the values (1..max_val). */
+int orc_rhs_block_valued(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int32_t* val, int32_t max_val, const int32_t* label,
+                         int32_t n_comm, const double* omega, const double* theta,
+                         double K, double tau, double* out, int32_t* block_val)
+{
+    if (n <= 0 || n_comm <= 0 || max_val < 1 || !row_ptr || !col || !val ||
+        !label || !omega || !theta || !out) return -1;
+    int64_t nc = n_comm, nv = (int64_t)max_val + 1;
+    int64_t* size = calloc((size_t)nc, sizeof(int64_t));
+    int64_t* cnt = calloc((size_t)(nc * nc * nv), sizeof(int64_t));
+    int32_t* bval = calloc((size_t)(nc * nc), sizeof(int32_t));
+    double* S = calloc((size_t)nc, sizeof(double));
+    double* C = calloc((size_t)nc, sizeof(double));
+    double* sn = malloc((size_t)n * sizeof(double));
+    double* cs = malloc((size_t)n * sizeof(double));
+    int32_t* arow = calloc((size_t)n, sizeof(int32_t));
+    int rc = 0;
+    if (!size || !cnt || !bval || !S || !C || !sn || !cs || !arow) { rc = -2; goto done; }
+    for (int64_t m = 0; m < n; m++) {
+        if (label[m] < 0 || label[m] >= n_comm) { rc = -1; goto done; }
+        size[label[m]]++;
+    }
+    /* value counts per block (nonzero values), diagonal entries ignored */
+    for (int64_t m = 0; m < n; m++)
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n || val[e] < 1 || val[e] > max_val) { rc = -1; goto done; }
+            if (col[e] == m) continue;
+            cnt[((int64_t)label[m] * nc + label[col[e]]) * nv + val[e]]++;
+        }
+    for (int64_t I = 0; I < nc; I++)
+        for (int64_t J = 0; J < nc; J++) {
+            double entries = (I == J) ? (double)size[I] * (double)(size[I] - 1)
+                                      : (double)size[I] * (double)size[J];
+            if (entries <= 0) continue;
+            int32_t best = 0;
+            int64_t bestc = 0;
+            for (int32_t v = 1; v <= max_val; v++)
+                if (cnt[(I * nc + J) * nv + v] > bestc) { bestc = cnt[(I * nc + J) * nv + v]; best = v; }
+            if (best > 0 && (1.0 - (double)bestc / entries) < tau) bval[I * nc + J] = best;
+        }
+    if (block_val) for (int64_t q = 0; q < nc * nc; q++) block_val[q] = bval[q];
+    for (int64_t l = 0; l < n; l++) { sn[l] = sin(theta[l]); cs[l] = cos(theta[l]); }
+    {
+        acc_t* sj = calloc((size_t)nc, sizeof(acc_t));
+        acc_t* cj = calloc((size_t)nc, sizeof(acc_t));
+        if (!sj || !cj) { free(sj); free(cj); rc = -2; goto done; }
+        for (int64_t l = 0; l < n; l++) { acc_add(&sj[label[l]], sn[l]); acc_add(&cj[label[l]], cs[l]); }
+        for (int64_t J = 0; J < nc; J++) { S[J] = acc_val(&sj[J]); C[J] = acc_val(&cj[J]); }
+        free(sj); free(cj);
+    }
+    for (int64_t m = 0; m < n; m++) {
+        int64_t I = label[m];
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++)
+            if (col[e] != m) arow[col[e]] = val[e];
+        acc_t as = {0, 0}, ac = {0, 0};
+        for (int64_t J = 0; J < nc; J++) {
+            int32_t v = bval[I * nc + J];
+            if (v) { acc_add(&as, (double)v * S[J]); acc_add(&ac, (double)v * C[J]); }
+        }
+        /* exceptions: every column l != m whose value differs from its block's value */
+        for (int64_t l = 0; l < n; l++) {
+            if (l == m) continue;
+            int32_t w = arow[l] - bval[I * nc + label[l]];
+            if (w) { acc_add(&as, (double)w * sn[l]); acc_add(&ac, (double)w * cs[l]); }
+        }
+        for (int64_t e = row_ptr[m]; e < row_ptr[m + 1]; e++) arow[col[e]] = 0;
+        out[m] = omega[m] + (K / (double)n) * (cs[m] * acc_val(&as) - sn[m] * acc_val(&ac));
+    }
+done:
+    free(size); free(cnt); free(bval); free(S); free(C); free(sn); free(cs); free(arow);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Block rule, eq:KuramotoGraphApproach.  The submatrices are the blocks
  * (I, J) = {rows with label I} x {columns with label J}; relabelling the
  * nodes community by community (P A P^T) only reorders rows and columns and

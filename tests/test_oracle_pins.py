@@ -434,3 +434,55 @@ def test_implicit_midpoint_solves_its_stage_equation_and_is_symmetric():
     ye = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, h, 1, 0, 1)
     backe = oracle.rk2_csr(g.row_ptr, g.col, w.omega, w.K, ye, -h, 1, 0, 1)
     assert np.max(np.abs(backe - w.theta0)) > 1e-9
+
+
+# ----------------------------------------------------------------------------- finite-valued adjacency (NEXT-4)
+def _valued_block_matrix(rng, sizes, vals, noise, max_val):
+    """Block matrix whose block (I, J) mostly holds vals[I][J] (0..max_val), with a fraction `noise` of entries
+    replaced by uniform values in 0..max_val; zero diagonal."""
+    sizes = np.asarray(sizes)
+    lab = np.repeat(np.arange(len(sizes)), sizes)
+    n = lab.size
+    A = np.asarray(vals, dtype=np.int32)[lab][:, lab]
+    flip = rng.random((n, n)) < noise
+    A[flip] = rng.integers(0, max_val + 1, int(flip.sum()))
+    np.fill_diagonal(A, 0)
+    return A.astype(np.int32), lab.astype(np.int32)
+
+
+def _csr_values(A):
+    rows, cols = np.nonzero(A)
+    row_ptr = np.zeros(A.shape[0] + 1, np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr), cols.astype(np.int32), A[rows, cols].astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_valued_block_rule_matches_definition(seed):
+    """Sec. 1 (Generalisations): for A in {0..3} with one prevalent value per block, the prevalent-value block
+    rule equals the definition (CSR and brute force) for every tau; the detected block values are the planted
+    ones where the noise leaves them prevalent."""
+    rng = np.random.default_rng(seed)
+    vals = [[2, 0, 1], [0, 3, 0], [1, 0, 1]]
+    A, lab = _valued_block_matrix(rng, [20, 15, 25], vals, 0.2, 3)
+    perm = rng.permutation(A.shape[0])
+    A, lab = A[perm][:, perm], lab[perm]
+    rp, cl, vl = _csr_values(A)
+    omega, theta = rng.normal(size=A.shape[0]), rng.uniform(-20, 20, A.shape[0])
+    ref = oracle.rhs_valued_dense(A, omega, theta, 1.7)
+    np.testing.assert_allclose(oracle.rhs_valued_csr(rp, cl, vl, omega, theta, 1.7), ref, atol=1e-13, rtol=0)
+    for tau in (0.0, 0.3, 0.5, 0.8, 1.0):
+        f, bv = oracle.rhs_block_valued(rp, cl, vl, 3, lab, 3, omega, theta, 1.7, tau)
+        np.testing.assert_allclose(f, ref, atol=1e-12, rtol=0)
+        if tau == 0.5:
+            assert np.array_equal(bv, np.asarray(vals))
+
+
+def test_valued_rule_reduces_to_binary_rule():
+    """With values in {0, 1} the valued rule is the 0/1 block rule of eq:KuramotoGraphApproach."""
+    w = G.workload_sbm_small(n=600, n_comm=4, min_size=80)
+    g = w.graph
+    val = np.ones(g.col.shape[0], np.int32)
+    f, _ = oracle.rhs_block_valued(g.row_ptr, g.col, val, 1, g.label, g.n_comm, w.omega, w.theta0, w.K)
+    f01, _ = oracle.rhs_block(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.theta0, w.K)
+    np.testing.assert_allclose(f, f01, atol=1e-12, rtol=0)
