@@ -138,6 +138,22 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
                         const int32_t* label, int32_t n_comm, const double* omega,
                         double K, const kura_opts* opts, void* stream, kura_t* out);
 
+/* Finite-valued adjacency (Sec. 1, "Generalisations": A_{ml} in {0, ..., J}):
+ * as kura_create, with val[nnz] (host, int32, 1..127, parallel to col) the
+ * value of each listed entry; n <= 2^24 - 2; uniform scaling only
+ * (f_m = omega_m + (K/n) sum_l A_{ml} sin(theta_l - theta_m)).  Per block the
+ * nonzero value of largest count v_IJ (ties: the smaller) is prevalent when
+ * the fraction of entries different from it is below tau: the block then
+ * contributes v_IJ (S_J, C_J) plus (A_{ml} - v_IJ)(sin, cos) theta_l over its
+ * exceptions, else (sparse) A_{ml} (sin, cos) theta_l over its entries.  Both
+ * corrections are index lists (no tensor cores, no bitmaps).  kura_rhs,
+ * kura_rk4_steps, kura_integrate, kura_order_params, kura_classify_blocks and
+ * kura_autotune apply; kura_adjoint, kura_potential and the direct baseline
+ * return KURA_ESTATE. */
+kura_status kura_create_valued(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                               const int32_t* label, int32_t n_comm, const double* omega, double K,
+                               const kura_opts* opts, void* stream, kura_t* out);
+
 /* Re-classifies the blocks with a new threshold tau in [0, 1] (pass a
  * negative tau to keep the current one) and rebuilds the streams (Sec. 3,
  * dense/sparse decision).  Needs the host CSR copy.  stats is nullable. */
@@ -392,6 +408,13 @@ kura_status kura_plan_row(kura_plan_t p, int64_t row, int32_t* missing, int64_t*
 /* Dense column blocks D(I) of row block I: up to cap entries, count in *count. */
 kura_status kura_plan_dense_blocks(kura_plan_t p, int32_t I, int32_t* J, int32_t cap,
                                    int32_t* count);
+
+/* Host-only plan of a finite-valued matrix (val as for kura_create_valued),
+ * and the prevalent value of each dense block of row block I (in the order
+ * of kura_plan_dense_blocks; 1 for 0/1 plans). */
+kura_status kura_plan_build_valued(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                                   const int32_t* label, int32_t n_comm, const kura_opts* opts, kura_plan_t* out);
+kura_status kura_plan_dense_values(kura_plan_t p, int32_t I, int32_t* v, int32_t cap, int32_t* count);
 /* Read-only views of the packed correction data the row kernel consumes:
  * gstream (int32, *gstream_len entries), groups (*n_groups records of
  * {int64 off; int32 len; int32 first_subrow; int32 n_subrows; int32 pad}),

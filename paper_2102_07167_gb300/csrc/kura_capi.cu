@@ -99,7 +99,7 @@ struct kura_ctx {
     cudaStream_t cap = nullptr;        // capture stream (graphs are replayed on `stream`)
     // host copies
     std::vector<int64_t> h_row_ptr;
-    std::vector<int32_t> h_col, h_label;
+    std::vector<int32_t> h_col, h_label, h_val;   // h_val: values of a finite-valued matrix (else empty)
     std::vector<double> h_omega;        // user order
     Plan plan;                          // host plan (streams released after upload)
     int64_t miss_total = 0, pres_total = 0, nnz = 0, stream_bytes = 0, bitmap_rows = 0;
@@ -108,7 +108,8 @@ struct kura_ctx {
     int64_t tile_work = 0;              // planner work target per tile (0: automatic); set by kura_autotune
     int32_t bm_stash_off = 0;
     // device buffers
-    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig;
+    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig, dval;
+    bool valued = false;
     DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
@@ -195,6 +196,7 @@ DevGraph dev_graph(kura_ctx* h)
     g.row_sub0 = h->row_sub0.as<int32_t>();
     g.bitmap = h->bitmap.as<uint32_t>();
     g.dig = h->has_tc ? h->dig.as<uint8_t>() : nullptr;
+    g.dval = h->valued ? h->dval.as<int32_t>() : nullptr;
     g.bm_stash_off = h->bm_stash_off;
     g.dptr = h->dptr.as<int64_t>();
     g.dcol = h->dcol.as<int32_t>();
@@ -412,7 +414,9 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     h->tc_mask_bits = p.tc_mask_bits;
     h->has_tc = p.tc_tiles > 0;
     h->stream_bytes = plan_stream_bytes(p);
-    h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2));
+    h->valued = p.valued;
+    // fixed point: n values of at most 2^q each, times the largest weight, stay below 2^61
+    h->q_bits = 61 - ceil_log2(std::max<int64_t>(h->n, 2)) - (p.valued ? ceil_log2(int64_t(p.max_weight) + 1) : 0);
     const int mode = h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
     const size_t esize = h->opts.precision == KURA_PREC_MIXED ? sizeof(float2) : sizeof(longlong2);
     // dynamic shared memory: the ring, then either [16 B | window | bitmap-pass
@@ -435,6 +439,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     KCHECK(h, upload(h->bitmap, p.bitmap, s), "upload row bitmaps");
     KCHECK(h, upload(h->dptr, p.dptr, s), "upload dptr");
     KCHECK(h, upload(h->dcol, p.dcol, s), "upload dcol");
+    if (p.valued) KCHECK(h, upload(h->dval, p.dval, s), "upload block values");
     KCHECK(h, upload(h->comm_off, p.comm_off, s), "upload comm_off");
     {
         std::vector<double> om(size_t(h->n));
@@ -566,9 +571,33 @@ const char* kura_status_string(kura_status s)
 
 const char* kura_last_error(kura_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
+static kura_status create_impl(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                               const int32_t* label, int32_t n_comm, const double* omega, double K,
+                               const kura_opts* opts, void* stream, kura_t* out);
+
 kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
                         int32_t n_comm, const double* omega, double K, const kura_opts* opts, void* stream,
                         kura_t* out)
+{
+    return create_impl(n, row_ptr, col, nullptr, label, n_comm, omega, K, opts, stream, out);
+}
+
+kura_status kura_create_valued(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                               const int32_t* label, int32_t n_comm, const double* omega, double K,
+                               const kura_opts* opts, void* stream, kura_t* out)
+{
+    g_create_error.clear();
+    if (!val) {
+        g_create_error = "val is NULL";
+        if (out) *out = nullptr;
+        return KURA_EINVAL;
+    }
+    return create_impl(n, row_ptr, col, val, label, n_comm, omega, K, opts, stream, out);
+}
+
+static kura_status create_impl(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                               const int32_t* label, int32_t n_comm, const double* omega, double K,
+                               const kura_opts* opts, void* stream, kura_t* out)
 {
     g_create_error.clear();
     if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
@@ -583,8 +612,13 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
         for (int64_t i = 0; i < n; i++)
             if (!std::isfinite(omega[i])) { g_create_error = "omega has a non-finite entry"; return KURA_EINVAL; }
     }
+    if (val && o.scaling != KURA_SCALING_UNIFORM) {
+        g_create_error = "finite-valued matrices use uniform scaling";
+        return KURA_EINVAL;
+    }
     PlanInput in;
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
+    in.val = val;
     in.tile_max_rows = TILE_MAX_ROWS;
     in.tile_max_sub = tile_max_sub_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
     in.slot_ints = slot_ints_for(o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
@@ -621,6 +655,7 @@ kura_status kura_create(int64_t n, const int64_t* row_ptr, const int32_t* col, c
         h->h_row_ptr.assign(row_ptr, row_ptr + n + 1);
         h->h_col.assign(col, col + row_ptr[n]);
         h->h_label.assign(label, label + n);
+        if (val) h->h_val.assign(val, val + row_ptr[n]);
     }
     kura_status st = build_device(h.get(), std::move(plan));
     if (st != KURA_OK) { g_create_error = h->err; return st; }
@@ -671,6 +706,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         PlanInput in;
         in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
         in.n_comm = h->n_comm; in.tau = tau;
+        in.val = h->h_val.empty() ? nullptr : h->h_val.data();
         in.tile_max_rows = TILE_MAX_ROWS;
         in.tile_max_sub = tile_max_sub_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
         in.slot_ints = slot_ints_for(h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64);
@@ -697,6 +733,7 @@ kura_status rebuild_plan(kura_t h, double tau, int32_t tensor_cores, int64_t til
     PlanInput in;
     in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
     in.n_comm = h->n_comm; in.tau = tau;
+    in.val = h->h_val.empty() ? nullptr : h->h_val.data();
     const int mode = h->opts.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
     in.tile_max_rows = TILE_MAX_ROWS;
     in.tile_max_sub = tile_max_sub_for(mode);
@@ -918,6 +955,7 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
 kura_status kura_potential(kura_t h, const double* theta, double* V)
 {
     if (kura_status st0 = check_single(h)) return st0;
+    if (h->valued) return h->fail(KURA_ESTATE, "the potential is defined here for 0/1 matrices");
     if (!theta || !V) return h->fail(KURA_EINVAL, "NULL argument");
     const int64_t n = h->n;
     const int64_t nb = (n + DIAG_THREADS - 1) / DIAG_THREADS;
@@ -1085,6 +1123,7 @@ static void launch_direct(kura_t h, const double* th_user, double* out_user, int
 kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32_t precision)
 {
     if (kura_status st0 = check_single(h)) return st0;
+    if (h->valued) return h->fail(KURA_ESTATE, "the direct baseline sums 0/1 matrices");
     if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
     if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
     if (kura_status st = ensure_direct(h)) return st;
@@ -1105,6 +1144,7 @@ kura_status kura_direct_rhs(kura_t h, const double* theta, double* dtheta, int32
 kura_status kura_direct_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps, int32_t precision)
 {
     if (kura_status st0 = check_single(h)) return st0;
+    if (h->valued) return h->fail(KURA_ESTATE, "the direct baseline sums 0/1 matrices");
     if (!theta) return h->fail(KURA_EINVAL, "theta is NULL");
     if (!(step > 0) || !std::isfinite(step) || n_steps < 0) return h->fail(KURA_EINVAL, "bad step or n_steps");
     if (precision != KURA_PREC_FP64 && precision != KURA_PREC_MIXED) return h->fail(KURA_EINVAL, "bad precision");
@@ -1437,6 +1477,7 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     if (loss_kind == 1 && !target) return h->fail(KURA_EINVAL, "loss_kind 1 needs a target");
     if (h->opts.precision != KURA_PREC_MIXED)
         return h->fail(KURA_ESTATE, "the adjoint runs on handles created with KURA_PREC_MIXED");
+    if (h->valued) return h->fail(KURA_ESTATE, "the adjoint runs on 0/1 matrices");
     if (h->sym < 0) {
         if (h->h_col.empty() && h->nnz > 0)
             return h->fail(KURA_ESTATE, "the adjoint needs the host CSR copy to check symmetry");
@@ -1834,8 +1875,33 @@ struct kura_plan_s {
     Plan p;
 };
 
+static kura_status plan_build_impl(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                                   const int32_t* label, int32_t n_comm, const kura_opts* opts, kura_plan_t* out);
+
 kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* label,
                             int32_t n_comm, const kura_opts* opts, kura_plan_t* out)
+{
+    return plan_build_impl(n, row_ptr, col, nullptr, label, n_comm, opts, out);
+}
+
+kura_status kura_plan_build_valued(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                                   const int32_t* label, int32_t n_comm, const kura_opts* opts, kura_plan_t* out)
+{
+    if (!val) return KURA_EINVAL;
+    return plan_build_impl(n, row_ptr, col, val, label, n_comm, opts, out);
+}
+
+kura_status kura_plan_dense_values(kura_plan_t pl, int32_t I, int32_t* v, int32_t cap, int32_t* count)
+{
+    if (!pl || !count || I < 0 || I >= pl->p.n_comm) return KURA_EINVAL;
+    const Plan& p = pl->p;
+    *count = int32_t(p.dptr[size_t(I) + 1] - p.dptr[size_t(I)]);
+    for (int32_t k = 0; k < *count && k < cap && v; k++) v[k] = p.dval[size_t(p.dptr[size_t(I)] + k)];
+    return KURA_OK;
+}
+
+static kura_status plan_build_impl(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* val,
+                                   const int32_t* label, int32_t n_comm, const kura_opts* opts, kura_plan_t* out)
 {
     g_create_error.clear();
     if (!out) return KURA_EINVAL;
@@ -1853,6 +1919,7 @@ kura_status kura_plan_build(int64_t n, const int64_t* row_ptr, const int32_t* co
     in.slot_ints = slot_ints_for(mode);
     in.entry_bytes = mode == MODE_MIXED ? 8 : 16;
     in.bitmap_zmin = o.bitmap_zmin;
+    in.val = val;
     in.tensor_cores = o.tensor_cores;
     std::string err;
     int rc = build_plan(in, p->p, err);

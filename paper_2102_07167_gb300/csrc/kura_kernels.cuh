@@ -88,6 +88,7 @@ struct DevGraph {
     const int64_t* comm_off;                // [n_comm+1]
     const double* omega;                    // [n] permuted
     void* table;                            // EntryT<MODE>::T [n + 2]
+    const int32_t* dval;                    // value of each dense block (finite-valued matrices), else null
     unsigned long long* bsum;               // [2 n_comm] accumulators, zero between launches
     long long* bsum_out;                    // [2 n_comm] last block sums (S_J, C_J)
     long long* tot;                         // [2] last totals
@@ -328,8 +329,9 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
             long long ts = 0, tc = 0;
             for (int64_t k = g.dptr[I]; k < g.dptr[I + 1]; k++) {
                 const int Jd = g.dcol[k];
-                ts += __ldcg(bs + 2 * Jd);
-                tc += __ldcg(bs + 2 * Jd + 1);
+                const long long bv = g.dval ? g.dval[k] : 1;      // the block's prevalent value
+                ts += bv * __ldcg(bs + 2 * Jd);
+                tc += bv * __ldcg(bs + 2 * Jd + 1);
             }
             if (MODE == MODE_FP64)
                 reinterpret_cast<longlong2*>(g.T)[I] = make_longlong2(ts, tc);
@@ -705,6 +707,24 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             if (have) {
                 A as = 0, ac = 0;
                 const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
+                if (t.flags & TILE_VALUED) {
+                    // finite-valued matrix: each entry is column | (weight + 128) << 24, added
+                    // with its weight (padding and lanes past the end read zero entries)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        if (32 * i < tot4) {
+                            const int idx[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+                            for (int q = 0; q < 4; q++) {
+                                const uint32_t raw = uint32_t(idx[q]);
+                                const A w = A(int(raw >> 24) - 128);
+                                const E e = gather_entry<MODE>(win, t.wbeg, t.wlen, table, int(raw & 0xFFFFFFu));
+                                as += w * e.x;
+                                ac += w * e.y;
+                            }
+                        }
+                    }
+                } else
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     if (32 * i < tot4) {                     // warp-uniform

@@ -74,6 +74,15 @@ inline bool is_dense(const Plan& p, int32_t I, int32_t J)
     return std::binary_search(b, e, J);
 }
 
+// Value of dense block (I, J), 0 when the block is sparse.
+inline int32_t dense_value(const Plan& p, int32_t I, int32_t J)
+{
+    const int32_t* b = p.dcol.data() + p.dptr[I];
+    const int32_t* e = p.dcol.data() + p.dptr[I + 1];
+    const int32_t* q = std::lower_bound(b, e, J);
+    return (q != e && *q == J) ? p.dval[size_t(p.dptr[I] + (q - b))] : 0;
+}
+
 int validate(const PlanInput& in, std::string& err)
 {
     if (in.n <= 0 || in.n >= (int64_t(1) << 31) - 8) { err = "n must be in [1, 2^31 - 8)"; return 1; }
@@ -101,6 +110,12 @@ int validate(const PlanInput& in, std::string& err)
     if (bad & 2) { err = "column index out of range"; return 1; }
     if (bad & 4) { err = "columns not strictly increasing within a row (unsorted or duplicate)"; return 1; }
     if (bad & 8) { err = "label out of range [0, n_comm)"; return 1; }
+    if (in.val) {
+        if (n > VALUED_MAX_N) { err = "a finite-valued matrix needs n <= 2^24 - 2"; return 1; }
+        const int64_t nnz = in.row_ptr[n];
+        for (int64_t k = 0; k < nnz; k++)
+            if (in.val[k] < 1 || in.val[k] > VALUED_MAX) { err = "values must be in [1, 127]"; return 1; }
+    }
     return 0;
 }
 
@@ -154,7 +169,53 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         // over n_I n_J entries (n_I (n_I - 1) off-diagonal entries on the
         // diagonal block, whose diagonal is don't-care); dense iff below tau.
         std::vector<std::vector<int32_t>> dense_of(static_cast<size_t>(nc));
+        std::vector<std::vector<int32_t>> dval_of(static_cast<size_t>(nc));
         int64_t nonempty = 0, ndense = 0;
+        p.valued = in.val != nullptr;
+        if (p.valued)
+            for (int64_t k = 0; k < in.row_ptr[n]; k++) p.max_weight = std::max(p.max_weight, in.val[k]);
+        if (p.valued) {
+            // finite values: per block the nonzero value of largest count (ties:
+            // the smaller); dense with that value iff the fraction of entries
+            // different from it is below tau
+            #pragma omp parallel reduction(+:nonempty, ndense)
+            {
+                std::vector<int64_t> keys;
+                #pragma omp for schedule(dynamic, 1)
+                for (int32_t I = 0; I < nc; I++) {
+                    keys.clear();
+                    for (int64_t v = p.comm_off[I]; v < p.comm_off[I + 1]; v++) {
+                        int64_t o = p.perm[size_t(v)];
+                        for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
+                            if (in.col[k] == o) continue;
+                            keys.push_back(int64_t(in.label[in.col[k]]) * 128 + in.val[k]);
+                        }
+                    }
+                    std::sort(keys.begin(), keys.end());
+                    for (size_t a = 0; a < keys.size();) {
+                        const int32_t J = int32_t(keys[a] / 128);
+                        int32_t best = 0;
+                        int64_t bestc = 0;
+                        size_t b = a;
+                        while (b < keys.size() && keys[b] / 128 == J) {
+                            size_t c = b;
+                            while (c < keys.size() && keys[c] == keys[b]) c++;
+                            if (int64_t(c - b) > bestc) { bestc = int64_t(c - b); best = int32_t(keys[b] % 128); }
+                            b = c;
+                        }
+                        const double entries = (J == I) ? double(csize(I)) * double(csize(I) - 1)
+                                                        : double(csize(I)) * double(csize(J));
+                        nonempty++;
+                        if (1.0 - double(bestc) / entries < in.tau) {
+                            dense_of[size_t(I)].push_back(J);
+                            dval_of[size_t(I)].push_back(best);
+                            ndense++;
+                        }
+                        a = b;
+                    }
+                }
+            }
+        } else
         #pragma omp parallel reduction(+:nonempty, ndense)
         {
             std::vector<int64_t> cnt(size_t(nc), 0);
@@ -177,7 +238,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                                               : double(csize(I)) * double(csize(J));
                     double zero_frac = 1.0 - double(cnt[size_t(J)]) / entries;
                     nonempty++;
-                    if (zero_frac < in.tau) { dense_of[size_t(I)].push_back(J); ndense++; }
+                    if (zero_frac < in.tau) { dense_of[size_t(I)].push_back(J); dval_of[size_t(I)].push_back(1); ndense++; }
                     cnt[size_t(J)] = 0;
                 }
             }
@@ -188,8 +249,11 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         p.dptr.assign(size_t(nc) + 1, 0);
         for (int32_t I = 0; I < nc; I++) p.dptr[I + 1] = p.dptr[I] + int64_t(dense_of[size_t(I)].size());
         p.dcol.resize(size_t(p.dptr[nc]));
-        for (int32_t I = 0; I < nc; I++)
+        p.dval.resize(size_t(p.dptr[nc]));
+        for (int32_t I = 0; I < nc; I++) {
             std::copy(dense_of[size_t(I)].begin(), dense_of[size_t(I)].end(), p.dcol.begin() + p.dptr[I]);
+            std::copy(dval_of[size_t(I)].begin(), dval_of[size_t(I)].end(), p.dval.begin() + p.dptr[I]);
+        }
         std::vector<int64_t> dense_span(size_t(nc), 0);   // sum of n_J over D(I)
         std::vector<uint8_t> self_dense(size_t(nc), 0);
         for (int32_t I = 0; I < nc; I++)
@@ -208,7 +272,16 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
             for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
                 int32_t c = in.col[k];
                 if (c == o) continue;
-                if (is_dense(p, I, in.label[c])) in_dense++; else np_++;
+                if (p.valued) {
+                    // in_dense counts the dense-block entries equal to their block's value
+                    const int32_t bv = dense_value(p, I, in.label[c]);
+                    if (bv == 0) np_++;
+                    else if (in.val[k] == bv) in_dense++;
+                } else if (is_dense(p, I, in.label[c])) {
+                    in_dense++;
+                } else {
+                    np_++;
+                }
             }
             p.miss_cnt[size_t(v)] = int32_t(dense_span[size_t(I)] - self_dense[size_t(I)] - in_dense);
             p.pres_cnt[size_t(v)] = int32_t(np_);
@@ -252,7 +325,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                 c_mpad[size_t(I)] = wbeg - 1;
             }
             p.max_wlen = std::max(p.max_wlen, wlen);
-            if (covers && in.tensor_cores > 0 && p.dptr[I + 1] > p.dptr[I]) {
+            if (covers && in.tensor_cores > 0 && !p.valued && p.dptr[I + 1] > p.dptr[I]) {
                 // tensor-core mask over the K-blocks spanning the dense columns [lo, hi)
                 const int64_t kb0 = lo / TC_KBLOCK, kb1 = (hi + TC_KBLOCK - 1) / TC_KBLOCK;
                 int64_t zeros = 0;
@@ -265,7 +338,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     continue;
                 }
             }
-            if (covers && wlen > 0 && in.bitmap_zmin >= 0 && p.dptr[I + 1] > p.dptr[I]) {
+            if (covers && wlen > 0 && in.bitmap_zmin >= 0 && !p.valued && p.dptr[I + 1] > p.dptr[I]) {
                 double zeros = 0, entries = 0;
                 for (int64_t v = rb; v < re; v++) zeros += p.miss_cnt[size_t(v)];
                 entries = double(re - rb) * double(dense_span[size_t(I)]);
@@ -359,6 +432,8 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     p.tc_tiles++;
                     p.tc_rows += r - s;
                     p.tc_mask_bits += nM * TC_MBLOCK * int64_t(t.nsw) * TC_KBLOCK;
+                } else if (p.valued) {
+                    t.flags |= TILE_VALUED;
                 } else {
                     if (c_inwin[size_t(I)]) t.flags |= TILE_MISS_IN_WINDOW;
                     if (!std::binary_search(p.dcol.begin() + p.dptr[I], p.dcol.begin() + p.dptr[I + 1], I))
@@ -384,8 +459,8 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     while (v < r) {
                         const int64_t si = sub_ints(v, k);
                         const bool short_ = si - 4 <= SHORT_SUB_INTS;
-                        const int64_t cap = (all_short && short_ && in.entry_bytes == 8) ? GROUP_MAX_SUB_SHORT
-                                                                                           : GROUP_MAX_SUB;
+                        const int64_t cap = (all_short && short_ && in.entry_bytes == 8 && !p.valued)
+                                                ? GROUP_MAX_SUB_SHORT : GROUP_MAX_SUB;
                         if (int64_t(members.size()) >= cap) break;
                         if (!members.empty() && size + si > in.slot_ints) break;
                         members.emplace_back(v, k);
@@ -425,12 +500,35 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         {
             std::vector<uint64_t> bits(size_t((n + 63) / 64), 0);
             std::vector<int32_t> ms, pr;
+            std::vector<int32_t> vmark(p.valued ? size_t(n) : size_t(0), 0);   // value of each neighbour
+            std::vector<std::pair<int32_t, int32_t>> prv;
             #pragma omp for schedule(dynamic, 256)
             for (int64_t v = 0; v < n; v++) {
                 int32_t I = p.node_comm[size_t(v)];
                 int64_t o = p.perm[size_t(v)];
                 ms.clear();
                 pr.clear();
+                if (p.valued) {
+                    // dense blocks: every column whose value differs from the block's value,
+                    // weight A - v; sparse blocks: the entries, weight A
+                    prv.clear();
+                    for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
+                        int32_t c = in.col[k];
+                        if (c == o) continue;
+                        int32_t w = p.inv_perm[size_t(c)];
+                        if (dense_value(p, I, in.label[c])) vmark[size_t(w)] = in.val[k];
+                        else prv.emplace_back(w, in.val[k]);
+                    }
+                    std::sort(prv.begin(), prv.end());
+                    for (const auto& e : prv) pr.push_back(valued_pack(e.first, e.second));
+                    for (int64_t k = p.dptr[I]; k < p.dptr[I + 1]; k++) {
+                        const int32_t J = p.dcol[size_t(k)], bv = p.dval[size_t(k)];
+                        for (int64_t w = p.comm_off[size_t(J)]; w < p.comm_off[size_t(J) + 1]; w++)
+                            if (w != v && vmark[size_t(w)] != bv) ms.push_back(valued_pack(w, vmark[size_t(w)] - bv));
+                    }
+                    for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++)
+                        if (in.col[k] != o) vmark[size_t(p.inv_perm[size_t(in.col[k])])] = 0;
+                } else {
                 for (int64_t k = in.row_ptr[o]; k < in.row_ptr[o + 1]; k++) {
                     int32_t c = in.col[k];
                     if (c == o) continue;
@@ -463,6 +561,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t w = p.inv_perm[size_t(c)];
                     bits[size_t(w) >> 6] = 0;
                 }
+                }
                 // tensor-core rows: the missing entries become mask bits
                 if (c_tc[size_t(I)]) {
                     const Tile& T = p.tiles[size_t(p.row_tile[size_t(v)])];
@@ -493,11 +592,19 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     int32_t* hdr = p.gstream.data() + p.sub_hdr[size_t(sg)];
                     int32_t* mdst = p.gstream.data() + sub_mpos[size_t(sg)];
                     int32_t* pdst = p.gstream.data() + sub_ppos[size_t(sg)];
-                    balance_banks(ms.data() + mb, mn, p.tiles[size_t(p.row_tile[size_t(v)])].wbeg,
-                                  in.entry_bytes >= 16 ? 8 : 16, mdst);
-                    for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = c_mpad[size_t(I)];
-                    for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
-                    for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = int32_t(n);
+                    if (p.valued) {
+                        const int32_t pad = valued_pack(n, 0);
+                        for (int64_t q = 0; q < mn; q++) mdst[q] = ms[size_t(mb + q)];
+                        for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = pad;
+                        for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
+                        for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = pad;
+                    } else {
+                        balance_banks(ms.data() + mb, mn, p.tiles[size_t(p.row_tile[size_t(v)])].wbeg,
+                                      in.entry_bytes >= 16 ? 8 : 16, mdst);
+                        for (int64_t q = mn; q < round_up4(mn); q++) mdst[q] = c_mpad[size_t(I)];
+                        for (int64_t q = 0; q < pn; q++) pdst[q] = pr[size_t(pb + q)];
+                        for (int64_t q = pn; q < round_up4(pn); q++) pdst[q] = int32_t(n);
+                    }
                     hdr[1] = int32_t(mn);
                     hdr[3] = int32_t(pn);
                 }

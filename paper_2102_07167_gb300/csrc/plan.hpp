@@ -47,6 +47,15 @@ constexpr int32_t BITMAP_MAX_SW = 5;
 // nM = ceil((r1 - r0) / 128); row r of the block is 4 words, bit c & 31 of
 // word c >> 5 for column wbeg + 128 kb + c, tile row 128 m + r.
 constexpr int32_t TILE_TC = 8;
+// Finite-valued adjacency (PlanInput::val): every listed entry is packed as
+// column | (weight + 128) << 24, the weight being A_ml - v_IJ for the
+// exceptions of a dense block of value v_IJ and A_ml for a sparse block's
+// entries (padding: column n, weight 0); both parts are added with their
+// weights.  No window shortcuts, no tensor cores, no bitmaps.
+constexpr int32_t TILE_VALUED = 16;
+constexpr int32_t VALUED_MAX = 127;             // values 1..127
+constexpr int64_t VALUED_MAX_N = (int64_t(1) << 24) - 2;
+inline int32_t valued_pack(int64_t col, int32_t w) { return int32_t(uint32_t(col) | (uint32_t(w + 128) << 24)); }
 constexpr int32_t TC_KBLOCK = 128;      // columns per K-block
 constexpr int32_t TC_MBLOCK = 128;      // rows per M-block (tensor-core tile height)
 
@@ -95,6 +104,8 @@ struct PlanInput {
     // there exceeds this (and the window holds every dense column); < 0: never
     double bitmap_zmin = -1.0;
     int32_t entry_bytes = 8;            // (sin, cos) table entry size of the row kernel: 8 or 16
+    // values of the listed edges (1..VALUED_MAX, parallel to col); null: a 0/1 matrix
+    const int32_t* val = nullptr;
     // tensor-core mask encoding of a community's dense blocks (TILE_TC):
     // 0 never, 1 when its mask bits take fewer bytes than its index lists,
     // 2 whenever the window holds every dense column
@@ -113,6 +124,9 @@ struct Plan {
     std::vector<int32_t> deg;           // [n] degree without self-loops (permuted order)
     std::vector<int64_t> dptr;          // [n_comm+1] dense column blocks of each row block
     std::vector<int32_t> dcol;
+    std::vector<int32_t> dval;          // value of each dense block (1 for a 0/1 matrix)
+    bool valued = false;                // finite-valued matrix (TILE_VALUED streams)
+    int32_t max_weight = 1;             // largest |weight| of a listed entry or block value
     // per-row counts, sub-rows and the packed group stream (see Group)
     std::vector<int32_t> miss_cnt, pres_cnt;
     std::vector<int32_t> row_sub0;      // [n+1] global index of each row's first sub-row

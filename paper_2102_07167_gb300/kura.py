@@ -111,6 +111,9 @@ def load() -> C.CDLL:
             "kura_measure_gather_rate": (S, [I64, I64, I32, P, C.POINTER(D)]),
             "kura_potential": (S, [P, P, C.POINTER(D)]),
             "kura_integrate": (S, [P, P, D, I64, I32, I32]),
+            "kura_create_valued": (S, [I64, P, P, P, P, I32, P, D, C.POINTER(KuraOpts), P, C.POINTER(P)]),
+            "kura_plan_build_valued": (S, [I64, P, P, P, P, I32, C.POINTER(KuraOpts), C.POINTER(P)]),
+            "kura_plan_dense_values": (S, [P, I32, P, I32, C.POINTER(I32)]),
             "kura_mean_deviation": (S, [P, P, P, D, C.POINTER(D)]),
             "kura_kernel_times": (S, [P, P, I32, C.POINTER(I32)]),
             "kura_set_stream": (S, [P, P]),
@@ -378,6 +381,29 @@ def kura_plan_build(n, row_ptr, col, label, n_comm, tau=0.5, precision=PREC_MIXE
     return p
 
 
+def kura_plan_build_valued(n, row_ptr, col, val, label, n_comm, tau=0.5, precision=PREC_MIXED):
+    p = C.c_void_p()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.int32)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    o = kura_default_opts()
+    o.tau, o.precision = float(tau), int(precision)
+    rc = load().kura_plan_build_valued(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                       val.ctypes.data if val.size else None, label.ctypes.data, int(n_comm),
+                                       C.byref(o), C.byref(p))
+    _check(rc, None)
+    return p
+
+
+def kura_plan_dense_values(p, I) -> np.ndarray:
+    cnt = C.c_int32()
+    _check(load().kura_plan_dense_values(p, int(I), None, 0, C.byref(cnt)), None)
+    out = np.zeros(max(cnt.value, 1), np.int32)
+    _check(load().kura_plan_dense_values(p, int(I), out.ctypes.data, int(cnt.value), C.byref(cnt)), None)
+    return out[:cnt.value]
+
+
 def kura_plan_stats(p) -> dict:
     st = KuraBlockStats()
     _check(load().kura_plan_stats(p, C.byref(st)))
@@ -414,6 +440,7 @@ TILE_DTYPE = np.dtype([("r0", np.int32), ("r1", np.int32), ("comm", np.int32), (
                        ("bm_off", np.int64), ("nsw", np.int32), ("flags", np.int32)])
 TILE_BITMAP = 1
 TILE_TC = 8
+TILE_VALUED = 16
 TC_KBLOCK = 128
 TC_MBLOCK = 128
 
@@ -439,12 +466,30 @@ def kura_plan_destroy(p):
 
 
 # ----------------------------------------------------------------------------- convenience wrapper
+def kura_create_valued(n, row_ptr, col, val, label, n_comm, omega, K, opts: Optional[KuraOpts] = None, stream=None):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.int32)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    if val.shape != col.shape:
+        raise ValueError("val must match col")
+    h = C.c_void_p()
+    rc = load().kura_create_valued(int(n), row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                   val.ctypes.data if val.size else None, label.ctypes.data, int(n_comm),
+                                   omega.ctypes.data, float(K), C.byref(opts) if opts is not None else None,
+                                   stream or None, C.byref(h))
+    _check(rc, None)
+    return h
+
+
 class Kuramoto:
-    """A libkura handle: the graph, omega and K resident on the GPU."""
+    """A libkura handle: the graph, omega and K resident on the GPU.  val (optional, int32 1..127 parallel to
+    col) makes the adjacency finite-valued (kura_create_valued)."""
 
     def __init__(self, row_ptr, col, label, n_comm, omega, K, precision=PREC_FP64,
                  scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None, bitmap_zmin=None,
-                 tensor_cores=None):
+                 tensor_cores=None, val=None):
         self.n = int(np.asarray(row_ptr).shape[0] - 1)
         self.n_comm = int(n_comm)
         o = kura_default_opts()
@@ -453,7 +498,10 @@ class Kuramoto:
             o.bitmap_zmin = float(bitmap_zmin)
         if tensor_cores is not None:
             o.tensor_cores = int(tensor_cores)
-        self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
+        if val is not None:
+            self.h = kura_create_valued(self.n, row_ptr, col, val, label, n_comm, omega, K, o, stream)
+        else:
+            self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
 
     def rhs(self, theta, out):
         kura_rhs(self.h, theta, out, self.n)

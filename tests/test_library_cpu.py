@@ -334,3 +334,83 @@ def test_gather_rate_probe_rejects_bad_sizes():
     for args in ((0, 1 << 20, 8), (1 << 20, 100, 8), (1 << 20, 1 << 20, 12), (1 << 31, 1 << 20, 8)):
         assert L.kura_measure_gather_rate(*args, None, C.byref(r)) == kura.KURA_EINVAL
     assert L.kura_measure_gather_rate(1 << 20, 1 << 20, 8, None, None) == kura.KURA_EINVAL
+
+
+# ----------------------------------------------------------------------------- finite-valued matrices
+def _valued_case(seed, sizes=(40, 70, 25, 130), max_val=3, noise=0.25):
+    rng = np.random.default_rng(seed)
+    k = len(sizes)
+    V = rng.integers(0, max_val + 1, (k, k))
+    lab = np.repeat(np.arange(k), sizes)
+    A = V[lab][:, lab].astype(np.int32)
+    flip = rng.random(A.shape) < noise
+    A[flip] = rng.integers(0, max_val + 1, int(flip.sum()))
+    np.fill_diagonal(A, 0)
+    perm = rng.permutation(A.shape[0])
+    A, lab = A[perm][:, perm], lab[perm].astype(np.int32)
+    rows, cols = np.nonzero(A)
+    rp = np.zeros(A.shape[0] + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return A, np.cumsum(rp), cols.astype(np.int32), A[rows, cols].astype(np.int32), lab, k
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_valued_plan_stream_emulation_matches_oracle(seed, prec):
+    """A finite-valued plan (Sec. 1, Generalisations) read the way the row kernel reads it: block values times
+    the block sums, plus every packed (column, weight) entry times its (sin, cos); equals the oracle's
+    definition, and the dense-block values are the oracle block rule's."""
+    import oracle
+    A, rp, cl, vl, lab, k = _valued_case(seed)
+    n = A.shape[0]
+    rng = np.random.default_rng(100 + seed)
+    omega, theta, K = rng.normal(size=n), rng.uniform(-20, 20, n), 1.3
+    p = kura.kura_plan_build_valued(n, rp, cl, vl, lab, k, 0.5, prec)
+    try:
+        perm, off = kura.kura_plan_perm(p, n, k)
+        gstream, groups, tiles, row_sub0, _ = kura.kura_plan_export(p, n)
+        dense = [kura.kura_plan_dense_blocks(p, I) for I in range(k)]
+        dvals = [kura.kura_plan_dense_values(p, I) for I in range(k)]
+    finally:
+        kura.kura_plan_destroy(p)
+    _, bv = oracle.rhs_block_valued(rp, cl, vl, 3, lab, k, omega, theta, K)
+    for I in range(k):
+        expect = np.nonzero(bv[I])[0]
+        assert np.array_equal(dense[I], expect) and np.array_equal(dvals[I], bv[I][expect])
+    th = theta[perm]
+    s_tab, c_tab = np.append(np.sin(th), [0, 0]), np.append(np.cos(th), [0, 0])
+    S = np.array([s_tab[off[J]:off[J + 1]].sum() for J in range(k)])
+    C = np.array([c_tab[off[J]:off[J + 1]].sum() for J in range(k)])
+    f = np.empty(n)
+    for t in tiles:
+        assert t["flags"] & kura.TILE_VALUED
+        stash = {}
+        for gi in range(t["g0"], t["g1"]):
+            G_ = groups[gi]
+            base = int(G_["off"])
+            for j in range(G_["nsub"]):
+                mrel, nm, prel, npr = gstream[base + 4 * j: base + 4 * j + 4]
+                seg = np.concatenate([gstream[base + mrel: base + mrel + 4 * ((nm + 3) // 4)],
+                                      gstream[base + prel: base + prel + 4 * ((npr + 3) // 4)]]).astype(np.uint32)
+                col, w = (seg & 0xFFFFFF).astype(np.int64), (seg >> 24).astype(np.int64) - 128
+                assert np.all(col <= n)
+                stash[int(G_["sub0"]) + j] = ((w * s_tab[col]).sum(), (w * c_tab[col]).sum())
+        for r in range(t["r0"], t["r1"]):
+            a_s = sum(stash[s][0] for s in range(row_sub0[r], row_sub0[r + 1]))
+            a_c = sum(stash[s][1] for s in range(row_sub0[r], row_sub0[r + 1]))
+            I = t["comm"]
+            Ts = sum(v * S[J] for J, v in zip(dense[I], dvals[I]))
+            Tc = sum(v * C[J] for J, v in zip(dense[I], dvals[I]))
+            f[r] = omega[perm[r]] + (K / n) * (c_tab[r] * (Ts + a_s) - s_tab[r] * (Tc + a_c))
+    out = np.empty(n)
+    out[perm] = f
+    np.testing.assert_allclose(out, oracle.rhs_valued_csr(rp, cl, vl, omega, theta, K), atol=1e-11, rtol=0)
+
+
+def test_valued_plan_rejects_bad_values():
+    A, rp, cl, vl, lab, k = _valued_case(0)
+    for bad in (0, 128):
+        vb = vl.copy()
+        vb[3] = bad
+        with pytest.raises(Exception):
+            kura.kura_plan_build_valued(A.shape[0], rp, cl, vb, lab, k)
