@@ -223,28 +223,42 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr)
         : "memory");
 }
-// sum_k D_k 16^k of exact-integer FP32 digit sums, in two's complement
+// Mask and digit scaling: a mask column c holds FP8 2^-6 (0x08) when c mod 8 < 4
+// and 2^-5 (0x10) otherwise (cheap to form from the bits, no subnormals); the
+// digits of the latter columns are stored halved, so every product is 2^-6 d and
+// every accumulator is 2^-6 times an exact integer (|sum| <= 4096 * 8 * 2^-6).
+constexpr float TC_DSCALE = 64.0f;
+// sum_k D_k 16^k of exact-integer digit sums (accumulators times 64), in two's complement
 __device__ __forceinline__ long long tc_combine(const uint32_t (&d)[16])
 {
     unsigned long long acc = 0;
 #pragma unroll
     for (int k = TC_NDIG - 1; k >= 0; k--)
-        acc = (acc << 4) + static_cast<unsigned long long>(__float2ll_rn(__uint_as_float(d[k])));
+        acc = (acc << 4) + static_cast<unsigned long long>(__float2ll_rn(__uint_as_float(d[k]) * TC_DSCALE));
     return static_cast<long long>(acc);
 }
 // balanced base-16 digits of the fixed-point (v_s, v_c) of node i into the digit image
+// (halved in columns c mod 8 >= 4, see TC_DSCALE; exact in E4M3)
 __device__ __forceinline__ void tc_write_digits(uint8_t* dig, int64_t i, long long vs, long long vc)
 {
     uint8_t* blk = dig + (i >> 7) * TC_BBYTES;
     const int c = int(i & 127);
+    const float sc = (c & 7) >= 4 ? 0.5f : 1.0f;
 #pragma unroll
     for (int k = 0; k < TC_NDIG; k++) {
         const int ds = int((vs + 8) & 15) - 8, dc = int((vc + 8) & 15) - 8;
         vs = (vs - ds) >> 4;
         vc = (vc - dc) >> 4;
-        blk[tc_digit_offset(k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(ds), __NV_SATFINITE, __NV_E4M3);
-        blk[tc_digit_offset(TC_NDIG + k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(dc), __NV_SATFINITE, __NV_E4M3);
+        blk[tc_digit_offset(k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(ds) * sc, __NV_SATFINITE, __NV_E4M3);
+        blk[tc_digit_offset(TC_NDIG + k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(dc) * sc, __NV_SATFINITE, __NV_E4M3);
     }
+}
+// 8 mask bits (columns 8 m .. 8 m + 7) -> 8 FP8 mask bytes: the low nibble's bits
+// spread to bit 3 of bytes 0-3 (0x08), the high nibble's to bit 4 of bytes 4-7
+// (0x10); the shifted copies of a nibble never overlap, so there are no carries
+__device__ __forceinline__ uint2 tc_expand_byte(uint32_t b)
+{
+    return make_uint2(((b & 0x0Fu) * 0x01020408u) & 0x08080808u, ((b & 0xF0u) * 0x00204081u) & 0x10101010u);
 }
 // digit scale 2^e of the adjoint table: |entry| 2^e < 2^42
 __device__ __forceinline__ int adj_digit_exp(unsigned int absmax_bits)
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         }
         // TILE_TC: warp w expands rows 8 w .. 8 w + 7 of every mask block; lane l
         // takes row 8 w + l / 4, columns 32 (l mod 4) .. + 31 (one mask word, two
-        // 16-byte chunks of FP8 1.0 = 0x38 or 0 in the 128-byte swizzle).
+        // 16-byte chunks of FP8 mask values in the 128-byte swizzle, see TC_DSCALE).
         const int nT = tc ? t.nsw * ((nrows + TC_MBLOCK - 1) / TC_MBLOCK) : 0;
         int tc_next = 0;
         const uint32_t* tc_bits = g.bitmap + t.bm_off + (8 * warp + (lane >> 2)) * 4 + (lane & 3);
@@ -615,12 +629,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             unsigned char* row = tcA + (tt % TC_NA) * TC_ABYTES + r * TC_KBLOCK;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const uint32_t b16 = (w >> (16 * h)) & 0xFFFFu;
-                uint32_t q[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) q[i] = ((((b16 >> (4 * i)) & 0xFu) * 0x00204081u) & 0x01010101u) * 0x38u;
+                const uint2 lo = tc_expand_byte(w >> (16 * h)), hi = tc_expand_byte(w >> (16 * h + 8));
                 const int c = 2 * (lane & 3) + h;
-                *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(q[0], q[1], q[2], q[3]);
+                *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
             }
             fence_proxy_async();
             __syncwarp();
