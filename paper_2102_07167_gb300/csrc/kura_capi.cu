@@ -108,7 +108,7 @@ struct kura_ctx {
     int64_t tile_work = 0;              // planner work target per tile (0: automatic); set by kura_autotune
     int32_t bm_stash_off = 0;
     // device buffers
-    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig, dval;
+    DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig, dval, tcmask;
     bool valued = false;
     DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
     // adjoint (allocated on first use)
@@ -196,6 +196,7 @@ DevGraph dev_graph(kura_ctx* h)
     g.row_sub0 = h->row_sub0.as<int32_t>();
     g.bitmap = h->bitmap.as<uint32_t>();
     g.dig = h->has_tc ? h->dig.as<uint8_t>() : nullptr;
+    g.tcmask = h->has_tc ? h->tcmask.as<uint8_t>() : nullptr;
     g.dval = h->valued ? h->dval.as<int32_t>() : nullptr;
     g.bm_stash_off = h->bm_stash_off;
     g.dptr = h->dptr.as<int64_t>();
@@ -392,8 +393,8 @@ int64_t plan_stream_bytes(const Plan& p)
     int64_t bm = 0;
     for (const Tile& t : p.tiles) {
         if (t.flags & TILE_BITMAP) bm += int64_t(t.r1 - t.r0) * t.nsw * 128;
-        if (t.flags & TILE_TC)
-            bm += int64_t((t.r1 - t.r0 + TC_MBLOCK - 1) / TC_MBLOCK) * t.nsw * TC_MBLOCK * 16 +
+        if (t.flags & TILE_TC)     // FP8 mask images (16 KB per 128 x 128 block) and digit blocks
+            bm += int64_t((t.r1 - t.r0 + TC_MBLOCK - 1) / TC_MBLOCK) * t.nsw * TC_ABYTES +
                   int64_t(t.nsw) * TC_BBYTES;
     }
     return 4 * listed + 16 * int64_t(p.row_sub0.empty() ? 0 : p.row_sub0.back()) + bm;
@@ -465,8 +466,15 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
         // digit image: one 4 KB block per 128 nodes; columns past n stay zero
         KCHECK(h, h->dig.alloc(size_t((h->n + TC_KBLOCK - 1) / TC_KBLOCK) * TC_BBYTES), "alloc digit image");
         KCHECK(h, cudaMemsetAsync(h->dig.p, 0, h->dig.bytes, s), "memset digit image");
+        // mask images: every 128 x 128 block of mask bits (512 words) as 16 KB of FP8 operand
+        const int64_t n_blocks = int64_t(p.bitmap.size()) / (TC_MBLOCK * 4);
+        KCHECK(h, h->tcmask.alloc(size_t(n_blocks) * TC_ABYTES), "alloc mask images");
+        k_tc_expand_masks<<<blocks_for(n_blocks * TC_MBLOCK, 256), 256, 0, s>>>(h->bitmap.as<uint32_t>(), n_blocks,
+                                                                             h->tcmask.as<uint8_t>());
+        KCHECK(h, cudaGetLastError(), "expanding the masks");
     } else {
         h->dig.release();
+        h->tcmask.release();
     }
     KCHECK(h, h->bsum.alloc(16 * nc), "alloc bsum");
     KCHECK(h, cudaMemsetAsync(h->bsum.p, 0, h->bsum.bytes, s), "memset bsum");

@@ -22,10 +22,11 @@ constexpr int ROW_THREADS = (ROW_CONSUMERS + 2) * 32;   // + a producer warp and
 constexpr int TILE_MAX_ROWS = 512;      // rows per tile (the planner's bound)
 constexpr int BM_ROWS = 4;              // rows per warp in the bitmap pass
 constexpr int TRIG_THREADS = 256;
-// slot capacity (int32 units) per precision mode: keeps two CTAs resident per SM
 // Per precision mode (FP64 entries are 16 bytes, mixed 8): ring slots, slot
-// capacity (int32 units) and sub-rows per tile -- two CTAs stay resident per SM.
-__host__ __device__ constexpr int slot_ints_for(int mode) { return mode == 0 ? 2048 : 3072; }
+// capacity (int32 units) and sub-rows per tile.  Two CTAs must stay resident
+// per SM under the default shared-memory carveout (about 98 KB per CTA; the
+// largest carveout would fit more but shrinks L1, which measured slower).
+__host__ __device__ constexpr int slot_ints_for(int mode) { return 2048; }
 __host__ __device__ constexpr int slots_for(int mode) { return mode == 0 ? 3 : 4; }
 __host__ __device__ constexpr int tile_max_sub_for(int mode) { return mode == 0 ? 512 : 768; }
 __host__ __device__ constexpr int ring_bytes_for(int mode) { return slots_for(mode) * slot_ints_for(mode) * 4; }
@@ -36,7 +37,7 @@ __host__ __device__ constexpr int ring_bytes_for(int mode) { return slots_for(mo
 // the cosine.  Both K-major with the 128-byte swizzle; D = 128 x 32 FP32 in
 // tensor memory per M-block (exact: every product is a small integer and
 // every partial sum stays below 2^24).
-constexpr int TC_NA = 2;                                  // mask stages (one per team of 8 warps)
+constexpr int TC_NA = 3;                                  // mask stages
 constexpr int TC_NB = 2;                                  // digit stages
 constexpr int TC_NDIG = 16;                               // digits per value
 constexpr int TC_ABYTES = TC_MBLOCK * TC_KBLOCK;          // 16384
@@ -80,7 +81,8 @@ struct DevGraph {
     const Group* groups;
     const Tile* tiles;
     const int32_t* row_sub0;                // [n+1] first sub-row of each row
-    const uint32_t* bitmap;                 // row bitmaps of TILE_BITMAP tiles, masks of TILE_TC tiles
+    const uint32_t* bitmap;                 // row bitmaps of TILE_BITMAP tiles, mask bits of TILE_TC tiles
+    const uint8_t* tcmask;                  // TILE_TC mask blocks as FP8 operand images (16 KB each, swizzled)
     uint8_t* dig;                           // digit image of the table (TILE_TC tiles; else null)
     int32_t bm_stash_off;                   // byte offset of the bitmap-pass stash in dynamic shared memory
     const int64_t* dptr;                    // [n_comm+1]
@@ -417,13 +419,13 @@ struct Acc2 {
 // added, and the RK4 stage update.
 //
 // TILE_TC tiles list only present entries.  Their missing entries are a 0/1
-// mask: between row groups (and after the last) every consumer warp expands
-// its 8 rows of the next 128 x 128 mask block into an FP8 operand tile in
-// shared memory whenever a stage is free; warp ROW_CONSUMERS + 1 (one lane)
-// loads the matching digit blocks with TMA and issues tcgen05.mma into tensor
-// memory, one 128 x 32 accumulator per M-block of 128 rows.  The epilogue
-// reads the accumulators back and forms the exact fixed-point sum over the
-// missing entries of every row.
+// mask, held as FP8 operand images of 128 x 128 blocks (expanded from the
+// plan's bits once, when the handle is built): warp ROW_CONSUMERS + 1 (one
+// lane) streams them and the matching digit blocks with TMA into shared-memory
+// stages and issues tcgen05.mma into tensor memory, one 128 x 32 accumulator
+// per M-block of 128 rows, while the consumer warps work through the present
+// entries.  The epilogue reads the accumulators back and forms the exact
+// fixed-point sum over the missing entries of every row.
 template <int MODE, int STAGE>
 __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs rk, AdjArgs adj)
 {
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     __shared__ __align__(8) uint64_t a_full[TC_NA], a_empty[TC_NA], b_full[TC_NB], b_empty[TC_NB], d_full;
     __shared__ Acc2<MODE> stash[tile_max_sub_for(MODE)];
     __shared__ int abort_flag;
-    __shared__ int issued[ROW_SLOTS], b_issued[TC_NB];
+    __shared__ int issued[ROW_SLOTS], b_issued[TC_NB], a_issued[TC_NA];
     __shared__ int2 slot_meta[ROW_SLOTS];        // (first sub-row relative to the tile, sub-rows) of the slot's group
     __shared__ uint32_t tmem_base;
 
@@ -474,8 +476,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         }
         mbar_init(&win_bar, 1);
         for (int q = 0; q < TC_NA; q++) {
-            mbar_init(&a_full[q], ROW_CONSUMERS);   // one arrival per consumer warp
+            mbar_init(&a_full[q], 1);               // TMA bulk copy (expect_tx)
             mbar_init(&a_empty[q], 1);              // tcgen05.commit
+            a_issued[q] = 0;
         }
         for (int q = 0; q < TC_NB; q++) {
             mbar_init(&b_full[q], 1);
@@ -517,20 +520,34 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             }
         }
     } else if (warp == TC_WARP) {
-        // ---------------- tensor cores: lane 0 loads the digit blocks with TMA and
-        // issues the MMAs of mask block tt = kb * nM + m (stage tt mod TC_NA) once
-        // every consumer warp has expanded its 8 rows of it
+        // ---------------- tensor cores: lane 0 streams the mask blocks (FP8 operand images
+        // expanded once when the handle is built) and the digit blocks with TMA into
+        // their stages, and issues the MMAs of mask block tt = kb * nM + m (stage tt mod TC_NA)
         if (tc && lane == 0) {
             const int nM = (nrows + TC_MBLOCK - 1) / TC_MBLOCK, nkb = t.nsw, nT = nkb * nM;
             const uint8_t* dsrc = g.dig + size_t(t.wbeg / TC_KBLOCK) * TC_BBYTES;
+            const uint8_t* asrc = g.tcmask + size_t(t.bm_off / (TC_MBLOCK * 4)) * TC_ABYTES;
             bool fail = false;
             for (int kb = 0; kb < TC_NB && kb < nkb; kb++) {
                 mbar_arrive_expect_tx(&b_full[kb], TC_BBYTES);
                 bulk_g2s(tcB + kb * TC_BBYTES, dsrc + size_t(kb) * TC_BBYTES, TC_BBYTES, &b_full[kb]);
                 b_issued[kb] = 1;
             }
+            for (int q = 0; q < TC_NA && q < nT; q++) {
+                mbar_arrive_expect_tx(&a_full[q], TC_ABYTES);
+                bulk_g2s(tcA + q * TC_ABYTES, asrc + size_t(q) * TC_ABYTES, TC_ABYTES, &a_full[q]);
+                a_issued[q] = 1;
+            }
             for (int tt = 0; tt < nT && !fail; tt++) {
                 const int kb = tt / nM, m = tt % nM, st = tt % TC_NA, sb = kb % TC_NB;
+                // refill the stage of block tt - 1 with block tt - 1 + TC_NA once its MMAs are done
+                if (tt >= 1 && tt - 1 + TC_NA < nT) {
+                    const int ps = (tt - 1) % TC_NA;
+                    if (!mbar_wait_bounded(&a_empty[ps], uint32_t((tt - 1) / TC_NA) & 1u, LIMIT_NS)) { fail = true; break; }
+                    mbar_arrive_expect_tx(&a_full[ps], TC_ABYTES);
+                    bulk_g2s(tcA + ps * TC_ABYTES, asrc + size_t(tt - 1 + TC_NA) * TC_ABYTES, TC_ABYTES, &a_full[ps]);
+                    a_issued[ps] = (tt - 1 + TC_NA) / TC_NA + 1;
+                }
                 if (m == 0 && !mbar_wait_bounded(&b_full[sb], uint32_t(kb / TC_NB) & 1u, LIMIT_NS)) { fail = true; break; }
                 if (!mbar_wait_bounded(&a_full[st], uint32_t(tt / TC_NA) & 1u, LIMIT_NS)) { fail = true; break; }
                 tc_fence_after();
@@ -613,42 +630,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 }
             }
         }
-        // TILE_TC: warp w expands rows 8 w .. 8 w + 7 of every mask block; lane l
-        // takes row 8 w + l / 4, columns 32 (l mod 4) .. + 31 (one mask word, two
-        // 16-byte chunks of FP8 mask values in the 128-byte swizzle, see TC_DSCALE).
-        const int nT = tc ? t.nsw * ((nrows + TC_MBLOCK - 1) / TC_MBLOCK) : 0;
-        int tc_next = 0;
-        const uint32_t* tc_bits = g.bitmap + t.bm_off + (8 * warp + (lane >> 2)) * 4 + (lane & 3);
-        // mask words of parts tc_next and tc_next + 1, loaded ahead
-        uint32_t pf0 = nT > 0 ? __ldg(tc_bits) : 0u, pf1 = nT > 1 ? __ldg(tc_bits + TC_MBLOCK * 4) : 0u;
-        auto expand_part = [&](int tt) {
-            const uint32_t w = pf0;
-            pf0 = pf1;
-            pf1 = tt + 2 < nT ? __ldg(tc_bits + size_t(tt + 2) * TC_MBLOCK * 4) : 0u;
-            const int r = 8 * warp + (lane >> 2);
-            unsigned char* row = tcA + (tt % TC_NA) * TC_ABYTES + r * TC_KBLOCK;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint2 lo = tc_expand_byte(w >> (16 * h)), hi = tc_expand_byte(w >> (16 * h + 8));
-                const int c = 2 * (lane & 3) + h;
-                *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
-            }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[tt % TC_NA]);
-        };
-        // non-blocking: expand the next parts while their stages are free
-        auto expand_ready = [&](int max_parts) {
-            for (int e = 0; e < max_parts && tc_next < nT; e++) {
-                const int use = tc_next / TC_NA;
-                int free_ = 1;
-                if (use > 0 && lane == 0) free_ = mbar_try_wait(&a_empty[tc_next % TC_NA], uint32_t(use - 1) & 1u) ? 1 : 0;
-                if (!__shfl_sync(0xffffffffu, free_, 0)) break;
-                expand_part(tc_next++);
-            }
-        };
         for (int gi = 0; gi < ngroups && ok; gi++) {
-            if (tc) expand_ready(4);
             const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
             if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
                 atomicOr(g.err, ERR_TIMEOUT);
@@ -767,16 +749,6 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             }
             if (*(volatile int*)&abort_flag) break;
         }
-        // the remaining mask parts, waiting for free stages
-        while (ok && tc_next < nT) {
-            const int use = tc_next / TC_NA;
-            if (use > 0 && !mbar_wait_bounded(&a_empty[tc_next % TC_NA], uint32_t(use - 1) & 1u, LIMIT_NS)) {
-                atomicOr(g.err, ERR_TIMEOUT);
-                atomicExch(&abort_flag, 1);
-                break;
-            }
-            expand_part(tc_next++);
-        }
     }
     __syncthreads();
     if (abort_flag) {
@@ -788,6 +760,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             if (tc) {
                 for (int q = 0; q < TC_NB; q++)
                     if (b_issued[q] > 0) mbar_wait_bounded(&b_full[q], uint32_t(b_issued[q] - 1) & 1u, LIMIT_NS);
+                for (int q = 0; q < TC_NA; q++)
+                    if (a_issued[q] > 0) mbar_wait_bounded(&a_full[q], uint32_t(a_issued[q] - 1) & 1u, LIMIT_NS);
                 mbar_wait_bounded(&d_full, 0u, LIMIT_NS);
             }
         }
@@ -895,6 +869,25 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         tc_fence_before();
         __syncthreads();
         if (warp == TC_WARP) tc_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- mask images (handle build)
+// One thread per (128 x 128 mask block, row): the row's 128 bits -> 128 FP8 mask
+// bytes in the 128-byte swizzle (16-byte chunk c of row r at chunk c ^ (r mod 8)).
+__global__ void k_tc_expand_masks(const uint32_t* __restrict__ bits, int64_t n_blocks, uint8_t* __restrict__ out)
+{
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= n_blocks * TC_MBLOCK) return;
+    const int r = int(q % TC_MBLOCK);
+    const uint4 w = reinterpret_cast<const uint4*>(bits)[q];
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+    uint8_t* row = out + q * TC_KBLOCK;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const uint32_t b16 = ww[c >> 1] >> ((c & 1) * 16);
+        const uint2 lo = tc_expand_byte(b16), hi = tc_expand_byte(b16 >> 8);
+        *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
     }
 }
 

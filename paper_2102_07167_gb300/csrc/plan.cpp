@@ -427,6 +427,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
                     t.wbeg = c_kb0[size_t(I)] * TC_KBLOCK;
                     t.wlen = 0;
                     t.nsw = c_nkb[size_t(I)];
+                    bm_words = (bm_words + TC_MBLOCK * 4 - 1) / (TC_MBLOCK * 4) * (TC_MBLOCK * 4);   // whole blocks
                     t.bm_off = bm_words;
                     bm_words += nM * int64_t(t.nsw) * TC_MBLOCK * 4;
                     p.tc_tiles++;
