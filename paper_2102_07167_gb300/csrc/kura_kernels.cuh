@@ -230,13 +230,15 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
 // digits of the latter columns are stored halved, so every product is 2^-6 d and
 // every accumulator is 2^-6 times an exact integer (|sum| <= 4096 * 8 * 2^-6).
 constexpr float TC_DSCALE = 64.0f;
-// sum_k D_k 16^k of exact-integer digit sums (accumulators times 64), in two's complement
+// sum_k D_k 16^k of exact-integer digit sums (accumulators times 64, |D_k| <= 4096 * 8,
+// so a 32-bit conversion is exact and far cheaper than a 64-bit one), in two's complement
 __device__ __forceinline__ long long tc_combine(const uint32_t (&d)[16])
 {
     unsigned long long acc = 0;
 #pragma unroll
     for (int k = TC_NDIG - 1; k >= 0; k--)
-        acc = (acc << 4) + static_cast<unsigned long long>(__float2ll_rn(__uint_as_float(d[k]) * TC_DSCALE));
+        acc = (acc << 4) + static_cast<unsigned long long>(
+                               static_cast<long long>(__float2int_rn(__uint_as_float(d[k]) * TC_DSCALE)));
     return static_cast<long long>(acc);
 }
 // balanced base-16 digits of the fixed-point (v_s, v_c) of node i into the digit image
