@@ -130,6 +130,8 @@ def _workload(name: str):
         return G.workload_sbm_large()
     if name == "sbm-2p18":     # same recipe at a quarter of the nodes and communities (profiling size)
         return G.workload_sbm_large(n=1 << 18, n_comm=256)
+    if name == "sbm-2p19":     # half the nodes and communities, p_out doubled: rows keep ~105 sparse entries
+        return G.workload_sbm_large(n=1 << 19, n_comm=512, p_out=2e-4)
     if name == "sbm-65536":
         return G.workload_sbm_small()
     if name == "complete-512":
@@ -489,7 +491,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sbm-2p20", choices=["sbm-2p20", "sbm-2p18", "sbm-65536", "complete-512"])
+    ap.add_argument("--workload", default="sbm-2p20", choices=["sbm-2p20", "sbm-2p19", "sbm-2p18", "sbm-65536", "complete-512"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip the extra comparisons and the CPU baseline")

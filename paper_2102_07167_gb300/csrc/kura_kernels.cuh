@@ -391,6 +391,19 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
 }
 
 // ---------------------------------------------------------------- fused row kernel
+// Releases a ring slot that this warp has read with ordinary shared-memory loads
+// and that TMA (the async proxy) will overwrite: the loads must have returned
+// (the warp-wide reduction over their values waits for every lane) and be ordered
+// before the overwrite (proxy fence) when lane 0 arrives on the slot's barrier.
+__device__ __forceinline__ void release_slot(uint64_t* empty, uint32_t loaded)
+{
+    const uint32_t all = __reduce_or_sync(0xffffffffu, loaded);
+    asm volatile("" ::"r"(all));
+    fence_proxy_async();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(empty);
+}
+
 template <int MODE>
 __device__ __forceinline__ typename EntryT<MODE>::T gather_entry(const typename EntryT<MODE>::T* win, int wbeg,
                                                                  int wlen, const typename EntryT<MODE>::T* table,
@@ -655,8 +668,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 const int4 z4 = make_int4(zidx, zidx, zidx, zidx);
                 const int4 va = lane < ta ? reinterpret_cast<const int4*>(slot + ha_.x)[lane] : z4;
                 const int4 vb = lane < tb ? reinterpret_cast<const int4*>(slot + hb_.x)[lane] : z4;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty_bar[sl]);      // indices are in registers: release the slot
+                release_slot(&empty_bar[sl], uint32_t(va.x | vb.x));      // indices are in registers
                 const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
                 const bool mia = lane < ma, mib = lane < mb;
                 auto fetch = [&](int idx, bool missing) -> E {
@@ -697,8 +709,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                     v[i] = (q < tot4) ? seg[q] : make_int4(zidx, zidx, zidx, zidx);
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty_bar[sl]);      // indices are in registers: release the slot
+            release_slot(&empty_bar[sl], uint32_t(v[0].x | v[1].x | v[2].x | v[3].x));   // indices are in registers
             if (have) {
                 A as = 0, ac = 0;
                 const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
@@ -773,7 +784,27 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         return;
     }
 
-    // ---------------- epilogue: one thread per row, FP64
+    // ---------------- epilogue: thread k takes tile row k (nrows <= TILE_MAX_ROWS <= ROW_THREADS), FP64
+    static_assert(TILE_MAX_ROWS <= ROW_THREADS, "one epilogue row per thread");
+    const bool has_row = tid < nrows;
+    const int64_t row = int64_t(t.r0) + tid;
+    // loads that do not depend on the sums first: their latency overlaps the tensor-memory read
+    int rs0 = 0, rs1 = 0;
+    E own;
+    own.x = 0;
+    own.y = 0;
+    double om = 0.0, yv = 0.0, kv = 0.0, sc = 0.0;
+    if (has_row) {
+        rs0 = g.row_sub0[row];
+        rs1 = g.row_sub0[row + 1];
+        own = gather_entry<MODE>(win, t.wbeg, t.wlen, table, static_cast<int>(row));
+        if (STAGE != ST_ADJ) {
+            om = g.omega[row];
+            sc = g.rscale ? g.rscale[row] : g.scale;
+            if (STAGE >= ST_1 && STAGE <= ST_4) yv = rk.y[row];
+            if (STAGE >= ST_2 && STAGE <= ST_4) kv = rk.krk[row];
+        }
+    }
     // TILE_TC: thread 32 w + l owns tile row 32 w + l = tensor-memory lane
     // 32 (w mod 4) + l of M-block w / 4; its missing-entry sums (fixed point)
     long long ms_s = 0, ms_c = 0;
@@ -790,19 +821,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     // scale of the digits: 2^-q (the table's fixed point), or the adjoint table's own
     const double dig_inv = (STAGE == ST_ADJ && tc) ? ldexp(1.0, -adj_digit_exp(*adj.absmax)) : g.inv_scale_q;
     double gk_local = 0.0;
-    for (int k = tid; k < nrows; k += ROW_THREADS) {
-        const int64_t row = int64_t(t.r0) + k;
-        const int s0 = g.row_sub0[row] - t.sub0, s1 = g.row_sub0[row + 1] - t.sub0;
+    if (has_row) {
+        const int s0 = rs0 - t.sub0, s1 = rs1 - t.sub0;
         A sa = 0, sc_ = 0;
         for (int sidx = s0; sidx < s1; sidx++) {
             sa += stash[sidx].s;
             sc_ += stash[sidx].c;
         }
         if (t.flags & TILE_BITMAP) {     // missing entries given by the bitmap: subtracted
-            sa -= bm_stash[k].s;
-            sc_ -= bm_stash[k].c;
+            sa -= bm_stash[tid].s;
+            sc_ -= bm_stash[tid].c;
         }
-        const E own = gather_entry<MODE>(win, t.wbeg, t.wlen, table, static_cast<int>(row));
         double acc_s, acc_c, si, ci;
         if (MODE == MODE_FP64) {
             const longlong2 T = reinterpret_cast<const longlong2*>(g.T)[t.comm];
@@ -833,25 +862,24 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             } else {
                 adj.lam[row] = adj.lam[row] + adj.asum[row] + a;
             }
-            continue;
-        }
-        const double sc = g.rscale ? g.rscale[row] : g.scale;
-        const double f = g.omega[row] + sc * (ci * acc_s - si * acc_c);
-        if (!isfinite(f)) atomicOr(g.err, ERR_NONFINITE);
-        if (rk.sums_out) rk.sums_out[row] = make_double2(acc_s, acc_c);
-        if (STAGE == ST_RHS) {
-            rk.out[row] = f;
-        } else if (STAGE == ST_1) {
-            rk.krk[row] = f;
-            rk.Y[row] = rk.y[row] + (0.5 * rk.h) * f;
-        } else if (STAGE == ST_2) {
-            rk.krk[row] = rk.krk[row] + 2.0 * f;
-            rk.Y[row] = rk.y[row] + (0.5 * rk.h) * f;
-        } else if (STAGE == ST_3) {
-            rk.krk[row] = rk.krk[row] + 2.0 * f;
-            rk.Y[row] = rk.y[row] + rk.h * f;
         } else {
-            rk.y_out[row] = rk.y[row] + (rk.h / 6.0) * (rk.krk[row] + f);
+            const double f = om + sc * (ci * acc_s - si * acc_c);
+            if (!isfinite(f)) atomicOr(g.err, ERR_NONFINITE);
+            if (rk.sums_out) rk.sums_out[row] = make_double2(acc_s, acc_c);
+            if (STAGE == ST_RHS) {
+                rk.out[row] = f;
+            } else if (STAGE == ST_1) {
+                rk.krk[row] = f;
+                rk.Y[row] = yv + (0.5 * rk.h) * f;
+            } else if (STAGE == ST_2) {
+                rk.krk[row] = kv + 2.0 * f;
+                rk.Y[row] = yv + (0.5 * rk.h) * f;
+            } else if (STAGE == ST_3) {
+                rk.krk[row] = kv + 2.0 * f;
+                rk.Y[row] = yv + rk.h * f;
+            } else {
+                rk.y_out[row] = yv + (rk.h / 6.0) * (kv + f);
+            }
         }
     }
     if (STAGE == ST_ADJ) {

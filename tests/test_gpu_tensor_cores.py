@@ -177,3 +177,26 @@ def test_gather_rate_probe():
     r8 = kura.kura_measure_gather_rate(1 << 20, 1 << 24, 8)
     r16 = kura.kura_measure_gather_rate(1 << 20, 1 << 24, 16)
     assert 1e10 < r8 < 1e13 and 1e10 < r16 < 1e13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_repeated_rhs_bitwise_identical_sbm_2p19(prec):
+    """Every right-hand side is a fixed function of theta: 150 repeated evaluations on the 2^19-node SBM
+    (rows with ~105 sparse entries next to tensor-core masks, the regime in which the row kernel's ring
+    slots turn over fastest) are bitwise identical.  A slot handed back to TMA before the warp's reads of
+    it had completed showed up here as one row of a few percent of FP64 evaluations differing."""
+    w = G.workload_sbm_large(n=1 << 19, n_comm=512, p_out=2e-4)
+    g = w.graph
+    th = torch.tensor(w.theta0, device="cuda:0")
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec) as k:
+        assert k.stats()["tc_tiles"] > 0
+        out = torch.empty_like(th)
+        k.rhs(th, out)
+        k.sync()
+        first = out.clone()
+        bad = 0
+        for _ in range(150):
+            k.rhs(th, out)
+            k.sync()
+            bad += int((out != first).sum())
+    assert bad == 0
