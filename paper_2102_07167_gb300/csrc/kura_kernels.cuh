@@ -241,21 +241,47 @@ __device__ __forceinline__ long long tc_combine(const uint32_t (&d)[16])
                                static_cast<long long>(__float2int_rn(__uint_as_float(d[k]) * TC_DSCALE)));
     return static_cast<long long>(acc);
 }
-// balanced base-16 digits of the fixed-point (v_s, v_c) of node i into the digit image
-// (halved in columns c mod 8 >= 4, see TC_DSCALE; exact in E4M3)
-__device__ __forceinline__ void tc_write_digits(uint8_t* dig, int64_t i, long long vs, long long vc)
+// Balanced base-16 digits d_k in [-8, 7] of a 64-bit two's complement value v
+// (v = sum_k d_k 16^k mod 2^64; the representation is unique since the digits
+// form a complete residue system mod 16): d_k = nibble k of (v + 0x88...8) - 8.
+__device__ __forceinline__ unsigned long long tc_digit_bias(long long v)
 {
-    uint8_t* blk = dig + (i >> 7) * TC_BBYTES;
-    const int c = int(i & 127);
+    return static_cast<unsigned long long>(v) + 0x8888888888888888ull;
+}
+// E4M3 byte of the balanced digit (nibble - 8) times sc (1, or 1/2 in columns c
+// mod 8 >= 4, see TC_DSCALE): 2^23 + nibble is the float with those mantissa
+// bits, and one FMA forms (nibble - 8) sc exactly
+__device__ __forceinline__ uint8_t tc_digit_byte(uint32_t nibble, float sc)
+{
+    const float f = fmaf(__int_as_float(0x4B000000 | int(nibble)), sc, -8388616.0f * sc);
+    return __nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3);
+}
+// the digits of the fixed-point (v_s, v_c) of column c (0..127) into a 4096-byte
+// block of the digit image (global or shared memory)
+__device__ __forceinline__ void tc_put_digits(uint8_t* blk, int c, long long vs, long long vc)
+{
     const float sc = (c & 7) >= 4 ? 0.5f : 1.0f;
+    const unsigned long long us = tc_digit_bias(vs), uc = tc_digit_bias(vc);
 #pragma unroll
     for (int k = 0; k < TC_NDIG; k++) {
-        const int ds = int((vs + 8) & 15) - 8, dc = int((vc + 8) & 15) - 8;
-        vs = (vs - ds) >> 4;
-        vc = (vc - dc) >> 4;
-        blk[tc_digit_offset(k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(ds) * sc, __NV_SATFINITE, __NV_E4M3);
-        blk[tc_digit_offset(TC_NDIG + k, c)] = __nv_cvt_float_to_fp8(static_cast<float>(dc) * sc, __NV_SATFINITE, __NV_E4M3);
+        blk[tc_digit_offset(k, c)] = tc_digit_byte(uint32_t(us >> (4 * k)) & 15u, sc);
+        blk[tc_digit_offset(TC_NDIG + k, c)] = tc_digit_byte(uint32_t(uc >> (4 * k)) & 15u, sc);
     }
+}
+// the digits of node i into the digit image
+__device__ __forceinline__ void tc_write_digits(uint8_t* dig, int64_t i, long long vs, long long vc)
+{
+    tc_put_digits(dig + (i >> 7) * TC_BBYTES, int(i & 127), vs, vc);
+}
+// round to nearest even of an FP32 value |x| < 2^47 as a 64-bit integer, with FP32
+// and 32-bit conversions only (a 64-bit conversion runs at the FP64 rate): the
+// rounded value splits exactly into hi 2^24 + lo, lo in [0, 2^24)
+__device__ __forceinline__ long long f32_to_ll_rn(float x)
+{
+    const float xi = rintf(x);
+    const float hi = floorf(xi * 0x1p-24f);
+    const float lo = fmaf(-hi, 0x1p24f, xi);
+    return static_cast<long long>(__float2int_rz(hi)) * (1ll << 24) + static_cast<long long>(__float2uint_rz(lo));
 }
 // 8 mask bits (columns 8 m .. 8 m + 7) -> 8 FP8 mask bytes: the low nibble's bits
 // spread to bit 3 of bytes 0-3 (0x08), the high nibble's to bit 4 of bytes 4-7
@@ -291,50 +317,69 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 template <int MODE, int WHAT>
 __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, const double* __restrict__ theta)
 {
+    static_assert(TRIG_THREADS == 2 * TC_KBLOCK, "a CTA writes two whole blocks of the digit image");
+    __shared__ __align__(16) uint8_t dstage[2 * TC_BBYTES];      // the CTA's two digit blocks
     const int64_t i = int64_t(blockIdx.x) * TRIG_THREADS + threadIdx.x;
     long long sf = 0, cf = 0;
     int J = -1;
+    float2 tab32 = make_float2(0.0f, 0.0f);
     if (i < g.n) {
         const double th = theta[i];
-        if (!isfinite(th)) atomicOr(g.err, ERR_NONFINITE);
+        if ((__double_as_longlong(th) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) atomicOr(g.err, ERR_NONFINITE);
         if (MODE == MODE_FP64) {
             double s, c;
             sincos(th, &s, &c);
             sf = __double2ll_rn(s * g.scale_q);
             cf = __double2ll_rn(c * g.scale_q);
-            if (WHAT & TB_TABLE) reinterpret_cast<longlong2*>(g.table)[i] = make_longlong2(sf, cf);
         } else {
             // reduce mod 2 pi in FP64, then FP32 sin/cos of |r| <= pi
             const double k = rint(th * KURA_INV_TWO_PI);
             double r = fma(-k, KURA_TWO_PI_HI, th);
             r = fma(-k, KURA_TWO_PI_LO, r);
-            float s, c;
-            sincosf(static_cast<float>(r), &s, &c);
+            sincosf(static_cast<float>(r), &tab32.x, &tab32.y);
             const float sq = static_cast<float>(g.scale_q);
-            sf = __float2ll_rn(s * sq);
-            cf = __float2ll_rn(c * sq);
-            if (WHAT & TB_TABLE) reinterpret_cast<float2*>(g.table)[i] = make_float2(s, c);
+            sf = f32_to_ll_rn(tab32.x * sq);
+            cf = f32_to_ll_rn(tab32.y * sq);
         }
         J = g.node_comm[i];
-        if ((WHAT & TB_TABLE) && g.dig) tc_write_digits(g.dig, i, sf, cf);
     }
+    // block sums first: the fence that orders them before the CTA's ticket then
+    // waits for these atomics only, not for the table and digit stores below
     const unsigned full = 0xffffffffu;
     const int J0 = __shfl_sync(full, J, 0);
     if (__all_sync(full, J == J0) && J0 >= 0) {
+        long long ws = sf, wc = cf;
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            sf += __shfl_xor_sync(full, sf, o);
-            cf += __shfl_xor_sync(full, cf, o);
+            ws += __shfl_xor_sync(full, ws, o);
+            wc += __shfl_xor_sync(full, wc, o);
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&g.bsum[2 * J0], static_cast<unsigned long long>(sf));
-            atomicAdd(&g.bsum[2 * J0 + 1], static_cast<unsigned long long>(cf));
+            atomicAdd(&g.bsum[2 * J0], static_cast<unsigned long long>(ws));
+            atomicAdd(&g.bsum[2 * J0 + 1], static_cast<unsigned long long>(wc));
         }
     } else if (J >= 0) {
         atomicAdd(&g.bsum[2 * J], static_cast<unsigned long long>(sf));
         atomicAdd(&g.bsum[2 * J + 1], static_cast<unsigned long long>(cf));
     }
     __threadfence();
+    if ((WHAT & TB_TABLE) && i < g.n) {
+        if (MODE == MODE_FP64) reinterpret_cast<longlong2*>(g.table)[i] = make_longlong2(sf, cf);
+        else reinterpret_cast<float2*>(g.table)[i] = tab32;
+    }
+    if ((WHAT & TB_TABLE) && g.dig) {
+        // digits staged in shared memory (columns past n hold zero digits), then
+        // written out as whole 16-byte chunks of the image
+        tc_put_digits(dstage + (threadIdx.x >> 7) * TC_BBYTES, int(threadIdx.x & 127), sf, cf);
+        __syncthreads();
+        const int64_t nblk = (g.n + TC_KBLOCK - 1) / TC_KBLOCK, b0 = int64_t(blockIdx.x) * 2;
+#pragma unroll
+        for (int q = threadIdx.x; q < 2 * TC_BBYTES / 16; q += TRIG_THREADS) {
+            const int64_t b = b0 + (q >> 8);
+            if (b < nblk)
+                reinterpret_cast<uint4*>(g.dig + b * TC_BBYTES)[q & 255] = reinterpret_cast<const uint4*>(dstage)[q];
+        }
+    }
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(g.counter, 1u) == gridDim.x - 1);
