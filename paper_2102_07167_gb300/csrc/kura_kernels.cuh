@@ -464,6 +464,31 @@ struct Acc2 {
     typename EntryT<MODE>::A s, c;
 };
 
+// Warp sums of two per-lane values by a halving butterfly: at the first level each
+// half of the warp keeps one value and receives the partner's copy of it, so one
+// shuffle serves both; the total of a lands in lanes 0-15, that of b in 16-31.
+template <class A>
+__device__ __forceinline__ A warp_sum2(A a, A b)
+{
+    const bool up = threadIdx.x & 16;
+    A v = (up ? b : a) + __shfl_xor_sync(0xffffffffu, up ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// The same for four values: totals of a, b, c, d in lanes 0-7, 8-15, 16-23, 24-31.
+template <class A>
+__device__ __forceinline__ A warp_sum4(A a, A b, A c, A d)
+{
+    const bool up = threadIdx.x & 16, mid = threadIdx.x & 8;
+    const A k0 = (up ? c : a) + __shfl_xor_sync(0xffffffffu, up ? a : c, 16);
+    const A k1 = (up ? d : b) + __shfl_xor_sync(0xffffffffu, up ? b : d, 16);
+    A v = (mid ? k1 : k0) + __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // One CTA per tile (rows of one community).  Warp ROW_CONSUMERS is the
 // producer: one elected lane streams the community's (sin, cos) window and
 // then the tile's row groups into a ring of shared-memory slots with TMA bulk
@@ -726,17 +751,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 A sb = (b0.x + b1.x) + (b2.x + b3.x), cb = (b0.y + b1.y) + (b2.y + b3.y);
                 if (mia) { sa = -sa; ca = -ca; }
                 if (mib) { sb = -sb; cb = -cb; }
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-                    ca += __shfl_xor_sync(0xffffffffu, ca, o);
-                    sb += __shfl_xor_sync(0xffffffffu, sb, o);
-                    cb += __shfl_xor_sync(0xffffffffu, cb, o);
-                }
-                if (lane == 0) {
-                    stash[rel0 + j] = Acc2<MODE>{sa, ca};
-                    if (hb) stash[rel0 + j + ROW_CONSUMERS] = Acc2<MODE>{sb, cb};
-                }
+                const A tot = warp_sum4(sa, ca, sb, cb);
+                if (lane == 0) stash[rel0 + j].s = tot;
+                if (lane == 8) stash[rel0 + j].c = tot;
+                if (hb && lane == 16) stash[rel0 + j + ROW_CONSUMERS].s = tot;
+                if (hb && lane == 24) stash[rel0 + j + ROW_CONSUMERS].c = tot;
                 if (*(volatile int*)&abort_flag) break;
                 continue;
             }
@@ -798,12 +817,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                         }
                     }
                 }
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    as += __shfl_xor_sync(0xffffffffu, as, o);
-                    ac += __shfl_xor_sync(0xffffffffu, ac, o);
-                }
-                if (lane == 0) stash[rel0 + j] = Acc2<MODE>{as, ac};
+                const A tot = warp_sum2(as, ac);
+                if (lane == 0) stash[rel0 + j].s = tot;
+                if (lane == 16) stash[rel0 + j].c = tot;
             }
             if (*(volatile int*)&abort_flag) break;
         }
