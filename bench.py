@@ -499,7 +499,14 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--only", choices=["ensemble", "batch"], default=None,
+                    help="run one of the extra measurements alone (for profiling) and print its JSON")
     args = ap.parse_args()
+    if args.only is not None:
+        import torch
+        fn = bench_ensemble if args.only == "ensemble" else bench_batch
+        print(json.dumps(fn(torch.device("cuda", 0), steps=args.steps)))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
