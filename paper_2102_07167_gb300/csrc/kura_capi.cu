@@ -82,7 +82,7 @@ struct BatchData {
 struct EnsData {
     int32_t groups = 0;
     int64_t nblk64 = 0;
-    DevMem comm_off, dptr, dcol, tiles, lptr, lidx, bitmap, node_comm;
+    DevMem comm_off, dptr, dcol, tiles, lptr, lidx, bitmap, aimage, node_comm;
     DevMem table, image, bsum, T, omega, scale, y, Y, krk, f, user;
 };
 
@@ -334,6 +334,7 @@ EnsArgs ens_args(kura_ctx* h)
     a.lptr = e.lptr.as<int64_t>();
     a.lidx = e.lidx.as<int32_t>();
     a.bitmap = e.bitmap.as<uint32_t>();
+    a.aimage = e.aimage.as<uint8_t>();
     a.table = e.table.as<float2>();
     a.image = e.image.as<__nv_bfloat16>();
     a.nblk64 = e.nblk64;
@@ -352,7 +353,7 @@ void enqueue_ens_stage(kura_ctx* h, const EnsArgs& a, const double* in, const Rk
     k_ens_trig<<<dim3(blocks_for(h->n, 256), G), 256, 0, s>>>(a, in);
     k_ens_bsum<<<dim3(unsigned(h->n_comm), G), 256, 0, s>>>(a);
     k_ens_T<<<dim3(blocks_for(int64_t(h->n_comm) * ENS_B, 256), G), 256, 0, s>>>(a);
-    const dim3 grid(unsigned(h->n_tiles), G);
+    const unsigned grid = unsigned(h->n_tiles) * G;      // group fastest: a tile's groups share its mask images
     switch (stage) {
     case ST_RHS: k_ens_row<ST_RHS><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
     case ST_1: k_ens_row<ST_1><<<grid, ENS_THREADS, ENS_SMEM, s>>>(a, rk); break;
@@ -1430,6 +1431,15 @@ kura_status kura_ensemble_create(int64_t n, const int64_t* row_ptr, const int32_
         ECHECK(upload(e.lidx, lidx, s), "upload listed entries");
     }
     ECHECK(upload(e.bitmap, p.bitmap, s), "upload masks");
+    {
+        // the masks as BF16 operand tiles (128 rows x 64 columns, swizzled), expanded once
+        const int64_t n_blocks = int64_t(p.bitmap.size()) / (TC_MBLOCK * 4);
+        ECHECK(e.aimage.alloc(std::max<size_t>(size_t(n_blocks) * 2 * ENS_ABYTES, 16)), "alloc mask images");
+        if (n_blocks > 0)
+            k_ens_expand_masks<<<blocks_for(n_blocks * 2 * TC_MBLOCK, 256), 256, 0, s>>>(e.bitmap.as<uint32_t>(), n_blocks,
+                                                                                      e.aimage.as<uint8_t>());
+        ECHECK(cudaGetLastError(), "expanding the masks");
+    }
     const size_t G = size_t(e.groups), N = size_t(n), B = ENS_B;
     {
         std::vector<double> om(G * N * B), sc(G * B);

@@ -8,7 +8,8 @@
 // (present entries of sparse blocks; missing entries of communities without
 // a mask) are gathered for all trajectories at once from a node-major table.
 //
-// Per stage of one group of ENS_B trajectories (blockIdx.y = group):
+// Per stage of one group of ENS_B trajectories (blockIdx.y = group; k_ens_row
+// runs the groups of a tile next to each other in a one-dimensional grid):
 //   k_ens_trig   FP32 (sin, cos) of the FP64-reduced phases -> node-major table
 //                and the split BF16 image of the mask product's B operand
 //   k_ens_bsum   S_J, C_J per community and trajectory (compensated FP32 per
@@ -25,9 +26,8 @@ namespace kura {
 constexpr int ENS_B = 16;                         // trajectories per group
 constexpr int ENS_N = 4 * ENS_B;                  // GEMM columns: (s_hi, s_lo, c_hi, c_lo) per trajectory
 constexpr int ENS_THREADS = 512;                  // 16 warps
-constexpr int ENS_EXP_THREADS = 128;              // warps 0-3 expand the mask (thread = row)
-constexpr int ENS_MMA_WARP = 4;                   // one lane issues the image copies and the MMAs
-constexpr int ENS_LIST_WARP0 = 5;                 // warps 5-15 gather the listed entries
+constexpr int ENS_MMA_WARP = 4;                   // one lane issues the operand copies and the MMAs
+constexpr int ENS_LIST_WARPS = ENS_THREADS / 32 - 1;   // every other warp gathers the listed entries
 constexpr int ENS_KSUB = 64;                      // mask columns per operand tile (128 bytes of BF16)
 constexpr int ENS_ABYTES = TC_MBLOCK * ENS_KSUB * 2;   // 16 KB
 constexpr int ENS_BBYTES = ENS_N * ENS_KSUB * 2;       // 8 KB: one 64-node block of the image
@@ -54,6 +54,7 @@ struct EnsArgs {
     const int64_t* lptr;                      // [n+1] listed entries of each row in lidx
     const int32_t* lidx;                      // column (present: added) or ~column (missing: subtracted)
     const uint32_t* bitmap;                   // mask blocks of TILE_TC tiles
+    const uint8_t* aimage;                    // the same masks as BF16 operand tiles (128 x 64, swizzled, 16 KB)
     float2* table;                            // [groups][n + 2][ENS_B]
     __nv_bfloat16* image;                     // [groups][nblk64][ENS_N][64] (swizzled blocks)
     int64_t nblk64;                           // 2 ceil(n / 128): covers every 128-column mask block
@@ -148,7 +149,32 @@ __global__ void k_ens_T(EnsArgs a)
     a.T[(size_t(grp) * a.n_comm + I) * ENS_B + b] = make_double2(s, c);
 }
 
-// One CTA per (tile of at most 128 rows, group).
+// Mask operand images, once per plan: one thread per (128 x 128 mask block, 64-column
+// half, row) writes the row's 64 mask bits as BF16 1.0 / 0 (128 bytes, 16-byte
+// chunk c at c xor (row mod 8): the 128-byte swizzle of the operand tile).
+__global__ void k_ens_expand_masks(const uint32_t* __restrict__ bits, int64_t n_blocks, uint8_t* __restrict__ out)
+{
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= n_blocks * 2 * TC_MBLOCK) return;
+    const int r = int(q % TC_MBLOCK);
+    const int64_t qt = q / TC_MBLOCK;                // operand tile: 2 block + half
+    const uint2 w = reinterpret_cast<const uint2*>(bits)[(qt >> 1) * TC_MBLOCK * 2 + int64_t(r) * 2 + (qt & 1)];
+    unsigned char* row = out + size_t(qt) * ENS_ABYTES + size_t(r) * 128;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {                    // 8 columns -> 16 bytes
+        const uint32_t byte = ((c < 4 ? w.x : w.y) >> ((c & 3) * 8)) & 0xFFu;
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t two = (byte >> (2 * k)) & 3u;
+            v[k] = (two & 1u) * 0x3F80u + (two >> 1) * 0x3F800000u;
+        }
+        *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// One CTA per (tile of at most 128 rows, group), the groups of a tile adjacent
+// in the launch order so that they share the tile's mask images in L2.
 template <int STAGE>
 __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk)
 {
@@ -157,9 +183,9 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
     __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], d_full;
     __shared__ float stash[TC_MBLOCK][2 * ENS_B];     // listed-entry sums per row: (s, c) per trajectory
     __shared__ uint32_t tmem_base;
-    __shared__ int fail_flag, b_issued[2];
-    const Tile t = a.tiles[blockIdx.x];
-    const int grp = blockIdx.y;
+    __shared__ int fail_flag, a_issued[2], b_issued[2];
+    const Tile t = a.tiles[blockIdx.x / a.groups];
+    const int grp = int(blockIdx.x % a.groups);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrows = t.r1 - t.r0;
     const bool tc = (t.flags & TILE_TC) != 0;
@@ -173,14 +199,14 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
 
     if (tid == 0) {
         for (int q = 0; q < 2; q++) {
-            mbar_init(&a_full[q], ENS_EXP_THREADS);
+            mbar_init(&a_full[q], 1);
             mbar_init(&a_empty[q], 1);
             mbar_init(&b_full[q], 1);
             mbar_init(&b_empty[q], 1);
         }
         mbar_init(&d_full, 1);
         fail_flag = 0;
-        b_issued[0] = b_issued[1] = 0;
+        a_issued[0] = a_issued[1] = b_issued[0] = b_issued[1] = 0;
     }
     if (tc && warp == ENS_MMA_WARP) tc_alloc(&tmem_base, ENS_TMEM_COLS);
     tc_fence_before();
@@ -188,43 +214,17 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
     tc_fence_after();
     const uint32_t tmem = tc ? tmem_base : 0u;
 
-    if (tid < ENS_EXP_THREADS) {
-        // ---- mask expansion: thread r writes row r of each 128 x 64 tile as BF16 1.0 / 0
-        const int r = tid;
-        // words 2 h, 2 h + 1 of row r of 128-column block kb = q / 2 (h = q mod 2), loaded one tile ahead
-        const uint2* bits = reinterpret_cast<const uint2*>(a.bitmap + t.bm_off) + size_t(r) * 2;
-        uint2 nxt = nT > 0 ? __ldg(bits) : make_uint2(0u, 0u);
-        for (int q = 0; q < nT; q++) {
-            const int st = q & 1, use = q >> 1;
-            const uint2 w = nxt;
-            if (q + 1 < nT) nxt = __ldg(bits + size_t((q + 1) >> 1) * TC_MBLOCK * 2 + ((q + 1) & 1));
-            if (use > 0 && !mbar_wait_bounded(&a_empty[st], uint32_t(use - 1) & 1u, LIMIT_NS)) {
-                atomicOr(a.err, ERR_TIMEOUT);
-                fail_flag = 1;
-                break;
-            }
-            unsigned char* row = A_ + st * ENS_ABYTES + r * 128;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {              // 8 columns -> 16 bytes
-                const uint32_t byte = ((c < 4 ? w.x : w.y) >> ((c & 3) * 8)) & 0xFFu;
-                uint32_t v[4];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t two = (byte >> (2 * k)) & 3u;
-                    v[k] = (two & 1u) * 0x3F80u + (two >> 1) * 0x3F800000u;
-                }
-                *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(v[0], v[1], v[2], v[3]);
-            }
-            fence_proxy_async();
-            mbar_arrive(&a_full[st]);
-        }
-    } else if (warp == ENS_MMA_WARP) {
-        // ---- image copies and MMAs
+    if (warp == ENS_MMA_WARP) {
+        // ---- operand copies (mask images and trajectory images) and MMAs
         if (tc && lane == 0) {
             const unsigned char* img = reinterpret_cast<const unsigned char*>(a.image) +
                                        (size_t(grp) * a.nblk64 + size_t(t.wbeg / ENS_KSUB)) * ENS_BBYTES;
+            const unsigned char* aimg = a.aimage + size_t(t.bm_off / (TC_MBLOCK * 4)) * 2 * ENS_ABYTES;
             bool fail = false;
             for (int q = 0; q < 2 && q < nT; q++) {
+                mbar_arrive_expect_tx(&a_full[q], ENS_ABYTES);
+                bulk_g2s(A_ + q * ENS_ABYTES, aimg + size_t(q) * ENS_ABYTES, ENS_ABYTES, &a_full[q]);
+                a_issued[q] = 1;
                 mbar_arrive_expect_tx(&b_full[q], ENS_BBYTES);
                 bulk_g2s(B_ + q * ENS_BBYTES, img + size_t(q) * ENS_BBYTES, ENS_BBYTES, &b_full[q]);
                 b_issued[q] = 1;
@@ -244,7 +244,13 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
                 tc_commit(&a_empty[st]);
                 tc_commit(&b_empty[st]);
                 if (q + 2 < nT) {
-                    if (!mbar_wait_bounded(&b_empty[st], ph, LIMIT_NS)) { fail = true; break; }
+                    if (!mbar_wait_bounded(&a_empty[st], ph, LIMIT_NS) || !mbar_wait_bounded(&b_empty[st], ph, LIMIT_NS)) {
+                        fail = true;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&a_full[st], ENS_ABYTES);
+                    bulk_g2s(A_ + st * ENS_ABYTES, aimg + size_t(q + 2) * ENS_ABYTES, ENS_ABYTES, &a_full[st]);
+                    a_issued[st] = ((q + 2) >> 1) + 1;
                     mbar_arrive_expect_tx(&b_full[st], ENS_BBYTES);
                     bulk_g2s(B_ + st * ENS_BBYTES, img + size_t(q + 2) * ENS_BBYTES, ENS_BBYTES, &b_full[st]);
                     b_issued[st] = ((q + 2) >> 1) + 1;
@@ -262,8 +268,8 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
         // loads of a round are in flight before any is summed; lanes past the end read the
         // table's zero entry n.
         const float* tabf = reinterpret_cast<const float*>(tab);
-        constexpr int LW = 16 - ENS_LIST_WARP0;
-        int r = warp - ENS_LIST_WARP0;
+        constexpr int LW = ENS_LIST_WARPS;
+        int r = warp < ENS_MMA_WARP ? warp : warp - 1;
         int64_t beg = 0, end = 0;
         if (r < nrows) { beg = a.lptr[t.r0 + r]; end = a.lptr[t.r0 + r + 1]; }
         const int zero = int(a.n);
@@ -343,8 +349,10 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
     if (tc) {
         if (!ok && tid == 0) {
             // let every copy and MMA in flight land before the CTA leaves
-            for (int q = 0; q < 2; q++)
+            for (int q = 0; q < 2; q++) {
+                if (a_issued[q] > 0) mbar_wait_bounded(&a_full[q], uint32_t(a_issued[q] - 1) & 1u, LIMIT_NS);
                 if (b_issued[q] > 0) mbar_wait_bounded(&b_full[q], uint32_t(b_issued[q] - 1) & 1u, LIMIT_NS);
+            }
             mbar_wait_bounded(&d_full, 0u, LIMIT_NS);
         }
         tc_fence_before();
