@@ -414,3 +414,60 @@ def test_valued_plan_rejects_bad_values():
         vb[3] = bad
         with pytest.raises(Exception):
             kura.kura_plan_build_valued(A.shape[0], rp, cl, vb, lab, k)
+
+
+# ----------------------------------------------------------------------------- digit and rounding identities
+# The trig/block-sum kernel forms the tensor-core digit image and the mixed-precision fixed point with two
+# shortcuts. These tests pin the arithmetic of both, in integer and float32 numpy, against the plain
+# definitions.
+
+def _balanced_digits_sequential(v):
+    """Balanced base-16 digits in [-8, 7] by the definition: d = ((v + 8) mod 16) - 8, v <- (v - d) / 16."""
+    out = []
+    for _ in range(16):
+        d = ((v + 8) & 15) - 8
+        out.append(d)
+        v = (v - d) >> 4
+    return out
+
+
+def _balanced_digits_bias(v):
+    """The kernel's form: nibble k of (v + 0x8888888888888888) mod 2^64, minus 8."""
+    u = (v + 0x8888888888888888) & 0xFFFFFFFFFFFFFFFF
+    return [((u >> (4 * k)) & 15) - 8 for k in range(16)]
+
+
+def test_balanced_digits_by_bias_equal_sequential_and_sum_back():
+    rng = np.random.default_rng(11)
+    vals = [0, 1, -1, 7, 8, -8, -9, 2**41, -2**41, 2**62, -2**63, 2**63 - 1]
+    vals += [int(x) for x in rng.integers(-2**62, 2**62, 2000)]
+    vals += [int(x) for x in rng.integers(-2**42, 2**42, 2000)]
+    for v in vals:
+        d = _balanced_digits_bias(v)
+        assert d == _balanced_digits_sequential(v), v
+        assert all(-8 <= x <= 7 for x in d)
+        assert sum(x * 16**k for k, x in enumerate(d)) % 2**64 == v % 2**64
+
+
+def _f32_to_ll_rn_split(x):
+    """The kernel's 64-bit rounding with FP32 operations only: xi = rint(x); hi = floor(xi 2^-24);
+    lo = fma(-hi, 2^24, xi) (exact: an integer in [0, 2^24)); result hi 2^24 + lo."""
+    x = np.float32(x)
+    xi = np.rint(x)                                   # round half to even, float32
+    hi = np.floor(np.float32(xi * np.float32(2.0**-24)))
+    lo = np.float32(np.float64(xi) - np.float64(hi) * 2.0**24)   # the exact fma result, representable
+    assert float(lo) == float(np.float64(xi) - np.float64(hi) * 2.0**24)
+    assert 0.0 <= float(lo) < 2.0**24
+    return int(hi) * 2**24 + int(lo)
+
+
+def test_fp32_split_rounding_equals_round_half_even():
+    rng = np.random.default_rng(12)
+    q = 41
+    s = rng.uniform(-1, 1, 20000).astype(np.float32)
+    s = np.concatenate([s, np.float32([0.0, -0.0, 1.0, -1.0, 2.0**-30, -2.0**-30, 2.0**-41, 1.5 * 2.0**-41,
+                                       2.5 * 2.0**-41, -2.5 * 2.0**-41, 0.5 * 2.0**-41])])
+    for v in s:
+        x = np.float32(v * np.float32(2.0**q))        # the kernel's FP32 product
+        want = int(np.rint(np.float64(x)))           # round half to even of the same float32 value
+        assert _f32_to_ll_rn_split(x) == want, v
