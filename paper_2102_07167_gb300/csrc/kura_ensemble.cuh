@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
     __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], d_full;
     __shared__ float stash[TC_MBLOCK][2 * ENS_B];     // listed-entry sums per row: (s, c) per trajectory
     __shared__ uint32_t tmem_base;
-    __shared__ int fail_flag, a_issued[2], b_issued[2];
+    __shared__ int fail_flag, a_issued[2], b_issued[2], next_row;
     const Tile t = a.tiles[blockIdx.x / a.groups];
     const int grp = int(blockIdx.x % a.groups);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
         mbar_init(&d_full, 1);
         fail_flag = 0;
         a_issued[0] = a_issued[1] = b_issued[0] = b_issued[1] = 0;
+        next_row = ENS_LIST_WARPS;                   // rows 0 .. LW - 1 go to the list warps in order
     }
     if (tc && warp == ENS_MMA_WARP) tc_alloc(&tmem_base, ENS_TMEM_COLS);
     tc_fence_before();
@@ -263,19 +264,22 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
             }
         }
     } else {
-        // ---- listed entries: a warp per row; lane l holds trajectory l / 2, component l mod 2.
+        // ---- listed entries: a warp per row, rows claimed from a shared counter one row
+        // ahead (rows differ in length); lane l holds trajectory l / 2, component l mod 2.
         // The next row's range and each segment's next 32 indices are loaded ahead; all 32 row
         // loads of a round are in flight before any is summed; lanes past the end read the
         // table's zero entry n.
         const float* tabf = reinterpret_cast<const float*>(tab);
-        constexpr int LW = ENS_LIST_WARPS;
         int r = warp < ENS_MMA_WARP ? warp : warp - 1;
         int64_t beg = 0, end = 0;
         if (r < nrows) { beg = a.lptr[t.r0 + r]; end = a.lptr[t.r0 + r + 1]; }
         const int zero = int(a.n);
         while (r < nrows) {
+            int rn = 0;
+            if (lane == 0) rn = atomicAdd(&next_row, 1);
+            rn = __shfl_sync(0xffffffffu, rn, 0);
             int64_t nbeg = 0, nend = 0;
-            if (r + LW < nrows) { nbeg = a.lptr[t.r0 + r + LW]; nend = a.lptr[t.r0 + r + LW + 1]; }
+            if (rn < nrows) { nbeg = a.lptr[t.r0 + rn]; nend = a.lptr[t.r0 + rn + 1]; }
             const int cnt = int(end - beg);
             float acc = 0.0f;
             int nidx = lane < cnt ? a.lidx[beg + lane] : zero;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ens_row(EnsArgs a, RkArgs rk
                 for (int u = 0; u < 32; u++) acc += v[u];
             }
             stash[r][lane] = acc;
-            r += LW;
+            r = rn;
             beg = nbeg;
             end = nend;
         }
