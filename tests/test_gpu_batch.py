@@ -61,3 +61,18 @@ def test_batch_host_pointers_and_limits(ensemble):
     with pytest.raises(kura.KuraError) as e:
         kura.KuramotoBatch([(None, None, None, 1, np.zeros(16385), 1.0)])
     assert e.value.status == kura.KURA_EINVAL
+
+
+def test_batch_integration_bitwise_repeatable():
+    """Three integrations of 256 batch trajectories (50 RK4 steps each, fresh handles) give bitwise equal
+    states: block sums are exact fixed-point sums and every other sum has a fixed order."""
+    ens = G.workload_batch(n_traj=256)
+    theta0 = np.concatenate([t0 for (_, _, _, t0, _) in ens])
+    res = []
+    for _ in range(3):
+        with kura.KuramotoBatch(G.batch_graphs(ens)) as b:
+            th = torch.tensor(theta0, device="cuda:0")
+            b.rk4_steps(th, 0.01, 50)
+            torch.cuda.synchronize()
+            res.append(th.cpu().numpy())
+    assert all(np.array_equal(r, res[0]) for r in res)

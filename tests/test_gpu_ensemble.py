@@ -112,3 +112,24 @@ def test_ensemble_rejects_bad_sizes(ragged):
     omega, K, _ = _inputs(g, 8, 4)
     with pytest.raises(Exception):
         kura.KuramotoEnsemble(g.row_ptr, g.col, g.label, g.n_comm, omega, K)      # 8 is not a multiple of 16
+
+
+def test_ensemble_rhs_bitwise_repeatable():
+    """The ensemble's right-hand side is a fixed function of theta: 100 repeated evaluations for 64
+    trajectories on the 65536-node SBM (mask and trajectory images streamed by TMA into two stages)
+    are bitwise identical."""
+    w = G.workload_sbm_small()
+    g = w.graph
+    omega, K, theta = _inputs(g, 64, 6)
+    with kura.KuramotoEnsemble(g.row_ptr, g.col, g.label, g.n_comm, omega, K) as e:
+        th = torch.tensor(theta, device="cuda:0")
+        out = torch.empty_like(th)
+        e.rhs(th, out)
+        e.sync()
+        first = out.clone()
+        bad = 0
+        for _ in range(100):
+            e.rhs(th, out)
+            e.sync()
+            bad += int((out != first).any(dim=1).sum())
+    assert bad == 0
