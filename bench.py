@@ -150,24 +150,63 @@ def _workload_desc(w, st):
                   (st["stream_bytes"] / 1e9)}
 
 
-def cpu_baseline_oracle(w, seconds: float = 12.0):
+def cpu_baseline_oracle(w, seconds: float = 12.0, keep_values: bool = False):
     """The FP64 oracle as it stands (CSR definition, one sine per edge, one core) on a bounded sample of
-    rows of the same graph; 4 right-hand-side evaluations per RK4 step."""
+    rows of the same graph; 4 right-hand-side evaluations per RK4 step.  With keep_values the sampled rows
+    and the oracle's values there are returned too (keys "_rows", "_ref"), so that the GPU's right-hand
+    side at the same phases can be compared with them."""
     import oracle
     from paper_2102_07167_gb300 import gen as G
     g = w.graph
     order = G.permutation(123, g.n).astype(np.int64)
     done, t0, pos, batch = 0, time.perf_counter(), 0, 2048
+    vals = []
     while time.perf_counter() - t0 < seconds and pos < g.n:
         rows = order[pos:pos + batch]
-        oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, rows=rows)
+        v = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K, rows=rows)
+        if keep_values:
+            vals.append(v)
         pos += rows.size
         done += rows.size
     el = time.perf_counter() - t0
     rows_per_s = done / el
-    return {"value": rows_per_s / 4.0, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle right-hand side (CSR definition) on {done} random rows of the "
-                      f"{g.n}-node graph in {el:.1f} s; RK4 step = 4 evaluations, extrapolated to N rows"}
+    out = {"value": rows_per_s / 4.0, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "nproc": os.cpu_count(), "cpu_model": _cpu_model(),
+           "sample": f"FP64 oracle right-hand side (CSR definition) on {done} random rows of the "
+                     f"{g.n}-node graph in {el:.1f} s on one core; RK4 step = 4 evaluations, extrapolated to "
+                     "N rows"}
+    if keep_values:
+        out["_rows"] = order[:done]
+        out["_ref"] = np.concatenate(vals) if vals else np.zeros(0)
+    return out
+
+
+def _cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def scale_free_errors(f_gpu, rows, ref, w) -> dict:
+    """max over the sampled rows of e_i = |f_i - o_i| / ((K/N)(1 + deg_i)) and of |f_i - o_i|."""
+    g = w.graph
+    deg = np.diff(g.row_ptr)[rows]
+    d = np.abs(np.asarray(f_gpu)[rows] - ref)
+    e = d / ((abs(w.K) / g.n) * (1.0 + deg))
+    return {"max_scale_free": float(e.max()) if e.size else None, "max_abs": float(d.max()) if d.size else None,
+            "rows": int(rows.size)}
 
 
 def bench_adjoint(dev):
@@ -360,9 +399,14 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (row kernel): algorithmic bytes / mean launch time
     peak, peak_kind = _peaks()
-    alg_bytes = st["stream_bytes"] + st["node_bytes_row"]
+    # algorithmic bytes of the method: 4 B per stored correction index (a missing entry of a dense block or
+    # a present entry of a sparse block, int32) plus the row kernel's per-node traffic; the bytes the
+    # chosen encoding streams (tensor-core mask images, headers, digits) are reported beside them
+    alg_bytes = 4 * (st["missing_entries"] + st["sparse_entries"]) + st["node_bytes_row"]
+    enc_bytes = st["stream_bytes"] + st["node_bytes_row"]
     row_ms = float(np.mean(launch_ms)) if launch_ms.size else None
     achieved = alg_bytes / (row_ms * 1e-3) / 1e9 if row_ms else None
+    achieved_enc = enc_bytes / (row_ms * 1e-3) / 1e9 if row_ms else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "row_kernel_traffic.json")
     if os.path.exists(tpath):
@@ -378,7 +422,12 @@ def run_ours(args):
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "kernel": "k_row_stage",
-                "algorithmic_bytes_per_launch": alg_bytes, "row_kernel_ms": row_ms,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_bytes_def": "4 B per stored correction index (missing + present entries) + "
+                                         f"{st['node_bytes_row'] // max(n, 1)} B per node (row kernel node traffic)",
+                "encoding_bytes_per_launch": enc_bytes, "encoding_achieved": achieved_enc,
+                "encoding_frac": (achieved_enc / peak) if achieved_enc else None,
+                "row_kernel_ms": row_ms,
                 "launches_timed": int(launch_ms.size),
                 # the kernel's actual limiter: random L2 gathers of the present (sparse-block) entries
                 "present_gathers_per_launch": int(st["sparse_entries"]),
@@ -413,6 +462,7 @@ def run_ours(args):
                                     "step, un-permute, D2H, synchronise"}
 
     extra = {}
+    f_host = {}
     if not args.quick and rank == 0:
         # mixed vs FP64 path error on one right-hand side (both through the library)
         th0 = torch.tensor(w.theta0, device=dev)
@@ -424,6 +474,7 @@ def run_ours(args):
         k2 = kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=other)
         f_b = torch.empty_like(th0)
         k2.rhs(th0, f_b)
+        f_host = {args.precision: f_a.cpu().numpy(), ("fp64" if other == kura.PREC_FP64 else "mixed"): f_b.cpu().numpy()}
         deg = torch.tensor(np.diff(g.row_ptr), device=dev, dtype=torch.float64)
         err = (f_a - f_b).abs()
         extra["rhs_error_vs_other_precision"] = {
@@ -468,8 +519,16 @@ def run_ours(args):
     if not args.quick and rank == 0 and not args.no_ensemble:
         extra["ensemble_shared_graph"] = bench_ensemble(dev)
 
-    cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds) if (rank == 0 and world == 1 and not args.quick) \
-        else None
+    cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds, keep_values=True) \
+        if (rank == 0 and world == 1 and not args.quick) else None
+    if cpu is not None:
+        rows, ref = cpu.pop("_rows"), cpu.pop("_ref")
+        # the rows the CPU-baseline leg evaluated with the oracle give the GPU's error at the same phases
+        extra["rhs_error_vs_oracle"] = {
+            p: scale_free_errors(f, rows, ref, w) for p, f in f_host.items()}
+        extra["rhs_error_vs_oracle"]["definition"] = (
+            "e_i = |f_i - o_i| / ((K/N)(1 + deg_i)) on the rows of the cpu_baseline sample, o = FP64 oracle "
+            "(CSR definition); bound 1e-6 mixed, 1e-10 FP64")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,

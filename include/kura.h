@@ -356,31 +356,39 @@ void kura_destroy(kura_t h);
 /* Order parameters for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a deployment convenience.  Some
  * callers may not call cudaMalloc at all: plug-ins inside a host application
- * that owns a fixed device-memory budget, code running while another library
- * holds a stream capture open (an allocation there would break the capture or
- * synchronise the device), or real-time loops that must not block.  Those
- * callers pass their own input and output buffers; the scratch this needs
- * lives in a file-scope __device__ array of the library (3 * 8 bytes per
- * community plus one word, at most KURA_STATIC_MAX_COMM communities, about
- * 96 KB), which every GPU that loads the library holds until process exit.
+ * that owns the whole device-memory budget and grants them none, and
+ * real-time or watchdog-supervised loops in which the implicit device
+ * synchronisation and unbounded latency of cudaMalloc/cudaFree are not
+ * allowed.  Those callers pass their own input and output buffers; the
+ * scratch this needs lives in a file-scope __device__ array of the library
+ * (3 * 8 bytes per community plus two words, at most KURA_STATIC_MAX_COMM
+ * communities, about 96 KB), which every GPU that loads the library holds
+ * until process exit.
  *
  *   n                 number of oscillators, >= 1
  *   theta[n]          device, phases (any order)
  *   label[n]          device, community of each oscillator in [0, n_comm),
  *                     or NULL for one community (then n_comm must be 1)
  *   n_comm            1 .. KURA_STATIC_MAX_COMM; larger values -> KURA_EINVAL
- *   out[2 + 2 n_comm] device: r, psi of eq:OrderParameter, then r_J, psi_J
- *                     of every community (0, 0 for an empty one)
+ *   out[2 + 2 n_comm] device: out[0] = |(1/n) sum_m e^{i theta_m}| and
+ *                     out[1] its argument (0 when the modulus is 0); then
+ *                     out[2 + 2 J], out[3 + 2 J] the same mean over the
+ *                     members of community J (0, 0 for an empty one)
  *   stream            cudaStream_t (NULL: legacy default stream)
  * Asynchronous on the stream.  It allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library routine.  The first call on a device looks
- * up that device's address of the scratch array (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call on a device
- * shares the one scratch array: calls that overlap on the GPU (concurrent
- * streams, or several host threads) race and give wrong results, so
- * serialise them.  Each call zeroes the part of the scratch it uses before
- * its kernel runs, and the kernel leaves it zeroed.  The sums are exact
- * 64-bit fixed-point sums of FP64 sin/cos, as in kura_order_params. */
+ * cudaFree, no allocating library routine.  The labels are device data, so
+ * the host cannot check them: the kernel skips every oscillator whose label
+ * lies outside [0, n_comm) and then writes NaN to every entry of out, so a
+ * bad label never touches memory outside the scratch rows of this call.
+ * Set-up: the first call in each CUDA context looks up the device address of
+ * the scratch array (cudaGetSymbolAddress, with the device current) and
+ * caches it with the context's id; after cudaDeviceReset the next call looks
+ * it up again.  Make that first call on a device before any stream capture.
+ * Every call on a device shares the one scratch array: calls that overlap on
+ * the GPU (concurrent streams, or several host threads) race and give wrong
+ * results, so serialise them.  Each call zeroes the part of the scratch it
+ * uses before its kernel runs, and the kernel leaves it zeroed.  The sums are
+ * exact 64-bit fixed-point sums of FP64 sin/cos, as in kura_order_params. */
 #define KURA_STATIC_MAX_COMM 4096
 kura_status kura_order_params_static(int64_t n, const double* theta, const int32_t* label,
                                      int32_t n_comm, double* out, void* stream);

@@ -18,13 +18,19 @@ class KuraRK4Loss(torch.autograd.Function):
     theta0, omega: float64 CUDA tensors of length n (user order); K: float64 0-d tensor.
     system: a kura.Kuramoto handle created with precision=kura.PREC_MIXED on the same graph.
     loss_kind 0: 1 - r(theta(T)); 1: 1/2 ||theta(T) - target||^2.
+    The handle runs the adjoint with the given omega and K and gets its previous omega and K back afterwards.
     """
 
     @staticmethod
     def forward(ctx, theta0, omega, K, system, step, n_steps, ckpt_every=64, loss_kind=0, target=None):
+        prev_omega, prev_K = system.omega, system.K
         system.set_param(omega=omega.detach().contiguous(), K=float(K))
-        loss, g_om, g_K, g_th = system.adjoint(theta0.detach().contiguous(), step, n_steps, ckpt_every,
-                                               loss_kind, None if target is None else target.detach().contiguous())
+        try:
+            loss, g_om, g_K, g_th = system.adjoint(theta0.detach().contiguous(), step, n_steps, ckpt_every,
+                                                   loss_kind,
+                                                   None if target is None else target.detach().contiguous())
+        finally:
+            system.set_param(omega=prev_omega, K=prev_K)
         ctx.save_for_backward(g_th, g_om, torch.tensor(g_K, dtype=torch.float64, device=theta0.device))
         return torch.tensor(loss, dtype=torch.float64, device=theta0.device)
 

@@ -25,6 +25,19 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// SM count of the current device (the planner sizes tiles by it); 152, the
+// GB300 count, if the query fails.
+int current_sm_count()
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return nsm;
+}
+
 // ---------------------------------------------------------------- device memory
 struct DevMem {
     void* p = nullptr;
@@ -626,6 +639,7 @@ static kura_status create_impl(int64_t n, const int64_t* row_ptr, const int32_t*
         return KURA_EINVAL;
     }
     PlanInput in;
+    in.n_sms = current_sm_count();
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.val = val;
     in.tile_max_rows = TILE_MAX_ROWS;
@@ -713,6 +727,7 @@ kura_status kura_classify_blocks(kura_t h, double tau, kura_block_stats* stats)
         if (h->h_col.empty() && h->nnz > 0)
             return h->fail(KURA_ESTATE, "re-classification needs the host CSR copy (keep_host_csr = 1)");
         PlanInput in;
+        in.n_sms = current_sm_count();
         in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
         in.n_comm = h->n_comm; in.tau = tau;
         in.val = h->h_val.empty() ? nullptr : h->h_val.data();
@@ -740,6 +755,7 @@ namespace {
 kura_status rebuild_plan(kura_t h, double tau, int32_t tensor_cores, int64_t tile_work)
 {
     PlanInput in;
+    in.n_sms = current_sm_count();
     in.n = h->n; in.row_ptr = h->h_row_ptr.data(); in.col = h->h_col.data(); in.label = h->h_label.data();
     in.n_comm = h->n_comm; in.tau = tau;
     in.val = h->h_val.empty() ? nullptr : h->h_val.data();
@@ -816,7 +832,7 @@ kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_t
     // the automatic work target, as the planner computes it
     int64_t total = 0;
     for (int64_t v = 0; v < h->n; v++) total += h->plan.miss_cnt[size_t(v)] + h->plan.pres_cnt[size_t(v)] + 8;
-    const int64_t auto_work = std::max<int64_t>(2048, total / (152 * 12));
+    const int64_t auto_work = std::max<int64_t>(2048, total / (int64_t(current_sm_count()) * 12));
     int64_t best_work = h->tile_work > 0 ? h->tile_work : auto_work;
     auto try_plan = [&](double tau, int32_t tc, int64_t work) -> kura_status {
         if (elapsed() > budget_s) return KURA_OK;
@@ -1372,6 +1388,7 @@ kura_status kura_ensemble_create(int64_t n, const int64_t* row_ptr, const int32_
     for (int32_t b = 0; b < n_traj; b++)
         if (!std::isfinite(K[b])) { g_create_error = "K has a non-finite entry"; return KURA_EINVAL; }
     PlanInput in;
+    in.n_sms = current_sm_count();
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.tile_max_rows = TC_MBLOCK;                  // one M-block per CTA
     in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
@@ -1750,6 +1767,7 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             p.row_sub0.assign(size_t(gd.n) + 1, 0);      // no sub-rows: no stored corrections
         } else {
             PlanInput in;
+            in.n_sms = current_sm_count();
             in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
             in.tau = o.tau;
             in.tile_max_rows = TILE_MAX_ROWS;
@@ -1930,7 +1948,7 @@ static kura_status plan_build_impl(int64_t n, const int64_t* row_ptr, const int3
     std::unique_ptr<kura_plan_s> p(new (std::nothrow) kura_plan_s());
     if (!p) return KURA_ENOMEM;
     const int mode = o.precision == KURA_PREC_MIXED ? MODE_MIXED : MODE_FP64;
-    PlanInput in;
+    PlanInput in;                      // host only: tile sizing for GB300's 152 SMs
     in.n = n; in.row_ptr = row_ptr; in.col = col; in.label = label; in.n_comm = n_comm; in.tau = o.tau;
     in.tile_max_rows = TILE_MAX_ROWS;
     in.tile_max_sub = tile_max_sub_for(mode);

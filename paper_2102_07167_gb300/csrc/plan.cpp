@@ -394,7 +394,7 @@ int build_plan(const PlanInput& in, Plan& p, std::string& err)
         // GROUP_MAX_SUB, whose packed stream fits one slot of the row kernel).
         int64_t total_work = 0;
         for (int64_t v = 0; v < n; v++) total_work += p.miss_cnt[size_t(v)] + p.pres_cnt[size_t(v)] + 8;
-        const int64_t target = in.tile_work > 0 ? in.tile_work : std::max<int64_t>(2048, total_work / (152 * 12));
+        const int64_t target = in.tile_work > 0 ? in.tile_work : std::max<int64_t>(2048, total_work / (int64_t(std::max(in.n_sms, 1)) * 12));
         p.sub_hdr.resize(size_t(n_sub));
         std::vector<int64_t>& sub_mpos = p.sub_mpos;
         std::vector<int64_t>& sub_ppos = p.sub_ppos;

@@ -97,6 +97,9 @@ struct PlanInput {
     double tau = 0.5;                   // dense iff zero fraction < tau
     int32_t window_cap = 4096;          // max staged window entries per tile
     int64_t tile_work = 0;              // target entries per tile (0: automatic)
+    // SM count of the GPU the plan is for: the automatic tile work aims at
+    // about 12 tiles per SM (the host-only plan builder assumes GB300's 152)
+    int32_t n_sms = 152;
     int32_t tile_max_rows = 512;
     int32_t tile_max_sub = 768;         // sub-rows per tile (stash capacity of the row kernel)
     int32_t slot_ints = 4096;           // capacity of one row-group slot (int32 units)

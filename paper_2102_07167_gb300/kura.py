@@ -502,6 +502,9 @@ class Kuramoto:
             self.h = kura_create_valued(self.n, row_ptr, col, val, label, n_comm, omega, K, o, stream)
         else:
             self.h = kura_create(self.n, row_ptr, col, label, n_comm, omega, K, o, stream)
+        # the handle's current parameters (copies), so that callers can put them back
+        self.omega = np.array(omega, dtype=np.float64)
+        self.K = float(K)
 
     def rhs(self, theta, out):
         kura_rhs(self.h, theta, out, self.n)
@@ -514,6 +517,10 @@ class Kuramoto:
 
     def set_param(self, omega=None, K=None):
         kura_set_param(self.h, omega, K, self.n)
+        if omega is not None:
+            self.omega = omega.clone() if hasattr(omega, "data_ptr") else np.array(omega, dtype=np.float64)
+        if K is not None:
+            self.K = float(K)
 
     def classify_blocks(self, tau=-1.0):
         return kura_classify_blocks(self.h, tau)

@@ -1,0 +1,101 @@
+"""Writes the FP64 trajectory goldens of the SBM workloads from the CPU oracle.
+
+The expected phases come from ``oracle.rk4_csr`` only: classical fixed-step
+RK4 (tableau 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) on eq:KuramotoGraph
+(Sec. 3) with uniform scaling K/N, the right-hand side evaluated by the CSR
+definition with one sine per edge and compensated sums.  The inputs come
+from the seeded generators in ``paper_2102_07167_gb300.gen`` (which draw
+inputs and hold none of the model's arithmetic).  Nothing here touches the
+CUDA library.
+
+The full trajectories take the single-threaded oracle minutes to hours, far
+longer than a test may take, so each case stores theta(T) at a fixed random
+sample of nodes, with a fingerprint of the inputs (SHA-256 of the CSR arrays,
+sums of omega and theta0) that the GPU test checks before it compares.
+
+Cases:
+  sbm65536_1000   65536-node SBM (64 communities, Dirichlet(2) sizes with
+                  minimum 128, p_in 0.95, p_out 0.001), K = 4, h = 0.005,
+                  1000 steps (T = 5), seed 0
+  sbm2p16_500     the 2^20-node recipe at N = 2^16 (64 communities, sizes
+                  clipped to [256, 4096], p_in ~ U[0.5, 0.99], p_out 1e-4,
+                  omega ~ Cauchy(0, 0.5) clipped at 10), K = 3, h = 0.01,
+                  500 steps (T = 5), seed 0
+  sbm2p20_10      the 2^20-node SBM itself (1024 communities), 10 steps of
+                  h = 0.01, seed 0
+
+Usage: python tests/golden/make_trajectory_goldens.py CASE [CASE ...]
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SAMPLE = 2048
+SAMPLE_SEED = 20210215
+
+
+def workload(case: str):
+    from paper_2102_07167_gb300 import gen as G
+    if case == "sbm65536_1000":
+        return G.workload_sbm_small(), 0.005, 1000
+    if case == "sbm2p16_500":
+        return G.workload_sbm_large(n=1 << 16, n_comm=64), 0.01, 500
+    if case == "sbm2p20_10":
+        return G.workload_sbm_large(), 0.01, 10
+    raise ValueError(f"unknown case {case}")
+
+
+def fingerprint(w) -> dict:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(w.graph.row_ptr, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(w.graph.col, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(w.graph.label, dtype="<i4").tobytes())
+    return {"n": int(w.graph.n), "nnz": int(w.graph.nnz), "n_comm": int(w.graph.n_comm),
+            "graph_sha256": h.hexdigest(), "omega_sum": float(np.sum(w.omega)),
+            "omega_abs_sum": float(np.sum(np.abs(w.omega))), "theta0_sum": float(np.sum(w.theta0))}
+
+
+def sample_nodes(n: int) -> np.ndarray:
+    return np.sort(np.random.default_rng(SAMPLE_SEED).choice(n, size=min(N_SAMPLE, n), replace=False))
+
+
+def path(case: str) -> str:
+    return os.path.join(HERE, f"traj_{case}_fp64.json")
+
+
+def make(case: str) -> None:
+    import oracle
+    w, h, steps = workload(case)
+    fp = fingerprint(w)
+    idx = sample_nodes(w.graph.n)
+    t0 = time.time()
+    th = oracle.rk4_csr(w.graph.row_ptr, w.graph.col, w.omega, w.K, w.theta0, h, steps)
+    secs = time.time() - t0
+    r, psi = oracle.order_params(th)
+    rec = {
+        "case": case, "workload": w.name, "K": w.K, "h": h, "n_steps": steps, "precision": "fp64",
+        "source": "oracle.rk4_csr (classical RK4 on eq:KuramotoGraph, CSR definition, uniform K/N)",
+        "oracle_seconds": round(secs, 1), **fp,
+        "r_T": r, "psi_T": psi,
+        "idx": [int(i) for i in idx], "theta_T": [float(v) for v in th[idx]],
+    }
+    with open(path(case) + ".tmp", "w") as f:
+        json.dump(rec, f, indent=0)
+    os.replace(path(case) + ".tmp", path(case))
+    print(f"{case}: {steps} steps in {secs:.0f} s, r(T) = {r:.6f}", flush=True)
+
+
+if __name__ == "__main__":
+    for c in sys.argv[1:]:
+        make(c)

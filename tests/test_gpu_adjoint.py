@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _parity import check_rhs
 from paper_2102_07167_gb300 import gen as G
 
 torch = pytest.importorskip("torch")
@@ -126,3 +127,11 @@ def test_autograd_function(small):
             K2 = K - 50.0 * K.grad
         loss2 = KuraRK4Loss.apply(th0.detach(), om.detach(), K2, k, 0.01, 20, 8, 0, None)
         assert loss2.item() < loss.item()
+        # the handle has its own omega and K back: its right-hand side is the oracle's with w.omega, w.K
+        assert k.K == w.K
+        th = torch.tensor(w.theta0, device=dev)
+        f = torch.empty_like(th)
+        k.rhs(th, f)
+        k.sync()
+        ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
+        check_rhs(f.cpu().numpy(), ref, np.diff(g.row_ptr), w.K, g.n, 1, "handle after KuraRK4Loss")

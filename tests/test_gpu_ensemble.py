@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _parity import check_rhs
 from paper_2102_07167_gb300 import gen as G
 
 torch = pytest.importorskip("torch")
@@ -66,7 +67,7 @@ def test_ensemble_rhs_every_trajectory_vs_oracle(ragged, tcm):
     deg = np.diff(g.row_ptr)
     for b in range(32):
         ref = oracle.rhs_csr(g.row_ptr, g.col, omega[b], theta[b], K[b])
-        assert np.all(np.abs(f[b] - ref) <= 2e-4 * (1 + deg) * np.maximum(1.0, np.abs(ref))), b
+        check_rhs(f[b], ref, deg, K[b], g.n, 1, f"ragged ensemble trajectory {b}")
 
 
 def test_ensemble_rk4_trajectories_vs_oracle(ragged):
@@ -84,9 +85,9 @@ def test_ensemble_rk4_trajectories_vs_oracle(ragged):
         assert np.abs(out[b] - ref).max() < 1e-5, b
 
 
-def test_ensemble_sbm_matches_single_handles():
-    """On an SBM the ensemble's trajectories agree with single-trajectory mixed-precision handles to
-    FP32-sum rounding."""
+def test_ensemble_sbm_matches_oracle_and_single_handles():
+    """On an SBM the ensemble's right-hand sides agree with the oracle and with single-trajectory
+    mixed-precision handles to FP32-sum rounding."""
     w = G.workload_sbm_small(n=6000, n_comm=6, min_size=128, seed=9)
     g = w.graph
     omega, K, theta = _inputs(g, 16, 3)
@@ -104,7 +105,32 @@ def test_ensemble_sbm_matches_single_handles():
             k.rhs(t1, o1)
             k.sync()
             f1 = o1.cpu().numpy()
-        assert np.all(np.abs(f[b] - f1) <= 2e-4 * (1 + deg) * np.maximum(1.0, np.abs(f1))), b
+        ref = oracle.rhs_csr(g.row_ptr, g.col, omega[b], theta[b], K[b])
+        check_rhs(f[b], ref, deg, K[b], g.n, 1, f"sbm-6000 ensemble trajectory {b} vs oracle")
+        check_rhs(f1, ref, deg, K[b], g.n, 1, f"sbm-6000 single handle {b} vs oracle")
+        check_rhs(f[b], f1, deg, K[b], g.n, 1, f"sbm-6000 ensemble trajectory {b} vs single handle",
+                  e_bound=2e-6)
+
+
+def test_ensemble_64x65536_sampled_rows_vs_oracle():
+    """The benchmarked ensemble shape: 64 trajectories on the 65536-node SBM (64 communities, p_in 0.95,
+    p_out 0.001), every dense community on the tensor cores; sampled rows of four trajectories (one per
+    group of 16) against the oracle."""
+    w = G.workload_sbm_small()
+    g = w.graph
+    omega, K, theta = _inputs(g, 64, 6)
+    with kura.KuramotoEnsemble(g.row_ptr, g.col, g.label, g.n_comm, omega, K) as e:
+        assert e.stats()["tc_tiles"] > 0
+        th = torch.tensor(theta, device="cuda:0")
+        out = torch.empty_like(th)
+        e.rhs(th, out)
+        e.sync()
+        f = out.cpu().numpy()
+    rows = np.unique(G.permutation(15, g.n)[:1500].astype(np.int64))
+    deg = np.diff(g.row_ptr)[rows]
+    for b in (0, 21, 42, 63):
+        ref = oracle.rhs_csr(g.row_ptr, g.col, omega[b], theta[b], K[b], rows=rows)
+        check_rhs(f[b][rows], ref, deg, K[b], g.n, 1, f"64x65536 ensemble trajectory {b}")
 
 
 def test_ensemble_rejects_bad_sizes(ragged):
