@@ -181,6 +181,83 @@ def cpu_baseline_oracle(w, seconds: float = 12.0, keep_values: bool = False):
     return out
 
 
+_CPB = None
+
+
+def cpu_block_lib():
+    """The OpenMP CPU block method (baseline/cpu_block.c), compiled with gcc on first use."""
+    global _CPB
+    if _CPB is not None:
+        return _CPB
+    import ctypes as C
+    src = os.path.join(ROOT, "baseline", "cpu_block.c")
+    lib = os.path.join(ROOT, "baseline", "_cpu_block.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-fopenmp", "-o", tmp, src, "-lm"])
+        os.replace(tmp, lib)
+    L = C.CDLL(lib)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.cpb_create.restype = P
+    L.cpb_create.argtypes = [I64, P, P, P, I32, P, D, D]
+    L.cpb_rk4.argtypes = [P, P, D, I64]
+    L.cpb_rhs.argtypes = [P, P, P]
+    L.cpb_threads.restype = C.c_int
+    L.cpb_destroy.argtypes = [P]
+    _CPB = L
+    return L
+
+
+class CpuBlock:
+    """Handle of the OpenMP CPU block method on one graph (host arrays, user order)."""
+
+    def __init__(self, g, omega, K, tau=0.5):
+        L = cpu_block_lib()
+        self._keep = [np.ascontiguousarray(g.row_ptr, dtype=np.int64), np.ascontiguousarray(g.col, dtype=np.int32),
+                      np.ascontiguousarray(g.label, dtype=np.int32), np.ascontiguousarray(omega, dtype=np.float64)]
+        rp, cl, lb, om = self._keep
+        self.n = g.n
+        self.h = L.cpb_create(g.n, rp.ctypes.data, cl.ctypes.data, lb.ctypes.data, int(g.n_comm), om.ctypes.data,
+                              float(K), float(tau))
+        if not self.h:
+            raise RuntimeError("cpb_create failed")
+
+    def rhs(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        f = np.empty(self.n)
+        cpu_block_lib().cpb_rhs(self.h, th.ctypes.data, f.ctypes.data)
+        return f
+
+    def rk4(self, theta, h, steps):
+        cpu_block_lib().cpb_rk4(self.h, theta.ctypes.data, float(h), int(steps))
+
+    def close(self):
+        if self.h:
+            cpu_block_lib().cpb_destroy(self.h)
+            self.h = None
+
+
+def cpu_block_baseline(w, seconds: float = 10.0, steps_full: int = 0):
+    """The block method on all host cores (OpenMP), timed over whole RK4 steps of the workload (about
+    `seconds` of work, at least one step; steps_full > 0 times that many steps instead)."""
+    t0 = time.perf_counter()
+    cb = CpuBlock(w.graph, w.omega, w.K)
+    t_setup = time.perf_counter() - t0
+    th = np.array(w.theta0, dtype=np.float64)
+    t0 = time.perf_counter()
+    cb.rk4(th, w.h, 1)
+    t1 = time.perf_counter() - t0
+    steps = steps_full if steps_full > 0 else max(1, min(int(seconds / max(t1, 1e-9)), 1000))
+    t0 = time.perf_counter()
+    cb.rk4(th, w.h, steps)
+    el = time.perf_counter() - t0
+    cb.close()
+    return {"value": w.graph.n * steps / el, "unit": UNIT, "cores": cpu_block_lib().cpb_threads(),
+            "kind": "cpu block method (OpenMP, FP64)", "nproc": os.cpu_count(), "cpu_model": _cpu_model(),
+            "steps": steps, "seconds": el, "setup_s": t_setup,
+            "sample": f"{steps} whole RK4 steps of the {w.graph.n}-node workload, all host cores"}
+
+
 def _cpu_model() -> str:
     """Host CPU model name (lscpu, else /proc/cpuinfo)."""
     try:
@@ -241,9 +318,10 @@ def bench_adjoint(dev):
             "g_K": gK, "g_theta0_norm": float(torch.linalg.norm(gth)), "g_omega_norm": float(torch.linalg.norm(gom))}
 
 
-def bench_batch(dev, steps: int = 1000):
+def bench_batch(dev, steps: int = 1000, tc_steps: int = 200):
     """2048 independent trajectories of uneven size in one persistent launch (half complete graphs, half SBMs),
-    1000 RK4 steps, h = 0.01, mixed precision."""
+    h = 0.01, mixed precision: the dense-block zeros as index lists (1000 steps), and as 0/1 masks multiplied
+    on the tensor cores with split BF16 (sin, cos) (tc_steps steps)."""
     import torch
     from paper_2102_07167_gb300 import gen as G
     from paper_2102_07167_gb300 import kura
@@ -251,28 +329,134 @@ def bench_batch(dev, steps: int = 1000):
     ens = G.workload_batch()
     t_gen = time.perf_counter() - t0
     theta0 = np.concatenate([th for (_, _, _, th, _) in ens])
+
+    def run(tcm, nsteps):
+        t0 = time.perf_counter()
+        with kura.KuramotoBatch(G.batch_graphs(ens), tensor_cores=tcm) as b:
+            t_create = time.perf_counter() - t0
+            st, info = b.stats(), b.info()
+            th = torch.tensor(theta0, device=dev)
+            b.rk4_steps(th, 0.01, 3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.rk4_steps(th, 0.01, nsteps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        return {"steps": nsteps, "ms": ms, "ms_per_step": ms / nsteps,
+                "value": info["n_total"] * nsteps / (ms / 1e3), "unit": UNIT, "create_s": t_create,
+                "listed_corrections": st["missing_entries"] + st["sparse_entries"],
+                "tc_trajectories": info["tc_traj"], "tc_tiles": info["tc_tiles"], "tc_mask_bits": info["tc_mask_bits"],
+                "gpu_launches": 3}
+    lists = run(0, steps)
+    tc = run(2, tc_steps)
+    return {"workload": "2048 trajectories, n log-uniform in [256, 16384], half complete graphs, half SBMs "
+                        "(8-32 communities, p_in 0.9, p_out 0.005), K ~ U[0.5, 5], h = 0.01",
+            "n_total": int(theta0.size), "value": lists["value"], "unit": UNIT, "generate_s": t_gen,
+            "precision": "mixed (FP32 sin/cos and corrections, exact fixed-point block sums, FP64 epilogue/state)",
+            "cuda_cores_index_lists": lists,
+            "tensor_cores_split_bf16": dict(tc, note="dense-block zeros as a BF16 0/1 mask x split BF16 (sin_hi, "
+                                            "sin_lo, cos_hi, cos_lo) per trajectory: M = 128, N = 16 (4 useful), "
+                                            "tcgen05.mma.kind::f16, FP32 accumulation; a matrix-vector product "
+                                            "per trajectory, so the tensor cores are 1/4 used"),
+            "tc_over_lists_time": tc["ms_per_step"] / lists["ms_per_step"]}
+
+
+def bench_complete_512(dev):
+    """Classical all-to-all model, N = 512, K = 2, h = 0.01, 200 steps, FP64 (the latency-bound case): the
+    CUDA-graph step loop (8 kernels per step) against the measured graph launch floor, the persistent
+    single-CTA form (a batch of one trajectory: one launch runs all 200 steps), the GPU direct sum, and the
+    CPU baselines on the whole trajectory."""
+    import torch
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_complete(512)
+    g = w.graph
+
+    def timed(fn, reps=5):
+        out = []
+        for _ in range(reps):
+            th = torch.tensor(w.theta0, device=dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(th)
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out)), th.cpu().numpy()
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K, precision=kura.PREC_FP64) as k:
+        k.rk4_steps(torch.tensor(w.theta0, device=dev), w.h, w.n_steps)
+        ms_graph, th_graph = timed(lambda th: k.rk4_steps(th, w.h, w.n_steps))
+        ms_direct, _ = timed(lambda th: k.direct_rk4_steps(th, w.h, w.n_steps, kura.PREC_FP64), reps=3)
+    with kura.KuramotoBatch([(None, None, None, 1, w.omega, w.K)], precision=kura.PREC_FP64) as b:
+        b.rk4_steps(torch.tensor(w.theta0, device=dev), w.h, w.n_steps)
+        ms_pers, th_pers = timed(lambda th: b.rk4_steps(th, w.h, w.n_steps))
+    floor_us = kura.kura_measure_graph_launch_floor(8, 2000)
+    st = w.n_steps
+    res = {"workload": "complete graph N=512, K = 2, h = 0.01, 200 RK4 steps, FP64",
+           "graph_step_loop": {"us_per_step": ms_graph * 1e3 / st, "value": g.n * st / (ms_graph / 1e3),
+                               "launches_per_step": 8},
+           "launch_floor": {"us_per_kernel": floor_us, "us_per_step": 8 * floor_us,
+                            "how": "CUDA graph of 8 empty dependent kernels, replayed 2000 times"},
+           "graph_over_floor": (ms_graph * 1e3 / st) / (8 * floor_us),
+           "persistent_single_cta": {"us_per_step": ms_pers * 1e3 / st, "value": g.n * st / (ms_pers / 1e3),
+                                     "launches": 1},
+           "direct_fp64": {"us_per_step": ms_direct * 1e3 / st, "value": g.n * st / (ms_direct / 1e3)}}
+    # CPU legs: the oracle as it stands (CSR definition, one core) on the whole trajectory, and the
+    # OpenMP block method; the oracle's final phases also give the GPU paths' error
+    import oracle
     t0 = time.perf_counter()
-    with kura.KuramotoBatch(G.batch_graphs(ens)) as b:
-        t_create = time.perf_counter() - t0
-        st = b.stats()
-        th = torch.tensor(theta0, device=dev)
-        b.rk4_steps(th, 0.01, 3)
+    ref = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, st)
+    t_orc = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": g.n * st / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"whole trajectory ({st} steps) by oracle.rk4_csr in {t_orc:.1f} s"}
+    res["cpu_block_baseline"] = cpu_block_baseline(w, steps_full=st)
+    res["max_abs_err_vs_oracle"] = {"graph_step_loop": float(np.abs(th_graph - ref).max()),
+                                    "persistent_single_cta": float(np.abs(th_pers - ref).max())}
+    return res
+
+
+def bench_sbm_65536(dev, cpu_seconds: float = 8.0):
+    """SBM N = 65536 (64 communities, p_in 0.95, p_out 0.001), K = 4, FP64, h = 0.005, its 1000 steps: the
+    correction stream (~35 MB) and node data stay in L2, so the row kernel is measured against the L2 read
+    bandwidth (measured here) as well as HBM."""
+    import torch
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_sbm_small()
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_FP64) as k:
+        st = k.stats()
+        th = torch.tensor(w.theta0, device=dev)
+        k.set_timing(True)
+        k.rk4_steps(th, w.h, 8)
         torch.cuda.synchronize()
-        b.set_timing(True)
+        th = torch.tensor(w.theta0, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.rk4_steps(th, 0.01, steps)
+        k.rk4_steps(th, w.h, w.n_steps)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        kt = b.kernel_times()
-    n_total = st["n_total"]
-    return {"workload": "2048 trajectories, n log-uniform in [256, 16384], half complete graphs, half SBMs "
-                        "(8-32 communities, p_in 0.9, p_out 0.005), K ~ U[0.5, 5], h = 0.01",
-            "n_total": n_total, "stored_corrections": st["missing_entries"] + st["sparse_entries"],
-            "steps": steps, "ms": ms, "value": n_total * steps / (ms / 1e3), "unit": UNIT,
-            "kernel_ms": float(kt[0]) if kt.size else None, "generate_s": t_gen, "create_s": t_create,
-            "precision": "mixed (FP32 sin/cos and corrections, exact fixed-point block sums, FP64 epilogue/state)"}
+        kt = k.kernel_times()
+    l2 = kura.kura_measure_l2_bandwidth(48 << 20)
+    hbm, _ = _peaks()
+    floor_us = kura.kura_measure_graph_launch_floor(8, 2000)
+    alg = 4 * (st["missing_entries"] + st["sparse_entries"]) + st["node_bytes_row"]
+    row_ms = float(np.mean(kt)) if kt.size else None
+    ach = alg / (row_ms * 1e-3) / 1e9 if row_ms else None
+    res = {"workload": "SBM N=65536, 64 communities, p_in 0.95, p_out 0.001, K = 4, FP64, h = 0.005, 1000 steps",
+           "value": g.n * w.n_steps / (ms / 1e3), "unit": UNIT, "us_per_step": ms * 1e3 / w.n_steps,
+           "launch_floor_us_per_step": 8 * floor_us,
+           "roofline": {"bound": "l2", "kernel": "k_row_stage", "achieved": ach, "peak": l2, "unit": "GB/s",
+                        "frac": ach / l2 if ach else None, "hbm_frac": ach / hbm if ach else None,
+                        "algorithmic_bytes_per_launch": alg, "row_kernel_ms": row_ms,
+                        "peak_source": "kura_measure_l2_bandwidth(48 MiB), measured in this run"}}
+    res["cpu_baseline"] = cpu_baseline_oracle(w, seconds=cpu_seconds)
+    res["cpu_block_baseline"] = cpu_block_baseline(w, seconds=cpu_seconds)
+    return res
 
 
 def bench_ensemble(dev, n_traj: int = 64, steps: int = 200):
@@ -516,12 +700,15 @@ def run_ours(args):
         extra["adjoint"] = bench_adjoint(dev)
     if not args.quick and rank == 0 and not args.no_batch:
         extra["batch"] = bench_batch(dev)
+    if not args.quick and rank == 0 and not args.no_configs:
+        extra["configs"] = {"complete_512": bench_complete_512(dev), "sbm_65536": bench_sbm_65536(dev)}
     if not args.quick and rank == 0 and not args.no_ensemble:
         extra["ensemble_shared_graph"] = bench_ensemble(dev)
 
     cpu = cpu_baseline_oracle(w, seconds=args.cpu_seconds, keep_values=True) \
         if (rank == 0 and world == 1 and not args.quick) else None
     if cpu is not None:
+        extra["cpu_block_baseline"] = cpu_block_baseline(w, seconds=args.cpu_seconds)
         rows, ref = cpu.pop("_rows"), cpu.pop("_ref")
         # the rows the CPU-baseline leg evaluated with the oracle give the GPU's error at the same phases
         extra["rhs_error_vs_oracle"] = {
@@ -558,13 +745,22 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--only", choices=["ensemble", "batch"], default=None,
+    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--only", choices=["ensemble", "batch", "complete-512", "sbm-65536"], default=None,
                     help="run one of the extra measurements alone (for profiling) and print its JSON")
     args = ap.parse_args()
     if args.only is not None:
         import torch
-        fn = bench_ensemble if args.only == "ensemble" else bench_batch
-        print(json.dumps(fn(torch.device("cuda", 0), steps=args.steps)))
+        dev = torch.device("cuda", 0)
+        if args.only == "ensemble":
+            out = bench_ensemble(dev, steps=args.steps)
+        elif args.only == "batch":
+            out = bench_batch(dev, steps=args.steps, tc_steps=max(1, args.steps // 5))
+        elif args.only == "complete-512":
+            out = bench_complete_512(dev)
+        else:
+            out = bench_sbm_65536(dev)
+        print(json.dumps(out))
         return
     if args.impl == "reference":
         run_reference(args)

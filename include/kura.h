@@ -247,11 +247,24 @@ typedef struct {
 } kura_graph_desc;
 
 /* Creates a batch handle: n_traj independent trajectories (uneven sizes,
- * 1 <= n <= 16384 and n_comm <= 1024 each), integrated together by one
- * persistent launch per kura_rk4_steps call.  Each trajectory is planned as
- * in kura_create (eq:KuramotoGraphApproach with opts->tau, uniform scaling
- * K/n); only KURA_PREC_MIXED is supported.  On a batch handle kura_rk4_steps
- * takes the phases of all trajectories concatenated in trajectory order
+ * n_comm <= 1024 each), integrated together by one persistent launch per
+ * kura_rk4_steps call: one CTA integrates a whole trajectory, all its steps,
+ * with the trajectory's (sin, cos) table in shared memory; trajectories are
+ * handed out longest first.  Each trajectory is planned as in kura_create
+ * (eq:KuramotoGraphApproach with opts->tau, uniform scaling K/n).
+ *   opts->precision  KURA_PREC_MIXED (1 <= n <= 16384 per trajectory) or
+ *                    KURA_PREC_FP64 (1 <= n <= 8192: FP64 sin/cos, every sum
+ *                    exact in 64-bit fixed point, FP64 epilogue and state)
+ *   opts->tensor_cores (mixed only) the dense-block zeros of a community as a
+ *                    0/1 mask multiplied on the tensor cores
+ *                    (tcgen05.mma.kind::f16: BF16 mask, split BF16 hi + lo
+ *                    (sin, cos), FP32 accumulation in tensor memory; the
+ *                    dense columns must span <= 4096 columns): 0 never, 1
+ *                    when the mask bits take fewer bytes than 4-byte index
+ *                    lists would, 2 whenever possible.  With one graph per
+ *                    trajectory the product has 4 useful columns (N = 16).
+ * On a batch handle kura_rk4_steps and kura_rhs take the phases (and the
+ * right-hand side) of all trajectories concatenated in trajectory order
  * (user order within each); the other per-graph calls return KURA_ESTATE.
  * Host arrays are copied.  Errors as for kura_create. */
 kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts,
@@ -259,6 +272,19 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
 
 /* Sizes of a batch: total oscillators and stored corrections (nullable outputs). */
 kura_status kura_batch_stats(kura_t h, int64_t* n_total, int64_t* missing, int64_t* present);
+
+typedef struct {
+    int32_t n_traj, precision;
+    int64_t n_total;             /* oscillators of all trajectories */
+    int64_t missing_listed;      /* dense-block zeros given as index lists */
+    int64_t present;             /* sparse-block non-zeros (index lists) */
+    int32_t tc_traj;             /* trajectories with tensor-core tiles */
+    int32_t pad;
+    int64_t tc_tiles, tc_mask_bits;   /* tensor-core tiles (<= 128 rows each) and their mask bits */
+} kura_batch_info_t;
+
+/* Layout of a batch handle (host struct). */
+kura_status kura_batch_info(kura_t h, kura_batch_info_t* out);
 
 /* Replaces omega (nullable; n entries, user order, device or host) and/or
  * K (nullable). */
@@ -338,6 +364,20 @@ kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_t
  * synchronous.  KURA_EINVAL for sizes out of range. */
 kura_status kura_measure_gather_rate(int64_t table_entries, int64_t gathers, int32_t entry_bytes, void* stream,
                                      double* gathers_per_s);
+
+/* Measurement for rooflines (not part of the method): the read bandwidth, in
+ * GB/s, of 16-byte loads streaming over a device buffer of `bytes` bytes
+ * (1 MiB .. 1 GiB) 16 times; below the L2 size (126 MiB usable here) the
+ * buffer stays in L2, so this is the L2 read bandwidth the L2-resident
+ * workloads are bounded by.  One warm-up run, median of three (CUDA events on
+ * stream).  Allocates and frees its own device memory; synchronous. */
+kura_status kura_measure_l2_bandwidth(int64_t bytes, void* stream, double* gb_per_s);
+
+/* Measurement (not part of the method): the time per kernel node, in
+ * microseconds, of replaying a CUDA graph of `kernels` (1..4096) empty
+ * dependent kernel launches `replays` (1..100000) times on stream: the launch
+ * floor of a step loop captured as a graph.  Synchronous. */
+kura_status kura_measure_graph_launch_floor(int32_t kernels, int32_t replays, void* stream, double* us_per_kernel);
 
 /* Switches the handle to another stream (cached graphs stay valid). */
 kura_status kura_set_stream(kura_t h, void* stream);

@@ -87,7 +87,10 @@ int ceil_log2(int64_t v)
 struct BatchData {
     int32_t n_traj = 0;
     int64_t n_total = 0, entries = 0, missing = 0, present = 0;
-    DevMem traj, order, comm_off, dptr, dcol, node_comm, row_off, row_nm, entries_d, queue, stash;
+    int64_t tc_tiles = 0, tc_mask_bits = 0;   // tensor-core tiles and their mask bits (0: CUDA cores only)
+    int32_t tc_traj = 0;                       // trajectories with tensor-core tiles
+    DevMem traj, order, comm_off, dptr, dcol, node_comm, row_off, row_nm, entries_d, queue, stash, tc_tiles_d,
+        tc_bits_d;
 };
 
 // Device data of an ensemble handle (kura_ensemble_create): trajectories in
@@ -887,11 +890,19 @@ kura_status kura_sync(kura_t h)
 static kura_status ens_rhs(kura_t h, const double* theta, double* dtheta);
 static kura_status ens_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps);
 
+static kura_status batch_launch(kura_t h, const double* theta, double* out, double step, int64_t n_steps,
+                                bool rhs_only);
+
 kura_status kura_rhs(kura_t h, const double* theta, double* dtheta)
 {
     if (h && h->ens) {
         cudaSetDevice(h->device);
         return ens_rhs(h, theta, dtheta);
+    }
+    if (h && h->batch) {
+        cudaSetDevice(h->device);
+        if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
+        return batch_launch(h, theta, dtheta, 0.0, 1, true);
     }
     if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !dtheta || theta == dtheta) return h->fail(KURA_EINVAL, "theta/dtheta NULL or aliased");
@@ -1663,16 +1674,22 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
 }
 
 // ---------------------------------------------------------------- batched ensembles
-static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
+static size_t batch_smem_bytes(bool tc) { return size_t(BATCH_SMEM_BASE) + (tc ? size_t(BATCH_TC_SMEM) : 0); }
+
+// One persistent launch over every trajectory: n_steps RK4 steps on theta in
+// place, or (rhs_only) one right-hand side of theta written to out.
+static kura_status batch_launch(kura_t h, const double* theta, double* out, double step, int64_t n_steps,
+                                bool rhs_only)
 {
     BatchData& B = *h->batch;
     const double* th_dev;
     bool host;
     if (kura_status st = stage_in(h, theta, &th_dev, &host)) return st;
-    double* io = host ? h->user.as<double>() : theta;
+    const bool host_out = rhs_only ? !is_device_ptr(out) : host;
+    double* io = host_out ? h->user.as<double>() : out;
     cudaStream_t s = h->stream;
     const unsigned nb = blocks_for(h->n, 256);
-    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), io, h->y.as<double>());
+    k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), th_dev, h->y.as<double>());
     KCHECK(h, cudaMemsetAsync(B.queue.p, 0, 16, s), "reset the trajectory queue");
     BatchDev bd{};
     bd.traj = B.traj.as<BatchTraj>();
@@ -1685,18 +1702,19 @@ static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t
     bd.row_off = B.row_off.as<int32_t>();
     bd.row_nm = B.row_nm.as<int32_t>();
     bd.entries = B.entries_d.as<uint16_t>();
+    bd.tc_tiles = B.tc_tiles_d.as<BatchTcTile>();
+    bd.tc_bits = B.tc_bits_d.as<uint32_t>();
     bd.omega = h->omega.as<double>();
     bd.y = h->y.as<double>();
     bd.Y = h->Y.as<double>();
     bd.krk = h->krk.as<double>();
-    bd.stash = B.stash.as<float2>();
+    bd.stash = B.stash.p;
     bd.queue = B.queue.as<unsigned int>();
     bd.err = h->err_flags.as<int>();
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-    const size_t smem = size_t(BATCH_MAX_N) * 8 + size_t(2 * BATCH_MAX_COMM) * 8 + size_t(BATCH_MAX_COMM) * 16;
-    static GraphEntry batch_events;   // unused placeholder keeps kernel_times semantics simple
-    (void)batch_events;
+    const bool tc = B.tc_tiles > 0;
+    const size_t smem = batch_smem_bytes(tc);
     if (n_steps > 0) {
         if (h->timing) {
             if (!h->last_graph || h->last_graph->events.size() != 2) {
@@ -1709,16 +1727,29 @@ static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t
             }
             cudaEventRecord(h->last_graph->events[0], s);
         }
-        k_batch_rk4<<<unsigned(std::min(nsm, B.n_traj)), BATCH_THREADS, smem, s>>>(bd, step, n_steps);
+        const unsigned grid = unsigned(std::min(std::max(nsm, 1), B.n_traj));
+        const int ro = rhs_only ? 1 : 0;
+        if (h->opts.precision == KURA_PREC_FP64)
+            k_batch_rk4<MODE_FP64, false><<<grid, BATCH_THREADS, smem, s>>>(bd, step, n_steps, ro);
+        else if (tc)
+            k_batch_rk4<MODE_MIXED, true><<<grid, BATCH_THREADS, smem, s>>>(bd, step, n_steps, ro);
+        else
+            k_batch_rk4<MODE_MIXED, false><<<grid, BATCH_THREADS, smem, s>>>(bd, step, n_steps, ro);
         if (h->timing) cudaEventRecord(h->last_graph->events[1], s);
     }
-    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->y.as<double>(), io);
+    k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), rhs_only ? h->krk.as<double>() : h->y.as<double>(),
+                                      io);
     KCHECK(h, cudaGetLastError(), "launching the batched integrator");
-    if (host) {
-        KCHECK(h, cudaMemcpyAsync(theta, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
+    if (host_out) {
+        KCHECK(h, cudaMemcpyAsync(out, io, size_t(h->n) * 8, cudaMemcpyDeviceToHost, s), "copy out");
         return read_flags(h);
     }
     return KURA_OK;
+}
+
+static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps)
+{
+    return batch_launch(h, theta, theta, step, n_steps, false);
 }
 
 kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, void* stream,
@@ -1731,8 +1762,15 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     kura_opts o;
     kura_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != KURA_PREC_MIXED) { g_create_error = "batches run in KURA_PREC_MIXED"; return KURA_EINVAL; }
+    if (o.precision != KURA_PREC_MIXED && o.precision != KURA_PREC_FP64) {
+        g_create_error = "unknown precision";
+        return KURA_EINVAL;
+    }
     if (o.scaling != KURA_SCALING_UNIFORM) { g_create_error = "batches use uniform scaling"; return KURA_EINVAL; }
+    const bool fp64 = o.precision == KURA_PREC_FP64;
+    const int64_t max_n = fp64 ? BATCH_MAX_N_FP64 : BATCH_MAX_N;
+    // tensor-core masks for the dense-block zeros: mixed precision only
+    const int32_t tc_mode = fp64 ? 0 : o.tensor_cores;
     std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
     if (!h) return KURA_ENOMEM;
     h->batch.reset(new BatchData());
@@ -1741,14 +1779,16 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     std::vector<BatchTraj> traj(static_cast<size_t>(n_traj));
     std::vector<int32_t> comm_off, dptr, dcol, row_off, row_nm, perm_g;
     std::vector<uint16_t> node_comm, entries;
+    std::vector<BatchTcTile> tc_tiles;
+    std::vector<uint32_t> tc_bits;
     std::vector<double> om;
     std::vector<double> cost(static_cast<size_t>(n_traj));
     int64_t node_off = 0;
     for (int32_t t = 0; t < n_traj; t++) {
         const kura_graph_desc& gd = graphs[t];
-        if (gd.n < 1 || gd.n > BATCH_MAX_N || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega ||
+        if (gd.n < 1 || gd.n > max_n || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega ||
             !std::isfinite(gd.K)) {
-            g_create_error = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(BATCH_MAX_N) +
+            g_create_error = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(max_n) +
                              ", 1 <= n_comm <= " + std::to_string(BATCH_MAX_COMM) + ", omega and finite K";
             return KURA_EINVAL;
         }
@@ -1770,15 +1810,31 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             in.n_sms = current_sm_count();
             in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
             in.tau = o.tau;
-            in.tile_max_rows = TILE_MAX_ROWS;
+            in.tile_max_rows = TC_MBLOCK;     // a tensor-core tile is one 128-row M-block
             in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
             in.slot_ints = slot_ints_for(MODE_MIXED);
-            in.tensor_cores = 0;          // the batch kernel reads index lists
+            in.tensor_cores = tc_mode;
             std::string err;
             int rc = build_plan(in, p, err);
             if (rc) { g_create_error = "trajectory " + std::to_string(t) + ": " + err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
         }
         BatchTraj& tr = traj[size_t(t)];
+        tr.tc0 = int32_t(tc_tiles.size());
+        for (const Tile& tl : p.tiles) {
+            if (!(tl.flags & TILE_TC)) continue;
+            BatchTcTile bt{};
+            bt.r0 = tl.r0;
+            bt.nrows = tl.r1 - tl.r0;
+            bt.wbeg = tl.wbeg;
+            bt.nkb = tl.nsw;
+            bt.bits_off = int64_t(tc_bits.size());
+            const int64_t words = int64_t(tl.nsw) * TC_MBLOCK * 4;     // one M-block per tile
+            tc_bits.insert(tc_bits.end(), p.bitmap.begin() + tl.bm_off, p.bitmap.begin() + tl.bm_off + words);
+            tc_tiles.push_back(bt);
+            B.tc_mask_bits += int64_t(tl.nsw) * TC_MBLOCK * TC_KBLOCK;
+        }
+        tr.tc1 = int32_t(tc_tiles.size());
+        if (tr.tc1 > tr.tc0) B.tc_traj++;
         tr.node_off = node_off;
         tr.entry_off = int64_t(entries.size());
         tr.n = int32_t(gd.n);
@@ -1816,7 +1872,11 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             B.present += int64_t(pres.size());
         }
         row_off.push_back(pos);
-        cost[size_t(t)] = double(gd.n) * 24.0 + double(pos);
+        // LPT cost: per-node work, listed entries, and about 600 entries' worth per 64-column operand
+        // block of the tensor-core tiles (expansion, barriers and MMA issue)
+        double tc_cost = 0.0;
+        for (int32_t q = tr.tc0; q < tr.tc1; q++) tc_cost += 1200.0 * double(tc_tiles[size_t(q)].nkb);
+        cost[size_t(t)] = double(gd.n) * 24.0 + double(pos) + tc_cost;
         node_off += gd.n;
     }
     B.n_total = node_off;
@@ -1837,7 +1897,9 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     h->n = node_off;
     h->n_comm = 0;
     h->stream = static_cast<cudaStream_t>(stream);
-    const size_t smem = size_t(BATCH_MAX_N) * 8 + size_t(2 * BATCH_MAX_COMM) * 8 + size_t(BATCH_MAX_COMM) * 16;
+    B.tc_tiles = int64_t(tc_tiles.size());
+    const bool use_tc = B.tc_tiles > 0;
+    const size_t smem = batch_smem_bytes(use_tc);
     cudaStream_t s = h->stream;
     kura_ctx* hc = h.get();
 #define BCHECK(call, what)                                                              \
@@ -1848,8 +1910,17 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             return e_ == cudaErrorMemoryAllocation ? KURA_ENOMEM : KURA_ECUDA;          \
         }                                                                               \
     } while (0)
-    BCHECK(cudaFuncSetAttribute((const void*)k_batch_rk4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-           "shared memory size");
+    if (fp64)
+        BCHECK(cudaFuncSetAttribute((const void*)k_batch_rk4<MODE_FP64, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "shared memory size");
+    else if (use_tc)
+        BCHECK(cudaFuncSetAttribute((const void*)k_batch_rk4<MODE_MIXED, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "shared memory size");
+    else
+        BCHECK(cudaFuncSetAttribute((const void*)k_batch_rk4<MODE_MIXED, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "shared memory size");
+    BCHECK(upload(B.tc_tiles_d, tc_tiles, s), "upload tensor-core tiles");
+    BCHECK(upload(B.tc_bits_d, tc_bits, s), "upload tensor-core masks");
     BCHECK(upload(B.traj, traj, s), "upload trajectories");
     BCHECK(upload(B.order, order, s), "upload order");
     BCHECK(upload(B.comm_off, comm_off, s), "upload community offsets");
@@ -1862,7 +1933,7 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     BCHECK(upload(hc->omega, om, s), "upload omega");
     BCHECK(upload(hc->perm, perm_g, s), "upload permutation");
     BCHECK(B.queue.alloc(16), "alloc queue");
-    BCHECK(B.stash.alloc(8 * size_t(node_off)), "alloc stash");
+    BCHECK(B.stash.alloc((fp64 ? 16 : 8) * size_t(node_off)), "alloc stash");
     for (DevMem* d : {&hc->y, &hc->Y, &hc->krk, &hc->user}) BCHECK(d->alloc(8 * size_t(node_off)), "alloc state");
     BCHECK(hc->err_flags.alloc(16), "alloc error flags");
     BCHECK(cudaMemsetAsync(hc->err_flags.p, 0, 16, s), "memset error flags");
@@ -1870,6 +1941,23 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     BCHECK(cudaStreamSynchronize(s), "upload");
 #undef BCHECK
     *out = h.release();
+    return KURA_OK;
+}
+
+kura_status kura_batch_info(kura_t h, kura_batch_info_t* out)
+{
+    if (check_handle(h) || !out) return KURA_EINVAL;
+    if (!h->batch) return h->fail(KURA_ESTATE, "not a batch handle");
+    const BatchData& B = *h->batch;
+    std::memset(out, 0, sizeof *out);
+    out->n_traj = B.n_traj;
+    out->precision = h->opts.precision;
+    out->n_total = B.n_total;
+    out->missing_listed = B.missing;
+    out->present = B.present;
+    out->tc_traj = B.tc_traj;
+    out->tc_tiles = B.tc_tiles;
+    out->tc_mask_bits = B.tc_mask_bits;
     return KURA_OK;
 }
 

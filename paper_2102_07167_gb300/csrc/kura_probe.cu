@@ -102,3 +102,120 @@ extern "C" kura_status kura_measure_gather_rate(int64_t table_entries, int64_t g
     if (st == KURA_OK && cudaGetLastError() != cudaSuccess) st = KURA_ECUDA;
     return st;
 }
+
+namespace {
+
+// Grid-stride int4 reads of a buffer, `passes` times over (the buffer stays in
+// L2 when it is smaller than L2).
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_stream(const int4* __restrict__ buf, int64_t n16, int passes,
+                                                                int* sink)
+{
+    int acc = 0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int p = 0; p < passes; p++)
+        for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const int4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x12345678) sink[0] = acc;     // keeps the loads; the buffer is zero
+}
+
+__global__ void k_probe_empty() {}
+
+}  // namespace
+
+extern "C" kura_status kura_measure_l2_bandwidth(int64_t bytes, void* stream, double* gb_per_s)
+{
+    if (!gb_per_s || bytes < (int64_t(1) << 20) || bytes > (int64_t(1) << 30)) return KURA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bytes = bytes / 16 * 16;
+    void* buf = nullptr;
+    int* sink = nullptr;
+    kura_status st = KURA_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int passes = 16;
+    do {
+        if (cudaMalloc(&buf, size_t(bytes)) != cudaSuccess || cudaMalloc(&sink, 16) != cudaSuccess) {
+            st = KURA_ENOMEM;
+            break;
+        }
+        if (cudaMemsetAsync(buf, 0, size_t(bytes), s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess) {
+            st = KURA_ECUDA;
+            break;
+        }
+        const unsigned grid = unsigned(nsm * 8);
+        std::vector<float> ms;
+        for (int r = 0; r < 4; r++) {
+            cudaEventRecord(e0, s);
+            k_probe_stream<<<grid, PROBE_THREADS, 0, s>>>(static_cast<const int4*>(buf), bytes / 16, passes, sink);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = KURA_ECUDA;
+                break;
+            }
+            float v = 0.0f;
+            cudaEventElapsedTime(&v, e0, e1);
+            if (r > 0) ms.push_back(v);
+        }
+        if (st) break;
+        std::sort(ms.begin(), ms.end());
+        *gb_per_s = double(bytes) * passes / (double(ms[ms.size() / 2]) * 1e-3) / 1e9;
+    } while (false);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    cudaFree(sink);
+    if (st == KURA_OK && cudaGetLastError() != cudaSuccess) st = KURA_ECUDA;
+    return st;
+}
+
+extern "C" kura_status kura_measure_graph_launch_floor(int32_t kernels, int32_t replays, void* stream,
+                                                       double* us_per_kernel)
+{
+    if (!us_per_kernel || kernels < 1 || kernels > 4096 || replays < 1 || replays > 100000) return KURA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    kura_status st = KURA_OK;
+    do {
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            st = KURA_ECUDA;
+            break;
+        }
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = KURA_ECUDA;
+            break;
+        }
+        for (int k = 0; k < kernels; k++) k_probe_empty<<<1, 32, 0, cap>>>();
+        if (cudaStreamEndCapture(cap, &graph) != cudaSuccess ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            st = KURA_ECUDA;
+            break;
+        }
+        for (int r = 0; r < 3; r++) cudaGraphLaunch(exec, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < replays; r++) cudaGraphLaunch(exec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = KURA_ECUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *us_per_kernel = double(ms) * 1e3 / (double(replays) * kernels);
+    } while (false);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cap) cudaStreamDestroy(cap);
+    if (st == KURA_OK && cudaGetLastError() != cudaSuccess) st = KURA_ECUDA;
+    return st;
+}

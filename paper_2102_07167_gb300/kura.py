@@ -69,6 +69,12 @@ class KuraTuneResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class KuraBatchInfo(C.Structure):
+    _fields_ = [("n_traj", C.c_int32), ("precision", C.c_int32), ("n_total", C.c_int64),
+                ("missing_listed", C.c_int64), ("present", C.c_int64), ("tc_traj", C.c_int32),
+                ("pad", C.c_int32), ("tc_tiles", C.c_int64), ("tc_mask_bits", C.c_int64)]
+
+
 class KuraGraphDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("label", C.c_void_p),
                 ("n_comm", C.c_int32), ("omega", C.c_void_p), ("K", C.c_double)]
@@ -124,6 +130,9 @@ def load() -> C.CDLL:
             "kura_plan_build": (S, [I64, P, P, P, I32, C.POINTER(KuraOpts), C.POINTER(P)]),
             "kura_batch_create": (S, [I32, C.POINTER(KuraGraphDesc), C.POINTER(KuraOpts), P, C.POINTER(P)]),
             "kura_batch_stats": (S, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+            "kura_batch_info": (S, [P, C.POINTER(KuraBatchInfo)]),
+            "kura_measure_l2_bandwidth": (S, [I64, P, C.POINTER(D)]),
+            "kura_measure_graph_launch_floor": (S, [I32, I32, P, C.POINTER(D)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
             "kura_plan_perm": (S, [P, P, P]),
             "kura_plan_row": (S, [P, I64, P, C.POINTER(I64), P, C.POINTER(I64), I64]),
@@ -240,6 +249,12 @@ def kura_batch_stats(h):
     return {"n_total": a.value, "missing_entries": b.value, "sparse_entries": c.value}
 
 
+def kura_batch_info(h):
+    info = KuraBatchInfo()
+    _check(load().kura_batch_info(h, C.byref(info)), h)
+    return {k: getattr(info, k) for k, _ in KuraBatchInfo._fields_ if k != "pad"}
+
+
 def kura_classify_blocks(h, tau: float = -1.0) -> dict:
     st = KuraBlockStats()
     _check(load().kura_classify_blocks(h, float(tau), C.byref(st)), h)
@@ -340,6 +355,20 @@ def kura_measure_gather_rate(table_entries=1 << 20, gathers=1 << 28, entry_bytes
     r = C.c_double()
     _check(load().kura_measure_gather_rate(int(table_entries), int(gathers), int(entry_bytes), stream or None,
                                            C.byref(r)), None)
+    return r.value
+
+
+def kura_measure_l2_bandwidth(nbytes=48 << 20, stream=None) -> float:
+    """Read bandwidth (GB/s) of 16-byte loads streaming over an L2-resident buffer of nbytes."""
+    r = C.c_double()
+    _check(load().kura_measure_l2_bandwidth(int(nbytes), stream or None, C.byref(r)), None)
+    return r.value
+
+
+def kura_measure_graph_launch_floor(kernels=8, replays=2000, stream=None) -> float:
+    """Microseconds per kernel node when replaying a CUDA graph of empty dependent kernels."""
+    r = C.c_double()
+    _check(load().kura_measure_graph_launch_floor(int(kernels), int(replays), stream or None, C.byref(r)), None)
     return r.value
 
 
@@ -651,17 +680,24 @@ class KuramotoBatch:
     """A batch handle: independent trajectories (own graph, omega, K) integrated by one persistent launch.
     Phases are passed concatenated in trajectory order; `offsets[t]:offsets[t+1]` is trajectory t."""
 
-    def __init__(self, graphs, tau=0.5, stream=None):
+    def __init__(self, graphs, tau=0.5, stream=None, precision=PREC_MIXED, tensor_cores=0):
         o = kura_default_opts()
-        o.precision, o.tau = PREC_MIXED, float(tau)
+        o.precision, o.tau, o.tensor_cores = int(precision), float(tau), int(tensor_cores)
         self.h, self.offsets = kura_batch_create(graphs, o, stream)
         self.n = int(self.offsets[-1])
 
     def rk4_steps(self, theta, step, n_steps):
         kura_rk4_steps(self.h, theta, step, n_steps, self.n)
 
+    def rhs(self, theta, out):
+        """Right-hand sides of every trajectory at theta (concatenated) into out."""
+        kura_rhs(self.h, theta, out, self.n)
+
     def stats(self):
         return kura_batch_stats(self.h)
+
+    def info(self):
+        return kura_batch_info(self.h)
 
     def set_timing(self, on=True):
         kura_set_timing(self.h, on)
