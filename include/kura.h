@@ -86,7 +86,10 @@ typedef struct {
      * tensor cores): a bitmap over the staged window when their fraction
      * exceeds this, else an index list; negative (default): index lists */
     double bitmap_zmin;
-    int32_t reserved[4];
+    /* batch handles: lanes that gather one row's listed entries, 32 (a warp
+     * per row; default when 0), 16 or 8 (2 or 4 rows per warp) */
+    int32_t row_lanes;
+    int32_t reserved[3];
 } kura_opts;
 
 typedef struct {
@@ -286,6 +289,11 @@ typedef struct {
 /* Layout of a batch handle (host struct). */
 kura_status kura_batch_info(kura_t h, kura_batch_info_t* out);
 
+/* Plan choices of trajectory t of a batch handle: tau, encoding of the
+ * dense-block zeros (as kura_opts.tensor_cores) and lanes per row (32, 16 or
+ * 8); any output may be NULL. */
+kura_status kura_batch_traj_params(kura_t h, int32_t t, double* tau, int32_t* tensor_cores, int32_t* row_lanes);
+
 /* Replaces omega (nullable; n entries, user order, device or host) and/or
  * K (nullable). */
 kura_status kura_set_param(kura_t h, const double* omega, const double* K);
@@ -342,7 +350,23 @@ typedef struct {
 } kura_tune_result;
 
 /* Autotuner of the block plan (not in the paper: its tau = 0.5 is a cost
- * argument, Sec. 1 and 3).  Every plan computes the same right-hand side up
+ * argument, Sec. 1 and 3).
+
+ * On a batch handle (kura_batch_create with keep_host_csr = 1; theta is the
+ * concatenated phases of all trajectories): the trajectories with a stored
+ * graph are grouped by size class (ceil(log2 n)); per class, heaviest first
+ * and within about budget_s seconds, one parameter at a time is moved from
+ * the handle's choice -- the encoding of the dense-block zeros (index lists
+ * or the tensor-core mask product, mixed precision only), the row tile
+ * (32, 16 or 8 lanes gather one row's listed entries) and tau (0.35, 0.5,
+ * 0.65) -- each candidate timed over 3 RK4 steps of a sub-batch of the class
+ * (at most one trajectory per SM).  The fastest choice is kept for the class
+ * and the batch is rebuilt.  out->rhs_ms and out->initial_rhs_ms are then
+ * milliseconds per RK4 step of the whole batch (after and before), tau and
+ * tensor_cores the choice of the heaviest class and tile_work its lanes per
+ * row; kura_batch_traj_params gives every trajectory's choice.
+ *
+ * On a single handle:  Every plan computes the same right-hand side up
  * to rounding; only speed differs.  Times kura_rhs at theta (host or device,
  * user order, n values) for candidate plans, one parameter at a time
  * starting from the handle's own: the encoding of dense-block zeros

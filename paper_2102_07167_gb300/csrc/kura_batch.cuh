@@ -64,7 +64,7 @@ struct BatchTraj {
     double scale;         // K / n
     int32_t q_bits;
     int32_t tc0, tc1;     // its tensor-core tiles [tc0, tc1) in BatchDev::tc_tiles
-    int32_t pad;
+    int32_t row_lanes;    // lanes that gather one row's listed entries (32, 16 or 8; 32 / row_lanes rows per warp)
 };
 
 // A tile of at most 128 rows of one community whose dense-block zeros are a
@@ -256,34 +256,37 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                 }
                 __syncthreads();
                 for (int i = tid; i < 2 * nc; i += BATCH_THREADS) S[i] = 0ull;
-                // ---- rows: a warp per row gathers its listed corrections from the shared table
+                // ---- rows: a group of L lanes per row (L = 32, 16 or 8, the trajectory's row tile:
+                // 32 / L rows per warp) gathers the row's listed corrections from the shared table
                 const int32_t* roff = b.row_off + o + cur;            // n + 1 offsets per trajectory
                 const uint16_t* e = b.entries + tr.entry_off;
-                for (int r = warp; r < n; r += NW) {
-                    const int beg = __ldg(roff + r), end = __ldg(roff + r + 1), nm = __ldg(b.row_nm + o + r);
+                const int L = tr.row_lanes, rpw = 32 / L, sub = lane / L, sl = lane - sub * L;
+                for (int r0 = warp * rpw; r0 < n; r0 += NW * rpw) {
+                    const int r = r0 + sub;
+                    int beg = 0, end = 0, nm = 0;
+                    if (r < n) { beg = __ldg(roff + r); end = __ldg(roff + r + 1); nm = __ldg(b.row_nm + o + r); }
                     A as = 0, ac = 0;
-                    for (int k0 = beg; k0 < end; k0 += 128) {      // up to 128 index loads in flight per row
+                    for (int k0 = beg; k0 < end; k0 += 4 * L) {    // up to 4 index loads in flight per lane
                         int idx[4];
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
-                            const int k = k0 + 32 * q + lane;
+                            const int k = k0 + L * q + sl;
                             idx[q] = (k < end) ? int(__ldg(e + k)) : -1;
                         }
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
                             if (idx[q] >= 0) {
                                 const E v = tab[idx[q]];
-                                if (k0 + 32 * q + lane - beg < nm) { as -= v.x; ac -= v.y; }
-                                else                               { as += v.x; ac += v.y; }
+                                if (k0 + L * q + sl - beg < nm) { as -= v.x; ac -= v.y; }
+                                else                            { as += v.x; ac += v.y; }
                             }
                         }
                     }
-#pragma unroll
-                    for (int off = 16; off; off >>= 1) {
+                    for (int off = L >> 1; off; off >>= 1) {       // within the lane group
                         as += __shfl_xor_sync(0xffffffffu, as, off);
                         ac += __shfl_xor_sync(0xffffffffu, ac, off);
                     }
-                    if (lane == 0) {
+                    if (sl == 0 && r < n) {
                         E v;
                         v.x = as;
                         v.y = ac;
@@ -298,7 +301,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                         const BatchTcTile tt = b.tc_tiles[tt_i];
                         const uint32_t* bits = b.tc_bits + tt.bits_off;
                         const int nT = 2 * tt.nkb;                 // 64-column operand blocks
+                        // the 4 mask words of this thread's row for one 128-column block cover two operand
+                        // blocks; the next block's words are loaded one block ahead
+                        const int ar = tid >> 3, ac = tid & 7;
+                        const uint4* rowbits = reinterpret_cast<const uint4*>(bits) + ar;
+                        uint4 wcur = __ldg(rowbits), wnext = make_uint4(0u, 0u, 0u, 0u);
                         for (int q = 0; q < nT; q++) {
+                            if ((q & 1) == 0) {
+                                if (q > 0) wcur = wnext;
+                                if (q + 2 < nT) wnext = __ldg(rowbits + size_t((q >> 1) + 1) * TC_MBLOCK);
+                            }
                             const int sst = q & 1;
                             if (q >= 2) {
                                 // the MMAs that read this stage (operand block q - 2) have to be complete
@@ -306,12 +318,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                                     atomicOr(&tc_fail, 1);
                                 if (sst) ph1 ^= 1u; else ph0 ^= 1u;
                             }
-                            {   // A: thread -> (row r, 8-column chunk c) of the 128 x 64 mask tile
-                                const int r = tid >> 3, c = tid & 7;
-                                const uint32_t w =
-                                    __ldg(bits + (size_t(q >> 1) * TC_MBLOCK + r) * 4 + (q & 1) * 2 + (c >> 2));
-                                *reinterpret_cast<uint4*>(A_ + sst * BATCH_TC_ABYTES + r * 128 + ((c ^ (r & 7)) << 4)) =
-                                    batch_bf16_mask8((w >> ((c & 3) * 8)) & 0xFFu);
+                            {   // A: thread -> (row ar, 8-column chunk ac) of the 128 x 64 mask tile
+                                const int wi = (q & 1) * 2 + (ac >> 2);
+                                const uint32_t w = wi == 0 ? wcur.x : wi == 1 ? wcur.y : wi == 2 ? wcur.z : wcur.w;
+                                *reinterpret_cast<uint4*>(A_ + sst * BATCH_TC_ABYTES + ar * 128 +
+                                                          ((ac ^ (ar & 7)) << 4)) =
+                                    batch_bf16_mask8((w >> ((ac & 3) * 8)) & 0xFFu);
                             }
                             if (tid < BATCH_TC_KSUB) {   // B rows 0-3: split BF16 (sin, cos) of the 64 columns
                                 const int col = tt.wbeg + q * BATCH_TC_KSUB + tid;

@@ -83,6 +83,28 @@ int ceil_log2(int64_t v)
 
 }  // namespace
 
+// Plan choices of one batch trajectory (set by kura_batch_create, moved by kura_autotune).
+struct BatchChoice {
+    double tau = 0.5;      // dense iff zero fraction < tau
+    int32_t tc = 0;        // tensor-core masks: as kura_opts.tensor_cores
+    int32_t lanes = 32;    // lanes that gather one row's listed entries: 32, 16 or 8
+};
+
+// Host copy of one batch trajectory's graph.
+struct HostGraph {
+    kura_graph_desc desc{};
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col, label;
+    std::vector<double> omega;
+    void rebind()
+    {
+        desc.omega = omega.data();
+        desc.row_ptr = row_ptr.empty() ? nullptr : row_ptr.data();
+        desc.col = row_ptr.empty() ? nullptr : col.data();
+        desc.label = row_ptr.empty() ? nullptr : label.data();
+    }
+};
+
 // Device data of a batch handle (kura_batch_create).
 struct BatchData {
     int32_t n_traj = 0;
@@ -91,6 +113,8 @@ struct BatchData {
     int32_t tc_traj = 0;                       // trajectories with tensor-core tiles
     DevMem traj, order, comm_off, dptr, dcol, node_comm, row_off, row_nm, entries_d, queue, stash, tc_tiles_d,
         tc_bits_d;
+    std::vector<BatchChoice> choice;     // plan choices of every trajectory
+    std::vector<HostGraph> host;         // host copies of the graphs (keep_host_csr), for kura_autotune
 };
 
 // Device data of an ensemble handle (kura_ensemble_create): trajectories in
@@ -811,8 +835,15 @@ kura_status time_rhs(kura_t h, const double* theta, double* out, int reps, doubl
 
 }  // namespace
 
+static kura_status batch_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out);
+
 kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out)
 {
+    if (h && h->batch) {
+        cudaSetDevice(h->device);
+        if (!theta || !out) return h->fail(KURA_EINVAL, "theta or out is NULL");
+        return batch_autotune(h, theta, budget_s, out);
+    }
     if (kura_status st0 = check_single(h)) return st0;
     if (!theta || !out) return h->fail(KURA_EINVAL, "theta or out is NULL");
     if (h->h_col.empty() && h->nnz > 0)
@@ -1752,30 +1783,18 @@ static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t
     return batch_launch(h, theta, theta, step, n_steps, false);
 }
 
-kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, void* stream,
-                              kura_t* out)
+// (Re)builds the device data of batch handle h for the trajectories gds with
+// the per-trajectory plan choices ch (h->device, h->stream and h->opts set).
+static kura_status batch_build(kura_ctx* h, const std::vector<kura_graph_desc>& gds,
+                               const std::vector<BatchChoice>& ch, std::string& err)
 {
-    g_create_error.clear();
-    if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
-    *out = nullptr;
-    if (n_traj <= 0 || !graphs) { g_create_error = "n_traj must be positive and graphs non-NULL"; return KURA_EINVAL; }
-    kura_opts o;
-    kura_default_opts(&o);
-    if (opts) o = *opts;
-    if (o.precision != KURA_PREC_MIXED && o.precision != KURA_PREC_FP64) {
-        g_create_error = "unknown precision";
-        return KURA_EINVAL;
-    }
-    if (o.scaling != KURA_SCALING_UNIFORM) { g_create_error = "batches use uniform scaling"; return KURA_EINVAL; }
-    const bool fp64 = o.precision == KURA_PREC_FP64;
+    const int32_t n_traj = int32_t(gds.size());
+    const bool fp64 = h->opts.precision == KURA_PREC_FP64;
     const int64_t max_n = fp64 ? BATCH_MAX_N_FP64 : BATCH_MAX_N;
-    // tensor-core masks for the dense-block zeros: mixed precision only
-    const int32_t tc_mode = fp64 ? 0 : o.tensor_cores;
-    std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
-    if (!h) return KURA_ENOMEM;
     h->batch.reset(new BatchData());
     BatchData& B = *h->batch;
     B.n_traj = n_traj;
+    B.choice = ch;
     std::vector<BatchTraj> traj(static_cast<size_t>(n_traj));
     std::vector<int32_t> comm_off, dptr, dcol, row_off, row_nm, perm_g;
     std::vector<uint16_t> node_comm, entries;
@@ -1783,19 +1802,20 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     std::vector<uint32_t> tc_bits;
     std::vector<double> om;
     std::vector<double> cost(static_cast<size_t>(n_traj));
+    const kura_graph_desc* graphs = gds.data();
     int64_t node_off = 0;
     for (int32_t t = 0; t < n_traj; t++) {
-        const kura_graph_desc& gd = graphs[t];
+        const kura_graph_desc& gd = graphs[size_t(t)];
         if (gd.n < 1 || gd.n > max_n || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega ||
             !std::isfinite(gd.K)) {
-            g_create_error = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(max_n) +
+            err = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(max_n) +
                              ", 1 <= n_comm <= " + std::to_string(BATCH_MAX_COMM) + ", omega and finite K";
             return KURA_EINVAL;
         }
         Plan p;
         const bool complete = gd.row_ptr == nullptr;    // all-to-all: one dense community, nothing stored
         if (complete) {
-            if (gd.n_comm != 1) { g_create_error = "a complete-graph trajectory has n_comm = 1"; return KURA_EINVAL; }
+            if (gd.n_comm != 1) { err = "a complete-graph trajectory has n_comm = 1"; return KURA_EINVAL; }
             p.n = gd.n;
             p.n_comm = 1;
             p.perm.resize(size_t(gd.n));
@@ -1809,14 +1829,14 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
             PlanInput in;
             in.n_sms = current_sm_count();
             in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
-            in.tau = o.tau;
+            in.tau = ch[size_t(t)].tau;
             in.tile_max_rows = TC_MBLOCK;     // a tensor-core tile is one 128-row M-block
             in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
             in.slot_ints = slot_ints_for(MODE_MIXED);
-            in.tensor_cores = tc_mode;
-            std::string err;
-            int rc = build_plan(in, p, err);
-            if (rc) { g_create_error = "trajectory " + std::to_string(t) + ": " + err; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+            in.tensor_cores = fp64 ? 0 : ch[size_t(t)].tc;
+            std::string perr;
+            int rc = build_plan(in, p, perr);
+            if (rc) { err = "trajectory " + std::to_string(t) + ": " + perr; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
         }
         BatchTraj& tr = traj[size_t(t)];
         tr.tc0 = int32_t(tc_tiles.size());
@@ -1845,6 +1865,7 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
         int k = 0;
         while ((int64_t(1) << k) < std::max<int64_t>(gd.n, 2)) k++;
         tr.q_bits = 61 - k;
+        tr.row_lanes = ch[size_t(t)].lanes;
         for (int64_t v : p.comm_off) comm_off.push_back(int32_t(v));
         const int32_t dbase = int32_t(dcol.size());
         for (int64_t v : p.dptr) dptr.push_back(int32_t(v) + dbase);
@@ -1885,28 +1906,18 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     for (int32_t t = 0; t < n_traj; t++) order[size_t(t)] = t;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[size_t(a)] > cost[size_t(b)]; });
 
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
-        return KURA_ECUDA;
-    }
-    cudaGetDevice(&h->device);
-    h->opts = o;
     h->n = node_off;
     h->n_comm = 0;
-    h->stream = static_cast<cudaStream_t>(stream);
     B.tc_tiles = int64_t(tc_tiles.size());
     const bool use_tc = B.tc_tiles > 0;
     const size_t smem = batch_smem_bytes(use_tc);
     cudaStream_t s = h->stream;
-    kura_ctx* hc = h.get();
+    kura_ctx* hc = h;
 #define BCHECK(call, what)                                                              \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) {                                                        \
-            g_create_error = std::string(what) + ": " + cudaGetErrorString(e_);         \
+            err = std::string(what) + ": " + cudaGetErrorString(e_);                    \
             return e_ == cudaErrorMemoryAllocation ? KURA_ENOMEM : KURA_ECUDA;          \
         }                                                                               \
     } while (0)
@@ -1935,12 +1946,265 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     BCHECK(B.queue.alloc(16), "alloc queue");
     BCHECK(B.stash.alloc((fp64 ? 16 : 8) * size_t(node_off)), "alloc stash");
     for (DevMem* d : {&hc->y, &hc->Y, &hc->krk, &hc->user}) BCHECK(d->alloc(8 * size_t(node_off)), "alloc state");
-    BCHECK(hc->err_flags.alloc(16), "alloc error flags");
-    BCHECK(cudaMemsetAsync(hc->err_flags.p, 0, 16, s), "memset error flags");
-    BCHECK(cudaStreamCreateWithFlags(&hc->cap, cudaStreamNonBlocking), "stream");
+    if (!hc->err_flags.p) {
+        BCHECK(hc->err_flags.alloc(16), "alloc error flags");
+        BCHECK(cudaMemsetAsync(hc->err_flags.p, 0, 16, s), "memset error flags");
+    }
+    if (!hc->cap) BCHECK(cudaStreamCreateWithFlags(&hc->cap, cudaStreamNonBlocking), "stream");
     BCHECK(cudaStreamSynchronize(s), "upload");
 #undef BCHECK
+    return KURA_OK;
+}
+
+
+kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, void* stream,
+                              kura_t* out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return KURA_EINVAL; }
+    *out = nullptr;
+    if (n_traj <= 0 || !graphs) { g_create_error = "n_traj must be positive and graphs non-NULL"; return KURA_EINVAL; }
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != KURA_PREC_MIXED && o.precision != KURA_PREC_FP64) {
+        g_create_error = "unknown precision";
+        return KURA_EINVAL;
+    }
+    if (o.scaling != KURA_SCALING_UNIFORM) { g_create_error = "batches use uniform scaling"; return KURA_EINVAL; }
+    if (!(o.tau >= 0.0 && o.tau <= 1.0)) { g_create_error = "tau must be in [0, 1]"; return KURA_EINVAL; }
+    if (o.row_lanes != 0 && o.row_lanes != 32 && o.row_lanes != 16 && o.row_lanes != 8) {
+        g_create_error = "row_lanes must be 0, 32, 16 or 8";
+        return KURA_EINVAL;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+        return KURA_ECUDA;
+    }
+    std::unique_ptr<kura_ctx> h(new (std::nothrow) kura_ctx());
+    if (!h) return KURA_ENOMEM;
+    cudaGetDevice(&h->device);
+    h->opts = o;
+    h->stream = static_cast<cudaStream_t>(stream);
+    std::vector<kura_graph_desc> gds(graphs, graphs + n_traj);
+    BatchChoice c0;
+    c0.tau = o.tau;
+    c0.tc = o.precision == KURA_PREC_FP64 ? 0 : o.tensor_cores;
+    c0.lanes = o.row_lanes ? o.row_lanes : 32;
+    std::vector<BatchChoice> ch(size_t(n_traj), c0);
+    std::string err;
+    kura_status st = batch_build(h.get(), gds, ch, err);
+    if (st) { g_create_error = err; return st; }
+    if (o.keep_host_csr) {
+        // host copies for kura_autotune, which rebuilds the batch with other plan choices
+        BatchData& B = *h->batch;
+        B.host.resize(size_t(n_traj));
+        for (int32_t t = 0; t < n_traj; t++) {
+            const kura_graph_desc& gd = graphs[t];
+            HostGraph& hg = B.host[size_t(t)];
+            hg.desc = gd;
+            hg.omega.assign(gd.omega, gd.omega + gd.n);
+            if (gd.row_ptr) {
+                hg.row_ptr.assign(gd.row_ptr, gd.row_ptr + gd.n + 1);
+                hg.col.assign(gd.col, gd.col + gd.row_ptr[gd.n]);
+                hg.label.assign(gd.label, gd.label + gd.n);
+            }
+            hg.rebind();
+        }
+    }
     *out = h.release();
+    return KURA_OK;
+}
+
+// Milliseconds per RK4 step of batch handle h started from the device phases th0 (user order): one warm-up
+// step, then the median of three timed runs of `steps` steps, each from a fresh copy of th0.
+static kura_status batch_step_ms(kura_t h, const double* th0, int64_t steps, double* ms)
+{
+    DevMem th;
+    KCHECK(h, th.alloc(size_t(h->n) * 8), "alloc tuning phases");
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KCHECK(h, cudaEventCreate(&e0), "cudaEventCreate");
+    KCHECK(h, cudaEventCreate(&e1), "cudaEventCreate");
+    std::vector<float> t;
+    kura_status st = KURA_OK;
+    for (int r = 0; r < 4 && !st; r++) {
+        if (cudaMemcpyAsync(th.p, th0, size_t(h->n) * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            st = h->fail(KURA_ECUDA, "copy tuning phases");
+            break;
+        }
+        cudaEventRecord(e0, s);
+        st = batch_launch(h, th.as<double>(), th.as<double>(), 0.01, r == 0 ? 1 : steps, false);
+        cudaEventRecord(e1, s);
+        if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = h->fail(KURA_ECUDA, "tuning run");
+        float v = 0.0f;
+        cudaEventElapsedTime(&v, e0, e1);
+        if (r > 0) t.push_back(v);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    std::sort(t.begin(), t.end());
+    *ms = double(t[1]) / double(steps);
+    return read_flags(h);
+}
+
+// The batch autotuner: trajectories with a stored graph are grouped by size class (ceil(log2 n)); per class,
+// starting from the handle's choices, one parameter at a time is moved -- the encoding of the dense-block
+// zeros (tensor-core mask or index lists; mixed precision), the row tile (lanes per row 32, 16, 8) and tau
+// (0.35, 0.5, 0.65) -- each candidate timed on a sub-batch of that class (at most one trajectory per SM, one
+// launch); the fastest choice is kept for the whole class and the handle is rebuilt with the choices.
+static kura_status batch_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out)
+{
+    BatchData& B = *h->batch;
+    if (B.host.empty()) return h->fail(KURA_ESTATE, "the autotuner rebuilds batches from host copies (keep_host_csr = 1)");
+    const auto t_start = std::chrono::steady_clock::now();
+    auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(); };
+    std::memset(out, 0, sizeof *out);
+    const int32_t n_traj = B.n_traj;
+    // user-order phases of every trajectory on the host
+    std::vector<double> th(size_t(h->n));
+    if (is_device_ptr(theta)) {
+        KCHECK(h, cudaMemcpyAsync(th.data(), theta, size_t(h->n) * 8, cudaMemcpyDeviceToHost, h->stream), "copy phases");
+        KCHECK(h, cudaStreamSynchronize(h->stream), "copy phases");
+    } else {
+        std::memcpy(th.data(), theta, size_t(h->n) * 8);
+    }
+    std::vector<int64_t> off(size_t(n_traj) + 1, 0);
+    for (int32_t t = 0; t < n_traj; t++) off[size_t(t) + 1] = off[size_t(t)] + B.host[size_t(t)].desc.n;
+    DevMem th_all;
+    KCHECK(h, th_all.alloc(size_t(h->n) * 8), "alloc phases");
+    KCHECK(h, cudaMemcpyAsync(th_all.p, th.data(), size_t(h->n) * 8, cudaMemcpyHostToDevice, h->stream), "phases");
+    double ms0 = 0.0;
+    if (kura_status st = batch_step_ms(h, th_all.as<double>(), 3, &ms0)) return st;
+    out->initial_rhs_ms = ms0;
+    int32_t cand = 1;
+    // size classes of the trajectories with a stored graph (complete graphs store nothing)
+    std::map<int, std::vector<int32_t>> classes;
+    for (int32_t t = 0; t < n_traj; t++) {
+        const kura_graph_desc& gd = B.host[size_t(t)].desc;
+        if (!gd.row_ptr) continue;
+        int k = 0;
+        while ((int64_t(1) << k) < gd.n) k++;
+        classes[k].push_back(t);
+    }
+    std::vector<BatchChoice> ch = B.choice;
+    const bool fp64 = h->opts.precision == KURA_PREC_FP64;
+    const int nsm = current_sm_count();
+    // heaviest classes first: sum of n^2 over the class
+    std::vector<std::pair<double, int>> order;
+    for (auto& kv : classes) {
+        double w = 0.0;
+        for (int32_t t : kv.second) w += double(B.host[size_t(t)].desc.n) * double(B.host[size_t(t)].desc.n);
+        order.push_back({-w, kv.first});
+    }
+    std::sort(order.begin(), order.end());
+    BatchChoice heaviest = ch.empty() ? BatchChoice() : ch[0];
+    bool first_class = true;
+    for (auto& ow : order) {
+        if (elapsed() > budget_s) break;
+        const std::vector<int32_t>& members = classes[ow.second];
+        // the sub-batch: up to one trajectory per SM, evenly spaced over the class
+        std::vector<int32_t> sub;
+        const size_t m = members.size(), take = std::min<size_t>(m, size_t(std::max(nsm, 1)));
+        for (size_t q = 0; q < take; q++) sub.push_back(members[q * m / take]);
+        std::vector<kura_graph_desc> gds;
+        std::vector<double> th_sub;
+        for (int32_t t : sub) {
+            gds.push_back(B.host[size_t(t)].desc);
+            th_sub.insert(th_sub.end(), th.begin() + off[size_t(t)], th.begin() + off[size_t(t) + 1]);
+        }
+        auto time_choice = [&](const BatchChoice& c, double* ms) -> kura_status {
+            std::unique_ptr<kura_ctx> tmp(new (std::nothrow) kura_ctx());
+            if (!tmp) return h->fail(KURA_ENOMEM, "tuning handle");
+            tmp->device = h->device;
+            tmp->opts = h->opts;
+            tmp->stream = h->stream;
+            std::string err;
+            std::vector<BatchChoice> cs(gds.size(), c);
+            if (kura_status st = batch_build(tmp.get(), gds, cs, err)) return h->fail(st, "tuning build: %s", err.c_str());
+            DevMem d;
+            KCHECK(h, d.alloc(th_sub.size() * 8), "alloc tuning phases");
+            KCHECK(h, cudaMemcpyAsync(d.p, th_sub.data(), th_sub.size() * 8, cudaMemcpyHostToDevice, h->stream), "phases");
+            kura_status st = batch_step_ms(tmp.get(), d.as<double>(), 3, ms);
+            if (st) return h->fail(st, "tuning run: %s", tmp->err.c_str());
+            cand++;
+            return KURA_OK;
+        };
+        BatchChoice best = ch[size_t(members[0])];
+        double best_ms = 0.0;
+        if (kura_status st = time_choice(best, &best_ms)) return st;
+        auto try_c = [&](const BatchChoice& c) -> kura_status {
+            if (elapsed() > budget_s) return KURA_OK;
+            double ms = 0.0;
+            if (kura_status st = time_choice(c, &ms)) return st;
+            if (ms < best_ms) { best_ms = ms; best = c; }
+            return KURA_OK;
+        };
+        if (!fp64) {
+            const BatchChoice base = best;
+            for (int32_t tc : {0, 2}) {
+                if (tc == base.tc) continue;
+                BatchChoice c = base;
+                c.tc = tc;
+                if (kura_status st = try_c(c)) return st;
+            }
+        }
+        {
+            const BatchChoice base = best;
+            for (int32_t lanes : {32, 16, 8}) {
+                if (lanes == base.lanes) continue;
+                BatchChoice c = base;
+                c.lanes = lanes;
+                if (kura_status st = try_c(c)) return st;
+            }
+        }
+        {
+            const BatchChoice base = best;
+            for (double tau : {0.35, 0.5, 0.65}) {
+                if (tau == base.tau) continue;
+                BatchChoice c = base;
+                c.tau = tau;
+                if (kura_status st = try_c(c)) return st;
+            }
+        }
+        for (int32_t t : members) ch[size_t(t)] = best;
+        if (first_class) heaviest = best;
+        first_class = false;
+    }
+    // rebuild the handle with the chosen plans (keeping the host copies)
+    std::vector<HostGraph> host = std::move(B.host);
+    std::vector<kura_graph_desc> gds;
+    for (auto& hg : host) gds.push_back(hg.desc);
+    KCHECK(h, cudaStreamSynchronize(h->stream), "synchronise before re-planning");
+    h->graphs.clear();
+    h->last_graph = nullptr;
+    std::string err;
+    if (kura_status st = batch_build(h, gds, ch, err)) return h->fail(st, "%s", err.c_str());
+    h->batch->host = std::move(host);
+    double ms1 = 0.0;
+    if (kura_status st = batch_step_ms(h, th_all.as<double>(), 3, &ms1)) return st;
+    out->rhs_ms = ms1;
+    out->tau = heaviest.tau;
+    out->tensor_cores = heaviest.tc;
+    out->tile_work = heaviest.lanes;
+    out->candidates = cand;
+    out->seconds = elapsed();
+    return KURA_OK;
+}
+
+kura_status kura_batch_traj_params(kura_t h, int32_t t, double* tau, int32_t* tensor_cores, int32_t* row_lanes)
+{
+    if (check_handle(h)) return KURA_EINVAL;
+    if (!h->batch) return h->fail(KURA_ESTATE, "not a batch handle");
+    if (t < 0 || t >= h->batch->n_traj) return h->fail(KURA_EINVAL, "trajectory index out of range");
+    const BatchChoice& c = h->batch->choice[size_t(t)];
+    if (tau) *tau = c.tau;
+    if (tensor_cores) *tensor_cores = c.tc;
+    if (row_lanes) *row_lanes = c.lanes;
     return KURA_OK;
 }
 

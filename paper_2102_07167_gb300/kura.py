@@ -43,7 +43,7 @@ class KuraError(RuntimeError):
 class KuraOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scaling", C.c_int32), ("tau", C.c_double),
                 ("keep_host_csr", C.c_int32), ("tensor_cores", C.c_int32), ("bitmap_zmin", C.c_double),
-                ("reserved", C.c_int32 * 4)]
+                ("row_lanes", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class KuraBlockStats(C.Structure):
@@ -131,6 +131,7 @@ def load() -> C.CDLL:
             "kura_batch_create": (S, [I32, C.POINTER(KuraGraphDesc), C.POINTER(KuraOpts), P, C.POINTER(P)]),
             "kura_batch_stats": (S, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
             "kura_batch_info": (S, [P, C.POINTER(KuraBatchInfo)]),
+            "kura_batch_traj_params": (S, [P, I32, C.POINTER(D), C.POINTER(I32), C.POINTER(I32)]),
             "kura_measure_l2_bandwidth": (S, [I64, P, C.POINTER(D)]),
             "kura_measure_graph_launch_floor": (S, [I32, I32, P, C.POINTER(D)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
@@ -680,9 +681,10 @@ class KuramotoBatch:
     """A batch handle: independent trajectories (own graph, omega, K) integrated by one persistent launch.
     Phases are passed concatenated in trajectory order; `offsets[t]:offsets[t+1]` is trajectory t."""
 
-    def __init__(self, graphs, tau=0.5, stream=None, precision=PREC_MIXED, tensor_cores=0):
+    def __init__(self, graphs, tau=0.5, stream=None, precision=PREC_MIXED, tensor_cores=0, row_lanes=32):
         o = kura_default_opts()
         o.precision, o.tau, o.tensor_cores = int(precision), float(tau), int(tensor_cores)
+        o.row_lanes = int(row_lanes)
         self.h, self.offsets = kura_batch_create(graphs, o, stream)
         self.n = int(self.offsets[-1])
 
@@ -698,6 +700,16 @@ class KuramotoBatch:
 
     def info(self):
         return kura_batch_info(self.h)
+
+    def traj_params(self, t):
+        """(tau, tensor_cores, row_lanes) of trajectory t."""
+        tau, tc, lanes = C.c_double(), C.c_int32(), C.c_int32()
+        _check(load().kura_batch_traj_params(self.h, int(t), C.byref(tau), C.byref(tc), C.byref(lanes)), self.h)
+        return tau.value, tc.value, lanes.value
+
+    def autotune(self, theta, budget_s=60.0):
+        """Per size class: the fastest of the dense-zero encodings, row tiles and tau (see kura_autotune)."""
+        return kura_autotune(self.h, theta, self.n, budget_s)
 
     def set_timing(self, on=True):
         kura_set_timing(self.h, on)
