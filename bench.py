@@ -746,7 +746,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
-    ap.add_argument("--only", choices=["ensemble", "batch", "complete-512", "sbm-65536"], default=None,
+    ap.add_argument("--only", choices=["ensemble", "batch", "complete-512", "sbm-65536", "adjoint"], default=None,
                     help="run one of the extra measurements alone (for profiling) and print its JSON")
     args = ap.parse_args()
     if args.only is not None:
@@ -758,6 +758,8 @@ def main():
             out = bench_batch(dev, steps=args.steps, tc_steps=max(1, args.steps // 5))
         elif args.only == "complete-512":
             out = bench_complete_512(dev)
+        elif args.only == "adjoint":
+            out = bench_adjoint(dev)
         else:
             out = bench_sbm_65536(dev)
         print(json.dumps(out))

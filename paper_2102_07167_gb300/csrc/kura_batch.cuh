@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
     TT* T = reinterpret_cast<TT*>(S + 2 * BATCH_MAX_COMM);                                         // MAX_COMM
     E* stash = reinterpret_cast<E*>(b.stash);
     __shared__ int cur;
-    __shared__ __align__(8) uint64_t mma_bar[2], d_bar;
+    __shared__ __align__(8) uint64_t mma_bar[2], d_bar;   // d_bar: the final drain after a wait gave up
     __shared__ uint32_t tmem_base;
     __shared__ int tc_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
     uint32_t sa = 0, sb = 0;
     unsigned char* A_ = nullptr;
     unsigned char* B_ = nullptr;
-    uint32_t ph0 = 0, ph1 = 0, phd = 0;     // parity of the next completion of mma_bar[0], mma_bar[1], d_bar
+    uint32_t ph0 = 0, ph1 = 0;              // thread 0: parity of the next completion of mma_bar[0], mma_bar[1]
     if constexpr (TC) {
         const uint32_t sbase = smem_u32(batch_smem);
         sa = (sbase + uint32_t(BATCH_SMEM_BASE) + 1023u) & ~1023u;
@@ -306,18 +306,17 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                         const int ar = tid >> 3, ac = tid & 7;
                         const uint4* rowbits = reinterpret_cast<const uint4*>(bits) + ar;
                         uint4 wcur = __ldg(rowbits), wnext = make_uint4(0u, 0u, 0u, 0u);
+                        // One waiter (thread 0) and one block barrier per operand block q: the CTA writes
+                        // stage q & 1 while thread 0 waits for the MMAs of block q - 1 (the last readers of
+                        // stage (q + 1) & 1, which block q + 1 overwrites); after the barrier thread 0 issues
+                        // the MMAs of block q.  The stage of block q was last read by block q - 2, whose
+                        // completion thread 0 waited for before the previous barrier.
                         for (int q = 0; q < nT; q++) {
                             if ((q & 1) == 0) {
                                 if (q > 0) wcur = wnext;
                                 if (q + 2 < nT) wnext = __ldg(rowbits + size_t((q >> 1) + 1) * TC_MBLOCK);
                             }
                             const int sst = q & 1;
-                            if (q >= 2) {
-                                // the MMAs that read this stage (operand block q - 2) have to be complete
-                                if (!tc_fail && !mbar_wait_bounded(&mma_bar[sst], sst ? ph1 : ph0, BATCH_LIMIT_NS))
-                                    atomicOr(&tc_fail, 1);
-                                if (sst) ph1 ^= 1u; else ph0 ^= 1u;
-                            }
                             {   // A: thread -> (row ar, 8-column chunk ac) of the 128 x 64 mask tile
                                 const int wi = (q & 1) * 2 + (ac >> 2);
                                 const uint32_t w = wi == 0 ? wcur.x : wi == 1 ? wcur.y : wi == 2 ? wcur.z : wcur.w;
@@ -338,6 +337,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                                 *reinterpret_cast<__nv_bfloat16*>(Bs + batch_tc_offset(3, tid)) = cl;
                             }
                             fence_proxy_async();           // the operand writes, visible to the tensor cores
+                            if (tid == 0 && q >= 1) {
+                                const int ps = (q - 1) & 1;    // stage of block q - 1
+                                if (!tc_fail && !mbar_wait_bounded(&mma_bar[ps], ps ? ph1 : ph0, BATCH_LIMIT_NS))
+                                    tc_fail = 1;
+                                if (ps) ph1 ^= 1u; else ph0 ^= 1u;
+                            }
                             __syncthreads();
                             if (tid == 0 && !tc_fail) {
                                 tc_fence_after();
@@ -350,19 +355,15 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
                                 tc_commit(&mma_bar[sst]);
                             }
                         }
-                        if (tid == 0 && !tc_fail) tc_commit(&d_bar);
-                        __syncthreads();
-                        if (!tc_fail && !mbar_wait_bounded(&d_bar, phd, BATCH_LIMIT_NS)) atomicOr(&tc_fail, 1);
-                        phd ^= 1u;
-                        // the stage commits of the last operand blocks have arrived with d_bar; consume them
-                        // so that every commit is waited on exactly once
-                        for (int q = (nT > 2 ? nT - 2 : 0); q < nT; q++) {
-                            const int sst = q & 1;
-                            if (!tc_fail) mbar_wait_bounded(&mma_bar[sst], sst ? ph1 : ph0, BATCH_LIMIT_NS);
-                            if (sst) ph1 ^= 1u; else ph0 ^= 1u;
+                        if (tid == 0) {
+                            // the last block's commit: all MMAs of the tile are complete when it arrives
+                            const int ps = (nT - 1) & 1;
+                            if (!tc_fail && !mbar_wait_bounded(&mma_bar[ps], ps ? ph1 : ph0, BATCH_LIMIT_NS))
+                                tc_fail = 1;
+                            if (ps) ph1 ^= 1u; else ph0 ^= 1u;
                         }
-                        tc_fence_after();
                         __syncthreads();
+                        tc_fence_after();
                         if (!tc_fail && warp < 4) {
                             // warp w reads tensor-memory lanes 32 w .. 32 w + 31: rows of the tile
                             uint32_t d[16];
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
         // after a wait that gave up, let the MMAs still in flight land before tensor memory is freed
         if (tid == 0 && tc_fail) {
             tc_commit(&d_bar);
-            mbar_wait_bounded(&d_bar, phd, BATCH_LIMIT_NS);
+            mbar_wait_bounded(&d_bar, 0u, BATCH_LIMIT_NS);
         }
         tc_fence_before();
         __syncthreads();

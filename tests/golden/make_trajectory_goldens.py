@@ -24,6 +24,12 @@ Cases:
   sbm2p20_10      the 2^20-node SBM itself (1024 communities), 10 steps of
                   h = 0.01, seed 0
 
+  adjoint_sbm65536_4
+                  the discrete RK4 adjoint (oracle.adjoint_rk4_csr: FP64, CSR
+                  definition) of L = 1 - r(T) on the 65536-node SBM above
+                  with h = 0.01 over 4 steps: L, dL/dK and dL/dtheta0,
+                  dL/domega at the sampled nodes, and the gradient norms
+
 Usage: python tests/golden/make_trajectory_goldens.py CASE [CASE ...]
 """
 from __future__ import annotations
@@ -74,7 +80,37 @@ def path(case: str) -> str:
     return os.path.join(HERE, f"traj_{case}_fp64.json")
 
 
+ADJOINT_CASES = {"adjoint_sbm65536_4": (0.01, 4)}
+
+
+def make_adjoint(case: str) -> None:
+    import oracle
+    from paper_2102_07167_gb300 import gen as G
+    h, steps = ADJOINT_CASES[case]
+    w = G.workload_sbm_small()
+    fp = fingerprint(w)
+    idx = sample_nodes(w.graph.n)
+    t0 = time.time()
+    L, g_om, g_K, g_th = oracle.adjoint_rk4_csr(w.graph.row_ptr, w.graph.col, w.omega, w.K, w.theta0, h, steps, 0)
+    secs = time.time() - t0
+    rec = {
+        "case": case, "workload": w.name, "K": w.K, "h": h, "n_steps": steps, "loss": "1 - r(T)",
+        "source": "oracle.adjoint_rk4_csr (discrete adjoint of classical RK4, FP64, CSR definition)",
+        "oracle_seconds": round(secs, 1), **fp,
+        "L": L, "g_K": g_K, "g_theta0_norm": float(np.linalg.norm(g_th)), "g_omega_norm": float(np.linalg.norm(g_om)),
+        "idx": [int(i) for i in idx], "g_theta0": [float(v) for v in g_th[idx]],
+        "g_omega": [float(v) for v in g_om[idx]],
+    }
+    out = os.path.join(HERE, f"{case}_fp64.json")
+    with open(out + ".tmp", "w") as f:
+        json.dump(rec, f, indent=0)
+    os.replace(out + ".tmp", out)
+    print(f"{case}: {steps} steps in {secs:.0f} s, L = {L:.9f}", flush=True)
+
+
 def make(case: str) -> None:
+    if case in ADJOINT_CASES:
+        return make_adjoint(case)
     import oracle
     w, h, steps = workload(case)
     fp = fingerprint(w)

@@ -135,3 +135,63 @@ def test_autograd_function(small):
         k.sync()
         ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
         check_rhs(f.cpu().numpy(), ref, np.diff(g.row_ptr), w.K, g.n, 1, "handle after KuraRK4Loss")
+
+
+def test_adjoint_config5_graph_vs_oracle_adjoint_golden():
+    """The 65536-node SBM of the adjoint workload (64 communities, p_in 0.95, p_out 0.001, K = 4), loss 1 - r(T),
+    h = 0.01 over 4 steps with a checkpoint every 2: the mixed-precision adjoint against the FP64 oracle adjoint
+    stored in tests/golden/ (the oracle needs about two minutes for it)."""
+    import json
+    import os
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, os.path.join(here, "golden"))
+    import make_trajectory_goldens as MG
+    path = os.path.join(here, "golden", "adjoint_sbm65536_4_fp64.json")
+    rec = json.load(open(path))
+    w = G.workload_sbm_small()
+    g = w.graph
+    fp = MG.fingerprint(w)
+    assert fp["graph_sha256"] == rec["graph_sha256"] and fp["nnz"] == rec["nnz"]
+    assert abs(fp["omega_sum"] - rec["omega_sum"]) <= 1e-12 * max(1.0, abs(rec["omega_sum"]))
+    idx = np.asarray(rec["idx"], dtype=np.int64)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+        L, gom, gK, gth = k.adjoint(torch.tensor(w.theta0, device="cuda:0"), rec["h"], rec["n_steps"], 2, 0)
+        gom, gth = gom.cpu().numpy(), gth.cpu().numpy()
+    assert abs(L - rec["L"]) <= 1e-6 * abs(rec["L"])
+    assert abs(gK - rec["g_K"]) <= 2e-4 * abs(rec["g_K"]), (gK, rec["g_K"])
+    assert _rel(gth[idx], rec["g_theta0"]) < 2e-4, _rel(gth[idx], rec["g_theta0"])
+    assert _rel(gom[idx], rec["g_omega"]) < 2e-4, _rel(gom[idx], rec["g_omega"])
+    assert abs(np.linalg.norm(gth) - rec["g_theta0_norm"]) <= 2e-4 * rec["g_theta0_norm"]
+    assert abs(np.linalg.norm(gom) - rec["g_omega_norm"]) <= 2e-4 * rec["g_omega_norm"]
+
+
+def test_adjoint_config5_finite_differences_32_directions():
+    """The adjoint workload itself: 65536-node SBM, loss 1 - r(T), T = 20 (h = 0.01, 2000 steps), a checkpoint
+    every 64 steps, FP32 right-hand side and FP64 state.  Directional derivatives along 32 random directions of
+    (theta0, omega, K), by central differences (eps = 1e-6) of the FP64 forward loss, against the adjoint's."""
+    w = G.workload_sbm_small()
+    g = w.graph
+    h, steps, M, eps = 0.01, 2000, 64, 1e-6
+    rng = np.random.default_rng(2000)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as ka, \
+            kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K) as kf:
+        L, gom, gK, gth = ka.adjoint(torch.tensor(w.theta0, device="cuda:0"), h, steps, M, 0)
+        gth, gom = gth.cpu().numpy(), gom.cpu().numpy()
+
+        def loss(theta0, omega, K):
+            kf.set_param(omega=np.ascontiguousarray(omega), K=K)
+            th = torch.tensor(theta0, device="cuda:0")
+            kf.rk4_steps(th, h, steps)
+            return 1.0 - kf.order_params(th)[0]
+
+        assert abs(loss(w.theta0, w.omega, w.K) - L) <= 1e-6
+        fd, ad = [], []
+        for _ in range(32):
+            dth, dom, dK = rng.normal(size=g.n), rng.normal(size=g.n), float(rng.normal())
+            lp = loss(w.theta0 + eps * dth, w.omega + eps * dom, w.K + eps * dK)
+            lm = loss(w.theta0 - eps * dth, w.omega - eps * dom, w.K - eps * dK)
+            fd.append((lp - lm) / (2 * eps))
+            ad.append(gth @ dth + gom @ dom + gK * dK)
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.linalg.norm(ad - fd) <= 2e-3 * np.linalg.norm(fd), (np.linalg.norm(ad - fd), np.linalg.norm(fd))
