@@ -124,6 +124,50 @@ def aggregate_replicas(el_ms_local: float, n: int, steps: int, dist=None, device
     return world * n * steps / (el / 1e3), el
 
 
+class EventTimer:
+    """Marks on the current CUDA stream (CUDA events)."""
+
+    def mark(self):
+        import torch
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def ms(self, a, b):
+        return a.elapsed_time(b)
+
+
+class WallTimer:
+    """Host wall-clock marks (for replicas whose step runs on the host)."""
+
+    def mark(self):
+        return time.perf_counter()
+
+    def ms(self, a, b):
+        return (b - a) * 1e3
+
+
+def timed_replicas(run_steps, n: int, steps: int, warmup: int, barrier, timer, dist=None, device=None):
+    """The replica protocol of the N-GPU run: max(warmup, 3) untimed steps, then exactly `steps` steps between
+    barriers, timed on each rank; returns (value, slowest rank's ms) from aggregate_replicas."""
+    run_steps(max(warmup, 3))
+    barrier()
+    barrier()
+    t0 = timer.mark()
+    run_steps(steps)
+    t1 = timer.mark()
+    barrier()
+    return aggregate_replicas(timer.ms(t0, t1), n, steps, dist, device)
+
+
+def core_line(value: float, world: int, steps: int, warmup: int, el_ms: float, dtype: str, config: dict) -> dict:
+    """The fields of the JSON line that follow from the replicas' times."""
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": max(warmup, 3), "ms_per_step": el_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": dict(config, parallelism="replicas" if world > 1 else "single-gpu")}
+
+
 def _workload(name: str):
     from paper_2102_07167_gb300 import gen as G
     if name == "sbm-2p20":
@@ -566,18 +610,10 @@ def run_ours(args):
 
     # ---- warm-up, then the timed region: K RK4 steps through one library call
     k.set_timing(True)
-    k.rk4_steps(theta, w.h, max(args.warmup, 3))
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        barrier()
-        ev0.record()
-        k.rk4_steps(theta, w.h, args.steps)
-        ev1.record()
-        barrier()
-    el_ms = ev0.elapsed_time(ev1)
+        value, el_ms = timed_replicas(lambda ks: k.rk4_steps(theta, w.h, ks), n, args.steps, args.warmup,
+                                      barrier, EventTimer(), dist, dev)
     launch_ms = k.kernel_times()
-    value, el_ms = aggregate_replicas(el_ms, n, args.steps, dist, dev)
     ms_step = el_ms / args.steps
     gpu_launches = 8 * args.steps + 2
 
@@ -717,14 +753,11 @@ def run_ours(args):
             "e_i = |f_i - o_i| / ((K/N)(1 + deg_i)) on the rows of the cpu_baseline sample, o = FP64 oracle "
             "(CSR definition); bound 1e-6 mixed, 1e-10 FP64")
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if prec == kura.PREC_MIXED else "f64", "data": "synthetic",
-                "config": dict(_workload_desc(w, st), precision=args.precision,
-                               parallelism="replicas" if world > 1 else "single-gpu"),
-                "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "gather_roofline": gather_roofline,
-                "cpu_baseline": cpu, "clocks": clk.summary()}
+        line = core_line(value, world, args.steps, args.warmup, el_ms,
+                         "f32+f64" if prec == kura.PREC_MIXED else "f64",
+                         dict(_workload_desc(w, st), precision=args.precision))
+        line.update({"e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+                     "gather_roofline": gather_roofline, "cpu_baseline": cpu, "clocks": clk.summary()})
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:

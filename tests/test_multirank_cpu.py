@@ -1,8 +1,13 @@
-"""The N > 1 path of bench.py on CPU: two gloo ranks, replica aggregation (total work of all ranks over the
-slowest rank's time, max taken across ranks) and the barrier."""
+"""The N > 1 path of bench.py on CPU: two gloo ranks run bench.timed_replicas (the replica protocol of the GPU
+run: warm-up, barriers, exactly K timed steps, max over ranks) with a host stand-in for the device step, and
+bench.core_line turns the ranks' times into the JSON line's fields.  Each rank also builds the host-only block
+plan of its replica (kura_plan_build, no GPU) and the ranks check that they hold identical plans: a single graph
+does not shard on this path, every rank integrates a full replica."""
 import os
 import socket
+import time
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -22,21 +27,53 @@ def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    el = 100.0 + 50.0 * rank                       # rank 1 is the slower replica
-    value, el_max = bench.aggregate_replicas(el, n=1000, steps=10, dist=dist, device="cpu")
-    dist.barrier()
-    out[rank] = (value, el_max)
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_sbm_small(n=3000, n_comm=6, min_size=128, seed=2)
+    g = w.graph
+    p = kura.kura_plan_build(g.n, g.row_ptr, g.col, g.label, g.n_comm)
+    st = kura.kura_plan_stats(p)
+    kura.kura_plan_destroy(p)
+    mine = torch.tensor([st["missing_entries"], st["sparse_entries"], st["dense_blocks"], st["tiles"]],
+                        dtype=torch.int64)
+    all_st = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(all_st, mine)
+    steps_run = []
+
+    def run_steps(k):                              # the host stand-in for k RK4 steps; rank 1 is slower
+        steps_run.append(k)
+        time.sleep(k * (0.004 + 0.004 * rank))
+
+    value, el_max = bench.timed_replicas(run_steps, g.n, 10, 2, dist.barrier, bench.WallTimer(), dist, "cpu")
+    line = bench.core_line(value, dist.get_world_size(), 10, 2, el_max, "f64", {"workload": w.name})
+    out[rank] = (value, el_max, line, [t.tolist() for t in all_st], steps_run)
     dist.destroy_process_group()
 
 
-def test_replica_aggregation_two_gloo_ranks():
+def test_replicas_two_gloo_ranks():
     world = 2
     port = _free_port()
     mgr = mp.Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert set(out.keys()) == {0, 1}
-    for r in range(world):
-        value, el_max = out[r]
-        assert el_max == 150.0
-        assert abs(value - world * 1000 * 10 / 0.150) < 1e-6
+    v0, el0, line0, st0, steps0 = out[0]
+    v1, el1, line1, st1, steps1 = out[1]
+    # identical replicas: every rank planned the same graph
+    assert st0 == st1 and st0[0] == st0[1]
+    # warm-up of max(W, 3) steps, then exactly K timed steps on every rank
+    assert steps0 == [3, 10] and steps1 == [3, 10]
+    # the slowest rank's time, agreed on by both ranks; rank 1 sleeps 8 ms per step
+    assert el0 == el1 and el0 >= 80.0
+    n = 3000
+    assert abs(v0 - world * n * 10 / (el0 / 1e3)) < 1e-6 * v0 and v0 == v1
+    assert line0["n_gpus"] == 2 and line0["value"] == v0 and line0["scaling"] == "weak"
+    assert line0["config"]["parallelism"] == "replicas"
+    assert abs(line0["ms_per_step"] - el0 / 10) < 1e-12
+
+
+def test_single_rank_line_fields():
+    import bench
+    line = bench.core_line(5.0e8, 1, 300, 1, 600.0, "f32+f64", {"workload": "x"})
+    assert line["warmup"] == 3 and line["ms_per_step"] == 2.0 and line["config"]["parallelism"] == "single-gpu"
+    assert line["higher_is_better"] is True and np.isclose(line["value"], 5.0e8)
