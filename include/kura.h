@@ -226,11 +226,15 @@ kura_status kura_mean_deviation(kura_t h, const double* theta_t, const double* t
  * theta0[n] (user order, device or host) is not modified.  The forward pass
  * keeps a checkpoint every ckpt_every steps; the backward pass recomputes one
  * segment at a time, keeping its stage inputs and stage row sums
- * (4 * ckpt_every * 24 bytes per node).  Outputs: *loss and *g_K (host),
- * g_omega[n] and g_theta0[n] (user order, device or host).  Needs a handle
- * created with KURA_PREC_MIXED (FP32 right-hand side, FP64 state and
- * accumulations) and a symmetric adjacency matrix (checked once on the host
- * CSR copy): KURA_ESTATE otherwise.  Synchronises the stream. */
+ * (4 * ckpt_every * 24 bytes per node); segments of exactly ckpt_every
+ * steps are replayed as one captured CUDA graph.  Outputs: *loss and *g_K
+ * (host), g_omega[n] and g_theta0[n] (user order, device or host).  Needs a
+ * handle created with KURA_PREC_MIXED (FP32 right-hand side, FP64 state and
+ * accumulations) and the host CSR copy: KURA_ESTATE otherwise.  For a
+ * directed A (checked once on the host CSR) the first call also plans A^T
+ * (same labels, so the same permutation), over which the nu-weighted sums of
+ * J^T w run; that plan keeps the options the handle had then.  Synchronises
+ * the stream. */
 kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_steps,
                          int32_t ckpt_every, int32_t loss_kind, const double* target,
                          double* loss, double* g_omega, double* g_K, double* g_theta0);

@@ -130,6 +130,7 @@ struct kura_ctx {
     std::string err;
     std::unique_ptr<BatchData> batch;    // non-null for a batch handle
     std::unique_ptr<EnsData> ens;        // non-null for an ensemble handle
+    std::unique_ptr<kura_ctx> tr;        // plan of A^T for the adjoint of a directed A (built on first use)
     int device = 0;
     kura_opts opts{};
     int64_t n = 0;
@@ -1560,7 +1561,31 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
             return h->fail(KURA_ESTATE, "the adjoint needs the host CSR copy to check symmetry");
         h->sym = csr_symmetric(h->n, h->h_row_ptr, h->h_col) ? 1 : 0;
     }
-    if (!h->sym) return h->fail(KURA_ESTATE, "the adjoint supports symmetric adjacency matrices only");
+    if (!h->sym && !h->tr) {
+        // directed A: the nu-weighted sums of J^T w run over A^T, planned from the transposed host CSR with
+        // the same labels (hence the same permutation and communities) and the handle's options
+        if (h->h_col.empty() && h->nnz > 0)
+            return h->fail(KURA_ESTATE, "the adjoint of a directed A needs the host CSR copy");
+        const int64_t nn = h->n;
+        std::vector<int64_t> rpT(size_t(nn) + 1, 0);
+        for (int64_t v = 0; v < nn; v++)
+            for (int64_t e = h->h_row_ptr[size_t(v)]; e < h->h_row_ptr[size_t(v) + 1]; e++) rpT[size_t(h->h_col[size_t(e)]) + 1]++;
+        for (int64_t v = 0; v < nn; v++) rpT[size_t(v) + 1] += rpT[size_t(v)];
+        std::vector<int32_t> colT(static_cast<size_t>(rpT[size_t(nn)]));
+        std::vector<int64_t> fill(rpT.begin(), rpT.end() - 1);
+        for (int64_t v = 0; v < nn; v++)            // rows of A^T come out sorted: v increases
+            for (int64_t e = h->h_row_ptr[size_t(v)]; e < h->h_row_ptr[size_t(v) + 1]; e++)
+                colT[size_t(fill[size_t(h->h_col[size_t(e)])]++)] = int32_t(v);
+        kura_opts o = h->opts;
+        o.keep_host_csr = 0;
+        kura_t t = nullptr;
+        const kura_status st = kura_create(nn, rpT.data(), colT.empty() ? nullptr : colT.data(), h->h_label.data(),
+                                           h->n_comm, h->h_omega.data(), h->K, &o, h->stream, &t);
+        if (st) return h->fail(st, "plan of the transposed matrix: %s", kura_last_error(nullptr));
+        h->tr.reset(t);
+        cudaSetDevice(h->device);
+    }
+    kura_ctx* ah = h->tr ? h->tr.get() : h;           // the plan the nu-weighted pass runs on
     cudaStream_t s = h->stream;
     const size_t n = size_t(h->n), N8 = 8 * n;
     const int64_t M = ckpt_every;
@@ -1575,11 +1600,14 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
             KCHECK(h, d->alloc(N8), "alloc adjoint vectors");
         KCHECK(h, h->ad_sc.alloc(8 * n), "alloc sc");
         KCHECK(h, h->ad_bs.alloc(16 * size_t(h->n_comm)), "alloc block sums");
-        KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(h->n_tiles, 1))), "alloc dK accumulators");
+        KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(ah->n_tiles, 1))), "alloc dK accumulators");
         KCHECK(h, h->ad_part.alloc(8 * ((n + 255) / 256)), "alloc loss partials");
-        KCHECK(h, h->ad_absmax.alloc(16), "alloc table maximum");
+        KCHECK(h, h->ad_absmax.alloc(16), "alloc table maximum");        // [0] max |entry|, [2] ticket
+        KCHECK(h, cudaMemsetAsync(h->ad_absmax.p, 0, 16, s), "zero the table maximum and the ticket");
         h->ad_M = M;
         h->ad_nck = nck;
+        h->graphs.clear();                 // captured segments point at the old buffers
+        h->last_graph = nullptr;
     }
     double* ck = h->ad_ck.as<double>();
     double* Ybuf = h->ad_Y.as<double>();                // stage inputs: slot 4 t + (s - 1), plus one spare
@@ -1622,10 +1650,24 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     // ---- backward, segment by segment
     const double cl[5] = {0, step / 6.0, step / 3.0, step / 3.0, step / 6.0};
     const double ca[5] = {0, 0.5 * step, 0.5 * step, step, 0.0};
-    for (int64_t c = nck - 1; c >= 0; c--) {
-        const int64_t L = std::min(M, n_steps - c * M);
-        // recompute the segment, keeping every stage input and the forward row sums
-        KCHECK(h, cudaMemcpyAsync(Ybuf, ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, s), "restore checkpoint");
+    unsigned int* absmax = ah->has_tc ? h->ad_absmax.as<unsigned int>() : nullptr;
+    unsigned int* ticket = h->ad_absmax.as<unsigned int>() + 2;
+    // graph of the nu-weighted pass: A's own, or A^T's plan reading A's table, T, scalings and error word
+    DevGraph ga = g;
+    if (h->tr) {
+        ga = dev_graph(h->tr.get());
+        ga.table = g.table;
+        ga.T = g.T;
+        ga.scale = g.scale;
+        ga.rscale = g.rscale;
+        ga.rinvdeg = g.rinvdeg;
+        ga.inv_n = g.inv_n;
+        ga.err = g.err;
+    }
+    // one segment of L steps from the checkpoint in Ybuf: recompute it, keeping every stage input and the
+    // forward row sums, then the adjoint steps, last to first (every pointer is fixed for a given L, so
+    // full segments are captured once as a CUDA graph)
+    auto enqueue_segment = [&](int64_t L, cudaStream_t q) {
         for (int64_t t = 0; t < L; t++) {
             for (int st = ST_1; st <= ST_4; st++) {
                 RkArgs rk{};
@@ -1635,23 +1677,20 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                 rk.krk = h->krk.as<double>();
                 rk.sums_out = Fbuf + size_t(4 * t + st - 1) * n;
                 rk.h = step;
-                launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, s);
-                launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
+                launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, q);
+                launch_row_stage<MODE_MIXED>(h, g, rk, st, q);
             }
         }
-        // adjoint steps, last to first
         for (int64_t t = L - 1; t >= 0; t--) {
             for (int st = 4; st >= 1; st--) {
                 double* a_next = (st < 4) ? ((st % 2 == 1) ? h->ad_a0.as<double>() : h->ad_a1.as<double>()) : nullptr;
                 double* a_out = (st % 2 == 0) ? h->ad_a0.as<double>() : h->ad_a1.as<double>();
-                unsigned int* absmax = h->has_tc ? h->ad_absmax.as<unsigned int>() : nullptr;
-                if (absmax) KCHECK(h, cudaMemsetAsync(absmax, 0, sizeof(unsigned int), s), "zero the table maximum");
-                k_adj_prep<<<nb, 256, 0, s>>>(g, Ybuf + size_t(4 * t + st - 1) * n, lam, a_next, cl[st], ca[st],
-                                              h->ad_w.as<double>(), h->ad_nu.as<double>(), h->ad_sc.as<float2>(),
-                                              h->ad_gom.as<double>(), absmax);
-                if (absmax) k_adj_digits<<<nb, 256, 0, s>>>(g, absmax);
-                k_adj_blocksum<<<unsigned(std::max(h->n_comm, 1)), 256, 0, s>>>(g, h->ad_bs.as<double2>());
-                k_adj_T<<<blocks_for(std::max(h->n_comm, 1), 256), 256, 0, s>>>(g, h->ad_bs.as<double2>());
+                if (absmax) cudaMemsetAsync(absmax, 0, sizeof(unsigned int), q);
+                k_adj_prep_bsum<<<unsigned(std::max(h->n_comm, 1)), 256, 0, q>>>(
+                    ga, Ybuf + size_t(4 * t + st - 1) * n, lam, a_next, cl[st], ca[st], h->ad_w.as<double>(),
+                    h->ad_nu.as<double>(), h->ad_sc.as<float2>(), h->ad_gom.as<double>(), absmax,
+                    h->ad_bs.as<double2>(), ticket);
+                if (absmax) k_adj_digits<<<nb, 256, 0, q>>>(ga, absmax);
                 AdjArgs adj{};
                 adj.fsums = Fbuf + size_t(4 * t + st - 1) * n;
                 adj.sc = h->ad_sc.as<float2>();
@@ -1664,8 +1703,32 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                 adj.absmax = absmax;
                 adj.stage = st;
                 RkArgs rk{};
-                launch_row<MODE_MIXED, ST_ADJ>(h, g, rk, s, adj);
+                launch_row<MODE_MIXED, ST_ADJ>(ah, ga, rk, q, adj);
             }
+        }
+    };
+    for (int64_t c = nck - 1; c >= 0; c--) {
+        const int64_t L = std::min(M, n_steps - c * M);
+        KCHECK(h, cudaMemcpyAsync(Ybuf, ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, s), "restore checkpoint");
+        if (L == M && nck > 2) {
+            // full segments: replay one captured graph (keyed apart from the forward step graphs)
+            const std::pair<double, int64_t> key{step, -(int64_t(1) << 40) - M};
+            auto it = h->graphs.find(key);
+            if (it == h->graphs.end()) {
+                std::unique_ptr<GraphEntry> ge(new GraphEntry());
+                cudaGraph_t graph = nullptr;
+                KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+                enqueue_segment(L, h->cap);
+                cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+                if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture of an adjoint segment");
+                ec = cudaGraphInstantiate(&ge->exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate an adjoint segment");
+                it = h->graphs.emplace(key, std::move(ge)).first;
+            }
+            KCHECK(h, cudaGraphLaunch(it->second->exec, s), "adjoint segment launch");
+        } else {
+            enqueue_segment(L, s);
         }
         KCHECK(h, cudaGetLastError(), "launching the adjoint");
     }
@@ -1676,7 +1739,7 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     double* gom_dev = gom_host ? h->fbuf.as<double>() : g_omega;
     k_scatter_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), h->ad_gom.as<double>(), gom_dev);
     KCHECK(h, cudaGetLastError(), "launching the permutation");
-    std::vector<double> gk(size_t(std::max(h->n_tiles, 1)));
+    std::vector<double> gk(size_t(std::max(ah->n_tiles, 1)));
     KCHECK(h, cudaMemcpyAsync(gk.data(), h->ad_gk.p, gk.size() * 8, cudaMemcpyDeviceToHost, s), "copy dK");
     double Lval = 0.0;
     std::vector<double> part;

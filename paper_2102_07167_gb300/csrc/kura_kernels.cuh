@@ -1056,18 +1056,28 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_sum_partials(const double* __r
     if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// ---------------------------------------------------------------- adjoint helpers
-// Per node, adjoint stage s: w = c_lam lambda + c_a a_{s+1}, nu = w K / calM,
-// (sin, cos) of the stage input in FP32 (as in the mixed forward), the table
-// entry (nu sin, nu cos), and dL/domega += w.
-__global__ void k_adj_prep(DevGraph g, const double* __restrict__ Ys, const double* __restrict__ lam,
-                           const double* __restrict__ a_next, double c_lam, double c_a, double* __restrict__ w,
-                           double* __restrict__ nu, float2* __restrict__ sc, double* __restrict__ g_omega,
-                           unsigned int* __restrict__ absmax)
+// One CTA per community J (256 threads), fused per adjoint stage:
+//   - per node i of J: w_i = c_lam lambda_i + c_a a_next_i (the stage weight of the RK4 adjoint),
+//     nu_i = w_i K / calM_i, FP32 (sin, cos) of the FP64-reduced stage input, the table entry
+//     (nu sin, nu cos) that the row kernel's ST_ADJ pass gathers, and g_omega += w;
+//   - the FP64 block sums of that table over J in a fixed order (thread t takes nodes t, t + 256, ...,
+//     then a fixed tree), so the result does not depend on scheduling;
+//   - the largest |table entry| (for the tensor-core digit scale), when absmax is given;
+//   - the last CTA to finish forms T_I = sum over the dense column blocks of I of the block sums and
+//     re-arms the ticket.
+__global__ void __launch_bounds__(256) k_adj_prep_bsum(DevGraph g, const double* __restrict__ Ys,
+                                                       const double* __restrict__ lam,
+                                                       const double* __restrict__ a_next, double c_lam, double c_a,
+                                                       double* __restrict__ w, double* __restrict__ nu,
+                                                       float2* __restrict__ sc, double* __restrict__ g_omega,
+                                                       unsigned int* __restrict__ absmax, double2* __restrict__ bs,
+                                                       unsigned int* __restrict__ ticket)
 {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int J = blockIdx.x;
+    const int64_t b = g.comm_off[J], e = g.comm_off[J + 1];
+    double s_sum = 0.0, c_sum = 0.0;
     float amax = 0.0f;
-    if (i < g.n) {
+    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
         const double wi = c_lam * lam[i] + (a_next ? c_a * a_next[i] : 0.0);
         const double scale = g.rscale ? g.rscale[i] : g.scale;
         const double nui = wi * scale;
@@ -1080,17 +1090,49 @@ __global__ void k_adj_prep(DevGraph g, const double* __restrict__ Ys, const doub
         w[i] = wi;
         nu[i] = nui;
         sc[i] = make_float2(s, c);
-        const float2 e = make_float2(static_cast<float>(nui * static_cast<double>(s)),
-                                     static_cast<float>(nui * static_cast<double>(c)));
-        reinterpret_cast<float2*>(g.table)[i] = e;
+        const float2 ent = make_float2(static_cast<float>(nui * static_cast<double>(s)),
+                                       static_cast<float>(nui * static_cast<double>(c)));
+        reinterpret_cast<float2*>(g.table)[i] = ent;
         g_omega[i] += wi;
-        amax = fmaxf(fabsf(e.x), fabsf(e.y));
+        s_sum += static_cast<double>(ent.x);
+        c_sum += static_cast<double>(ent.y);
+        amax = fmaxf(amax, fmaxf(fabsf(ent.x), fabsf(ent.y)));
     }
     if (absmax) {
         // non-negative floats order like their bit patterns
         const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
         if ((threadIdx.x & 31) == 0 && m) atomicMax(absmax, m);
     }
+    __shared__ double rs[256], rc[256];
+    __shared__ bool last;
+    rs[threadIdx.x] = s_sum;
+    rc[threadIdx.x] = c_sum;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            rs[threadIdx.x] += rs[threadIdx.x + o];
+            rc[threadIdx.x] += rc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bs[J] = make_double2(rs[0], rc[0]);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int I = threadIdx.x; I < g.n_comm; I += 256) {
+        double ts = 0.0, tc = 0.0;
+        for (int64_t q = g.dptr[I]; q < g.dptr[I + 1]; q++) {
+            const double2 v = __ldcg(&bs[g.dcol[q]]);
+            ts += v.x;
+            tc += v.y;
+        }
+        reinterpret_cast<double2*>(g.T)[I] = make_double2(ts, tc);
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // Digit image of the adjoint table for TILE_TC tiles: fixed point with the
@@ -1103,47 +1145,6 @@ __global__ void k_adj_digits(DevGraph g, const unsigned int* __restrict__ absmax
     const double sc = ldexp(1.0, adj_digit_exp(*absmax));
     const float2 e = reinterpret_cast<const float2*>(g.table)[i];
     tc_write_digits(g.dig, i, __double2ll_rn(static_cast<double>(e.x) * sc), __double2ll_rn(static_cast<double>(e.y) * sc));
-}
-
-// One CTA per community: FP64 sums of the (nu sin, nu cos) table over the
-// community's nodes in a fixed order (deterministic), into out[J].
-__global__ void __launch_bounds__(256) k_adj_blocksum(DevGraph g, double2* __restrict__ out)
-{
-    const int J = blockIdx.x;
-    const int64_t b = g.comm_off[J], e = g.comm_off[J + 1];
-    const float2* tab = reinterpret_cast<const float2*>(g.table);
-    double s = 0.0, c = 0.0;
-    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
-        const float2 v = tab[i];
-        s += static_cast<double>(v.x);
-        c += static_cast<double>(v.y);
-    }
-    __shared__ double rs[256], rc[256];
-    rs[threadIdx.x] = s;
-    rc[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o) {
-            rs[threadIdx.x] += rs[threadIdx.x + o];
-            rc[threadIdx.x] += rc[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[J] = make_double2(rs[0], rc[0]);
-}
-
-// T_I = sum over the dense column blocks J of I of the block sums (mixed layout).
-__global__ void k_adj_T(DevGraph g, const double2* __restrict__ bs)
-{
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= g.n_comm) return;
-    double s = 0.0, c = 0.0;
-    for (int64_t k = g.dptr[I]; k < g.dptr[I + 1]; k++) {
-        const double2 v = bs[g.dcol[k]];
-        s += v.x;
-        c += v.y;
-    }
-    reinterpret_cast<double2*>(g.T)[I] = make_double2(s, c);
 }
 
 // Terminal adjoint of L = 1 - r: lambda_m = -sin(psi - theta_m) / N, psi from order_out[1].

@@ -97,13 +97,39 @@ def test_adjoint_rejects_unsupported_handles(small):
         with pytest.raises(kura.KuraError) as e:
             k.adjoint(np.ascontiguousarray(w.theta0), 0.01, 2)
         assert e.value.status == kura.KURA_ESTATE
-    A = np.zeros((6, 6), np.uint8)
-    A[0, 1] = 1                                                                        # directed edge
-    gd = G.from_dense(A)
-    with kura.Kuramoto(gd.row_ptr, gd.col, gd.label, 1, np.zeros(6), 1.0, precision=kura.PREC_MIXED) as k:
-        with pytest.raises(kura.KuraError) as e:
-            k.adjoint(np.zeros(6), 0.01, 2)
-        assert e.value.status == kura.KURA_ESTATE
+
+
+@pytest.mark.parametrize("loss_kind", [0, 1])
+def test_adjoint_directed_graph_vs_oracle(loss_kind):
+    """A directed A (each SBM edge kept in one direction only with probability 0.3, plus one-way dense
+    off-diagonal blocks): the nu-weighted sums of J^T w run over the plan of A^T; against the FP64 oracle
+    adjoint, which forms J^T from the CSR directly."""
+    rng = np.random.default_rng(21)
+    sizes = [300, 513, 129, 700]
+    lab = np.repeat(np.arange(4), sizes)
+    n = int(sum(sizes))
+    P = np.full((4, 4), 0.01)
+    np.fill_diagonal(P, [0.9, 0.7, 0.95, 0.8])
+    P[0, 3] = 0.75                                              # a dense block whose transpose is sparse
+    A = (rng.random((n, n)) < P[lab][:, lab]).astype(np.uint8)
+    np.fill_diagonal(A, 0)
+    drop = rng.random((n, n)) < 0.3
+    A[drop] = 0                                                 # breaks the symmetry
+    perm = rng.permutation(n)
+    gd = G.from_dense(A[perm][:, perm], lab[perm].astype(np.int32), 4)
+    omega, theta0, K = rng.normal(size=n), rng.uniform(0, 2 * np.pi, n), 3.0
+    h, steps, M = 0.01, 20, 6
+    target = theta0 + 0.1 * rng.normal(size=n) if loss_kind == 1 else None
+    L_ref, gom_ref, gK_ref, gth_ref = oracle.adjoint_rk4_csr(gd.row_ptr, gd.col, omega, K, theta0, h, steps,
+                                                             loss_kind, target)
+    with kura.Kuramoto(gd.row_ptr, gd.col, gd.label, 4, omega, K, precision=kura.PREC_MIXED) as k:
+        tg = torch.tensor(target, device="cuda:0") if target is not None else None
+        L, gom, gK, gth = k.adjoint(torch.tensor(theta0, device="cuda:0"), h, steps, M, loss_kind, tg)
+        gom, gth = gom.cpu().numpy(), gth.cpu().numpy()
+    assert abs(L - L_ref) <= 1e-6 * max(1.0, abs(L_ref))
+    assert _rel(gth, gth_ref) < 2e-4, _rel(gth, gth_ref)
+    assert _rel(gom, gom_ref) < 2e-4, _rel(gom, gom_ref)
+    assert abs(gK - gK_ref) <= 2e-4 * max(abs(gK_ref), 1e-12), (gK, gK_ref)
 
 
 def test_autograd_function(small):

@@ -353,12 +353,21 @@ def test_paper_classical_runs_synchronise(K):
 
 
 # ----------------------------------------------------------------------------- discrete adjoint
+@pytest.mark.parametrize("directed", [False, True])
 @pytest.mark.parametrize("loss_kind", [0, 1])
-def test_adjoint_matches_central_finite_differences(loss_kind):
+def test_adjoint_matches_central_finite_differences(loss_kind, directed):
     """The oracle's discrete RK4 adjoint against central differences of the oracle's own forward loss
-    (eps = 1e-6): directional derivatives in theta0 and omega, and the K derivative."""
+    (eps = 1e-6): directional derivatives in theta0 and omega, and the K derivative; on a symmetric SBM and
+    on a directed one (each edge kept in one direction with probability 0.6), where J^T differs from J."""
     rng = np.random.default_rng(21 + loss_kind)
     g = G.sbm(5, [30, 25, 20], [0.8, 0.7, 0.9], 0.1)
+    if directed:
+        A = np.zeros((g.n, g.n), np.uint8)
+        for u in range(g.n):
+            A[u, g.col[g.row_ptr[u]:g.row_ptr[u + 1]]] = 1
+        A[np.random.default_rng(7).random(A.shape) < 0.4] = 0
+        assert (A != A.T).any()
+        g = G.from_dense(A, g.label, g.n_comm)
     n = g.n
     omega, theta0 = rng.normal(size=n), rng.uniform(0, 2 * np.pi, n)
     K, h, steps = 3.0, 0.02, 15
