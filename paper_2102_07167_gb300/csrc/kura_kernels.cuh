@@ -715,92 +715,50 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 }
             }
         }
-        // A group of short sub-rows (mixed precision only, more sub-rows than consumer warps): this warp
-        // takes sub-rows j and j + ROW_CONSUMERS, one int4 of indices per lane each.  Its indices are read
-        // into registers and its ring slot handed back at once; the next group's indices are read while
-        // this group's gathers are in flight (one group ahead), so the ring's barrier, header and index
-        // reads do not sit between two rounds of gathers.
-        struct ShortWork {
-            int rel0, j, ma, mb;
-            bool hb;
-            int4 va, vb;
-        };
-        auto load_short = [&](int sl, int2 meta, ShortWork& wk) {
-            const int32_t* slot = ring + size_t(sl) * SLOT;
-            wk.rel0 = meta.x;
-            wk.j = ((warp - meta.x) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
-            wk.hb = wk.j + ROW_CONSUMERS < meta.y;            // warp-uniform; j < meta.y always
-            const int4 ha_ = reinterpret_cast<const int4*>(slot)[wk.j];
-            const int4 hb_ = wk.hb ? reinterpret_cast<const int4*>(slot)[wk.j + ROW_CONSUMERS] : make_int4(0, 0, 0, 0);
-            wk.ma = (ha_.y + 3) >> 2;
-            wk.mb = (hb_.y + 3) >> 2;
-            const int ta = wk.ma + ((ha_.w + 3) >> 2), tb = wk.mb + ((hb_.w + 3) >> 2);
-            const int4 z4 = make_int4(zidx, zidx, zidx, zidx);
-            wk.va = lane < ta ? reinterpret_cast<const int4*>(slot + ha_.x)[lane] : z4;
-            wk.vb = lane < tb ? reinterpret_cast<const int4*>(slot + hb_.x)[lane] : z4;
-            release_slot(&empty_bar[sl], uint32_t(wk.va.x | wk.vb.x));      // indices are in registers
-        };
-        ShortWork nxt{};
-        bool have_nxt = false;
         for (int gi = 0; gi < ngroups && ok; gi++) {
             const int sl = gi % ROW_SLOTS, fill = gi / ROW_SLOTS;
-            int2 meta = make_int2(0, 0);
-            bool is_short = false;
-            ShortWork cur{};
-            if (have_nxt) {
-                cur = nxt;
-                is_short = true;
-                have_nxt = false;
-            } else {
-                if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
-                    atomicOr(g.err, ERR_TIMEOUT);
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
-                meta = slot_meta[sl];
-                if constexpr (MODE == MODE_MIXED) is_short = meta.y > ROW_CONSUMERS;
-                if (is_short) load_short(sl, meta, cur);
+            if (!mbar_wait_bounded(&full_bar[sl], uint32_t(fill) & 1u, LIMIT_NS)) {
+                atomicOr(g.err, ERR_TIMEOUT);
+                atomicExch(&abort_flag, 1);
+                break;
             }
-            if constexpr (MODE == MODE_MIXED) if (is_short) {
+            const int2 meta = slot_meta[sl];
+            const int rel0 = meta.x;
+            const int j = ((warp - rel0) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
+            const int32_t* slot = ring + size_t(sl) * SLOT;
+            if constexpr (MODE == MODE_MIXED) if (meta.y > ROW_CONSUMERS) {
+                // ---- group of short sub-rows (mixed precision only): this warp takes j and
+                // j + ROW_CONSUMERS (one int4 of indices per lane each) and gathers both
+                // before summing
+                const bool hb = j + ROW_CONSUMERS < meta.y;       // warp-uniform; j < meta.y always
+                const int4 ha_ = reinterpret_cast<const int4*>(slot)[j];
+                const int4 hb_ = hb ? reinterpret_cast<const int4*>(slot)[j + ROW_CONSUMERS] : make_int4(0, 0, 0, 0);
+                const int ma = (ha_.y + 3) >> 2, ta = ma + ((ha_.w + 3) >> 2);
+                const int mb = (hb_.y + 3) >> 2, tb = mb + ((hb_.w + 3) >> 2);
+                const int4 z4 = make_int4(zidx, zidx, zidx, zidx);
+                const int4 va = lane < ta ? reinterpret_cast<const int4*>(slot + ha_.x)[lane] : z4;
+                const int4 vb = lane < tb ? reinterpret_cast<const int4*>(slot + hb_.x)[lane] : z4;
+                release_slot(&empty_bar[sl], uint32_t(va.x | vb.x));      // indices are in registers
                 const bool miss_fast = t.flags & TILE_MISS_IN_WINDOW, pres_check = t.flags & TILE_PRES_CHECK;
-                const bool mia = lane < cur.ma, mib = lane < cur.mb;
+                const bool mia = lane < ma, mib = lane < mb;
                 auto fetch = [&](int idx, bool missing) -> E {
                     if (missing) return miss_fast ? win[idx - t.wbeg] : gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx);
                     return pres_check ? gather_entry<MODE>(win, t.wbeg, t.wlen, table, idx) : __ldg(table + idx);
                 };
-                const E a0 = fetch(cur.va.x, mia), a1 = fetch(cur.va.y, mia), a2 = fetch(cur.va.z, mia),
-                        a3 = fetch(cur.va.w, mia);
-                const E b0 = fetch(cur.vb.x, mib), b1 = fetch(cur.vb.y, mib), b2 = fetch(cur.vb.z, mib),
-                        b3 = fetch(cur.vb.w, mib);
-                // the next group, while the gathers are in flight: a short one is loaded now
-                if (gi + 1 < ngroups) {
-                    const int sl2 = (gi + 1) % ROW_SLOTS, fill2 = (gi + 1) / ROW_SLOTS;
-                    if (!mbar_wait_bounded(&full_bar[sl2], uint32_t(fill2) & 1u, LIMIT_NS)) {
-                        atomicOr(g.err, ERR_TIMEOUT);
-                        atomicExch(&abort_flag, 1);
-                    } else {
-                        const int2 m2 = slot_meta[sl2];
-                        if (m2.y > ROW_CONSUMERS) {
-                            load_short(sl2, m2, nxt);
-                            have_nxt = true;
-                        }
-                    }
-                }
+                const E a0 = fetch(va.x, mia), a1 = fetch(va.y, mia), a2 = fetch(va.z, mia), a3 = fetch(va.w, mia);
+                const E b0 = fetch(vb.x, mib), b1 = fetch(vb.y, mib), b2 = fetch(vb.z, mib), b3 = fetch(vb.w, mib);
                 A sa = (a0.x + a1.x) + (a2.x + a3.x), ca = (a0.y + a1.y) + (a2.y + a3.y);
                 A sb = (b0.x + b1.x) + (b2.x + b3.x), cb = (b0.y + b1.y) + (b2.y + b3.y);
                 if (mia) { sa = -sa; ca = -ca; }
                 if (mib) { sb = -sb; cb = -cb; }
                 const A tot = warp_sum4(sa, ca, sb, cb);
-                if (lane == 0) stash[cur.rel0 + cur.j].s = tot;
-                if (lane == 8) stash[cur.rel0 + cur.j].c = tot;
-                if (cur.hb && lane == 16) stash[cur.rel0 + cur.j + ROW_CONSUMERS].s = tot;
-                if (cur.hb && lane == 24) stash[cur.rel0 + cur.j + ROW_CONSUMERS].c = tot;
+                if (lane == 0) stash[rel0 + j].s = tot;
+                if (lane == 8) stash[rel0 + j].c = tot;
+                if (hb && lane == 16) stash[rel0 + j + ROW_CONSUMERS].s = tot;
+                if (hb && lane == 24) stash[rel0 + j + ROW_CONSUMERS].c = tot;
                 if (*(volatile int*)&abort_flag) break;
                 continue;
             }
-            const int rel0 = meta.x;
-            const int j = ((warp - rel0) % ROW_CONSUMERS + ROW_CONSUMERS) % ROW_CONSUMERS;
-            const int32_t* slot = ring + size_t(sl) * SLOT;
             const bool have = j < meta.y;                       // warp-uniform
             int4 v[4];
             int m4 = 0, tot4 = 0;
