@@ -339,9 +339,10 @@ def bench_adjoint(dev):
     w = G.workload_sbm_small()
     g = w.graph
     h, steps, M = 0.01, 2000, 64
-    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+
+    def measure(k):
         th0 = torch.tensor(w.theta0, device=dev)
-        k.adjoint(th0, h, 64, M, 0)                       # warm-up (buffers, graphs)
+        k.adjoint(th0, h, 3 * M, M, 0)                    # warm-up (buffers, captured segments)
         th = th0.clone()
         k.rk4_steps(th, h, 8)
         torch.cuda.synchronize()
@@ -352,14 +353,25 @@ def bench_adjoint(dev):
         e1.record()
         torch.cuda.synchronize()
         fwd_ms = e0.elapsed_time(e1)
-        t0 = time.perf_counter()
+        e0.record()
         L, gom, gK, gth = k.adjoint(th0, h, steps, M, 0)
+        e1.record()
         torch.cuda.synchronize()
-        adj_ms = (time.perf_counter() - t0) * 1e3
-    return {"workload": "SBM N=65536 (64 communities, p_in 0.95, p_out 0.001), loss 1 - r(T), T = 20, "
-                        "h = 0.01, 2000 RK4 steps, checkpoint every 64", "precision": "mixed (FP32 RHS, FP64 state)",
-            "forward_ms": fwd_ms, "forward_backward_ms": adj_ms, "ratio": adj_ms / fwd_ms, "loss": L,
-            "g_K": gK, "g_theta0_norm": float(torch.linalg.norm(gth)), "g_omega_norm": float(torch.linalg.norm(gom))}
+        adj_ms = e0.elapsed_time(e1)
+        return {"forward_ms": fwd_ms, "forward_backward_ms": adj_ms, "ratio": adj_ms / fwd_ms, "loss": L,
+                "g_K": gK, "g_theta0_norm": float(torch.linalg.norm(gth)),
+                "g_omega_norm": float(torch.linalg.norm(gom))}
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED) as k:
+        default = measure(k)
+        tune = k.autotune(torch.tensor(w.theta0, device=dev), budget_s=20.0)
+        tuned = measure(k)
+        tuned["autotune"] = tune
+    out = {"workload": "SBM N=65536 (64 communities, p_in 0.95, p_out 0.001), loss 1 - r(T), T = 20, "
+                       "h = 0.01, 2000 RK4 steps, checkpoint every 64", "precision": "mixed (FP32 RHS, FP64 state)",
+           "timing": "CUDA events around each library call (the adjoint call synchronises at its end)"}
+    out.update(tuned)
+    out["default_plan"] = default
+    return out
 
 
 def bench_batch(dev, steps: int = 1000, tc_steps: int = 200):
@@ -454,10 +466,14 @@ def bench_complete_512(dev):
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1))
         return float(np.median(out)), th.cpu().numpy()
-    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K, precision=kura.PREC_FP64) as k:
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K, precision=kura.PREC_FP64,
+                       persistent_small=0) as k:
         k.rk4_steps(torch.tensor(w.theta0, device=dev), w.h, w.n_steps)
         ms_graph, th_graph = timed(lambda th: k.rk4_steps(th, w.h, w.n_steps))
         ms_direct, _ = timed(lambda th: k.direct_rk4_steps(th, w.h, w.n_steps, kura.PREC_FP64), reps=3)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, 1, w.omega, w.K, precision=kura.PREC_FP64) as kc:
+        kc.rk4_steps(torch.tensor(w.theta0, device=dev), w.h, w.n_steps)
+        ms_cluster, th_cluster = timed(lambda th: kc.rk4_steps(th, w.h, w.n_steps))
     with kura.KuramotoBatch([(None, None, None, 1, w.omega, w.K)], precision=kura.PREC_FP64) as b:
         b.rk4_steps(torch.tensor(w.theta0, device=dev), w.h, w.n_steps)
         ms_pers, th_pers = timed(lambda th: b.rk4_steps(th, w.h, w.n_steps))
@@ -471,6 +487,9 @@ def bench_complete_512(dev):
            "graph_over_floor": (ms_graph * 1e3 / st) / (8 * floor_us),
            "persistent_single_cta": {"us_per_step": ms_pers * 1e3 / st, "value": g.n * st / (ms_pers / 1e3),
                                      "launches": 1},
+           "persistent_cluster": {"us_per_step": ms_cluster * 1e3 / st, "value": g.n * st / (ms_cluster / 1e3),
+                                  "launches": 1, "how": "kura_rk4_steps on a small graph: one launch of one "
+                                                        "8-CTA thread-block cluster for all 200 steps"},
            "direct_fp64": {"us_per_step": ms_direct * 1e3 / st, "value": g.n * st / (ms_direct / 1e3)}}
     # CPU legs: the oracle as it stands (CSR definition, one core) on the whole trajectory, and the
     # OpenMP block method; the oracle's final phases also give the GPU paths' error
@@ -482,7 +501,10 @@ def bench_complete_512(dev):
                            "sample": f"whole trajectory ({st} steps) by oracle.rk4_csr in {t_orc:.1f} s"}
     res["cpu_block_baseline"] = cpu_block_baseline(w, steps_full=st)
     res["max_abs_err_vs_oracle"] = {"graph_step_loop": float(np.abs(th_graph - ref).max()),
-                                    "persistent_single_cta": float(np.abs(th_pers - ref).max())}
+                                    "persistent_single_cta": float(np.abs(th_pers - ref).max()),
+                                    "persistent_cluster": float(np.abs(th_cluster - ref).max())}
+    res["value"] = g.n * st / (ms_cluster / 1e3)
+    res["unit"] = UNIT
     return res
 
 

@@ -89,7 +89,14 @@ typedef struct {
     /* batch handles: lanes that gather one row's listed entries, 32 (a warp
      * per row; default when 0), 16 or 8 (2 or 4 rows per warp) */
     int32_t row_lanes;
-    int32_t reserved[3];
+    /* single handles of small graphs (n <= 4096, n_comm <= 256, 0/1 matrix,
+     * host CSR kept, at most 16 listed corrections per row on average):
+     * 1 (default) kura_rk4_steps runs every step in one launch of one
+     * thread-block cluster of 8 CTAs, the (sin, cos) table spread over their
+     * shared memory and read through the cluster (not while kernel timing is
+     * on); 0: always the CUDA-graph step loop */
+    int32_t persistent_small;
+    int32_t reserved[2];
 } kura_opts;
 
 typedef struct {

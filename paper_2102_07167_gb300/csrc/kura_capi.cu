@@ -17,6 +17,7 @@
 #include "kura_batch.cuh"
 #include "kura_ensemble.cuh"
 #include "kura_kernels.cuh"
+#include "kura_small.cuh"
 #include "plan.hpp"
 
 using namespace kura;
@@ -158,6 +159,10 @@ struct kura_ctx {
     int64_t ad_M = 0, ad_nck = 0;
     int sym = -1;   // host CSR symmetric? (-1 unknown)
     DevMem y, Y, krk, fbuf, user, red, order_out;
+    // small graphs: per-row lists of the persistent cluster step loop (kura_small.cuh)
+    bool small = false;
+    int32_t small_P = 0;
+    DevMem sm_row_off, sm_row_nm, sm_ent, sm_node_comm, sm_dptr, sm_dcol;
     DevMem deg, sums, diag;                   // diagnostics: degrees, row sums, partials (lazily)
     DevMem d_row_ptr, d_col, d_omega_user;   // direct baseline (user order), lazily uploaded
     int q_bits = 0;
@@ -442,6 +447,102 @@ int64_t plan_stream_bytes(const Plan& p)
     return 4 * listed + 16 * int64_t(p.row_sub0.empty() ? 0 : p.row_sub0.back()) + bm;
 }
 
+// Per-row lists for the persistent cluster step loop of small graphs, from the host CSR and the plan's
+// permutation and dense blocks: [zeros of the row's dense blocks (the diagonal excluded) | non-zeros of its
+// sparse blocks], permuted columns.  Only graphs with n <= SMALL_MAX_N, n_comm <= SMALL_MAX_COMM, a 0/1
+// matrix, the host CSR kept and at most 16 listed entries per row on average take this path.
+kura_status build_small(kura_ctx* h)
+{
+    h->small = false;
+    const Plan& p = h->plan;
+    const int64_t n = h->n;
+    if (!h->opts.persistent_small || p.valued || n > SMALL_MAX_N || h->n_comm > SMALL_MAX_COMM ||
+        (h->h_col.empty() && h->nnz > 0))
+        return KURA_OK;
+    const int nc = h->n_comm;
+    std::vector<int32_t> inv(static_cast<size_t>(n));
+    for (int64_t r = 0; r < n; r++) inv[size_t(p.perm[size_t(r)])] = int32_t(r);
+    std::vector<uint8_t> dense(size_t(nc) * size_t(nc), 0);
+    for (int I = 0; I < nc; I++)
+        for (int64_t k = p.dptr[size_t(I)]; k < p.dptr[size_t(I) + 1]; k++) dense[size_t(I) * nc + size_t(p.dcol[size_t(k)])] = 1;
+    std::vector<int32_t> row_off(size_t(n) + 1, 0), row_nm(size_t(n), 0), ent;
+    std::vector<uint8_t> mark(static_cast<size_t>(n), 0);
+    for (int64_t r = 0; r < n; r++) {
+        const int64_t v = p.perm[size_t(r)];
+        const int I = p.node_comm[size_t(r)];
+        const int64_t b = h->h_row_ptr[size_t(v)], e = h->h_row_ptr[size_t(v) + 1];
+        for (int64_t q = b; q < e; q++) mark[size_t(inv[size_t(h->h_col[size_t(q)])])] = 1;
+        int32_t nm = 0;
+        for (int64_t k = p.dptr[size_t(I)]; k < p.dptr[size_t(I) + 1]; k++) {
+            const int J = p.dcol[size_t(k)];
+            for (int64_t c = p.comm_off[size_t(J)]; c < p.comm_off[size_t(J) + 1]; c++)
+                if (!mark[size_t(c)] && c != r) { ent.push_back(int32_t(c)); nm++; }
+        }
+        for (int64_t q = b; q < e; q++) {
+            const int32_t c = inv[size_t(h->h_col[size_t(q)])];
+            if (c != r && !dense[size_t(I) * nc + size_t(p.node_comm[size_t(c)])]) ent.push_back(c);
+        }
+        for (int64_t q = b; q < e; q++) mark[size_t(inv[size_t(h->h_col[size_t(q)])])] = 0;
+        row_nm[size_t(r)] = nm;
+        row_off[size_t(r) + 1] = int32_t(ent.size());
+        if (int64_t(ent.size()) > 16 * n) return KURA_OK;        // too many listed entries: keep the graph loop
+    }
+    std::vector<int32_t> nci(p.node_comm.begin(), p.node_comm.end());
+    std::vector<int32_t> dp(p.dptr.begin(), p.dptr.end()), dc(p.dcol.begin(), p.dcol.end());
+    cudaStream_t s = h->stream;
+    KCHECK(h, upload(h->sm_row_off, row_off, s), "upload small-graph rows");
+    KCHECK(h, upload(h->sm_row_nm, row_nm, s), "upload small-graph rows");
+    KCHECK(h, upload(h->sm_ent, ent, s), "upload small-graph entries");
+    KCHECK(h, upload(h->sm_node_comm, nci, s), "upload small-graph communities");
+    KCHECK(h, upload(h->sm_dptr, dp, s), "upload small-graph dense blocks");
+    KCHECK(h, upload(h->sm_dcol, dc, s), "upload small-graph dense blocks");
+    h->small_P = int32_t(((n + SMALL_CLUSTER - 1) / SMALL_CLUSTER + 31) / 32 * 32);
+    h->small = true;
+    return KURA_OK;
+}
+
+// All n_steps RK4 steps of a small graph in one launch of one cluster of SMALL_CLUSTER CTAs (the permuted
+// state in h->y).
+kura_status launch_small(kura_ctx* h, double step, int64_t n_steps, cudaStream_t s)
+{
+    SmallArgs a{};
+    a.n = int(h->n);
+    a.n_comm = h->n_comm;
+    a.P = h->small_P;
+    a.node_comm = h->sm_node_comm.as<int32_t>();
+    a.dptr = h->sm_dptr.as<int32_t>();
+    a.dcol = h->sm_dcol.as<int32_t>();
+    a.row_off = h->sm_row_off.as<int32_t>();
+    a.row_nm = h->sm_row_nm.as<int32_t>();
+    a.ent = h->sm_ent.as<int32_t>();
+    a.omega = h->omega.as<double>();
+    a.rscale = h->opts.scaling == KURA_SCALING_DEGREE ? h->rscale.as<double>() : nullptr;
+    a.scale = h->K / double(h->n);
+    a.scale_q = std::ldexp(1.0, h->q_bits);
+    a.inv_scale_q = std::ldexp(1.0, -h->q_bits);
+    a.y = h->y.as<double>();
+    a.Y = h->Y.as<double>();
+    a.krk = h->krk.as<double>();
+    a.err = h->err_flags.as<int>();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(SMALL_CLUSTER);
+    cfg.blockDim = dim3(SMALL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SMALL_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = h->opts.precision == KURA_PREC_MIXED
+                        ? cudaLaunchKernelEx(&cfg, k_small_rk4<MODE_MIXED>, a, step, n_steps)
+                        : cudaLaunchKernelEx(&cfg, k_small_rk4<MODE_FP64>, a, step, n_steps);
+    KCHECK(h, e, "launching the small-graph step loop");
+    return KURA_OK;
+}
+
 kura_status build_device(kura_ctx* h, Plan&& plan)
 {
     cudaStream_t s = h->stream;
@@ -531,6 +632,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     }
     for (DevMem* d : {&h->y, &h->Y, &h->krk, &h->fbuf, &h->user}) KCHECK(h, d->alloc(8 * n), "alloc state");
     KCHECK(h, h->order_out.alloc(8 * (2 + 2 * nc)), "alloc order_out");
+    if (kura_status st = build_small(h)) return st;
     KCHECK(h, cudaStreamSynchronize(s), "upload");
     // the correction stream now lives on the device
     std::vector<int32_t>().swap(p.gstream);
@@ -601,6 +703,7 @@ void kura_default_opts(kura_opts* o)
     o->keep_host_csr = 1;
     o->tensor_cores = 1;
     o->bitmap_zmin = -1.0;
+    o->persistent_small = 1;
 }
 
 int32_t kura_version(void) { return 100; }
@@ -984,6 +1087,11 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
     KCHECK(h, cudaGetLastError(), "launching the permutation");
     const int64_t chunk_max = 8;
     int64_t left = n_steps;
+    if (h->small && !h->timing && n_steps > 0) {
+        // small graph: every step in one launch of one thread-block cluster
+        if (kura_status st = launch_small(h, step, n_steps, s)) return st;
+        left = 0;
+    }
     while (left > 0) {
         const int64_t c = std::min(left, chunk_max);
         auto key = std::make_pair(step, c * (h->timing ? -1 : 1));
