@@ -521,8 +521,6 @@ kura_status launch_small(kura_ctx* h, double step, int64_t n_steps, cudaStream_t
     a.scale_q = std::ldexp(1.0, h->q_bits);
     a.inv_scale_q = std::ldexp(1.0, -h->q_bits);
     a.y = h->y.as<double>();
-    a.Y = h->Y.as<double>();
-    a.krk = h->krk.as<double>();
     a.err = h->err_flags.as<int>();
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(SMALL_CLUSTER);

@@ -8,8 +8,10 @@
 // barrier publishes both; every CTA adds up the community sums of all CTAs
 // (distributed shared memory, a fixed order) into T_I, and its rows gather
 // their listed corrections from whichever CTA owns the column (ld from the
-// owner's shared memory through the cluster window).  The FP64 epilogue and
-// RK4 update write the CTA's own nodes; a second cluster barrier ends the
+// owner's shared memory through the cluster window).  Thread t of CTA r owns
+// node r P + t for the whole launch: its state, stage input and RK4 sum stay
+// in registers (the state is written back once, at the end), and it runs the
+// node's FP64 epilogue and RK4 update.  A second cluster barrier ends each
 // stage before any table slice is overwritten.  Method: eq:KuramotoGraph by
 // eq:KuramotoGraphApproach (Sec. 3), classical RK4.
 #pragma once
@@ -38,9 +40,7 @@ struct SmallArgs {
     const double* rscale;             // [n] K / deg (degree scaling) or null
     double scale;                     // K / n (uniform scaling)
     double scale_q, inv_scale_q;      // fixed point 2^q, 2^-q
-    double* y;                        // [n] state, in place
-    double* Y;                        // [n] stage input
-    double* krk;                      // [n] k1 + 2 k2 + 2 k3
+    double* y;                        // [n] state, in place (read at the start, written at the end)
     int* err;
 };
 
@@ -84,9 +84,11 @@ __device__ __forceinline__ unsigned long long ld_cluster(const unsigned long lon
 template <int MODE>
 __global__ void __launch_bounds__(SMALL_THREADS, 1) k_small_rk4(SmallArgs a, double h, int64_t n_steps)
 {
+    static_assert(SMALL_MAX_P <= SMALL_THREADS, "one own node per thread");
     using E = typename EntryT<MODE>::T;
     using A = typename EntryT<MODE>::A;
     __shared__ E tab[SMALL_MAX_P];                           // this CTA's slice of the (sin, cos) table
+    __shared__ E stash[SMALL_MAX_P];                         // listed-entry sums of the own rows
     __shared__ unsigned long long S[2 * SMALL_MAX_COMM];     // this CTA's fixed-point community sums
     __shared__ long long Tq[2 * SMALL_MAX_COMM];             // T_I in fixed point (exact cluster totals)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -95,14 +97,21 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_small_rk4(SmallArgs a, dou
     const int base = int(rank) * a.P;
     const int cnt = max(0, min(a.P, a.n - base));
     const int nc = a.n_comm;
+    // thread tid owns node base + tid for the whole launch: its frequency, scaling and community stay in
+    // registers, and its state is read and written by this thread only
+    const bool own = tid < cnt;
+    const int row = base + tid;
+    const double om = own ? a.omega[row] : 0.0;
+    const double sc = own ? (a.rscale ? a.rscale[row] : a.scale) : 0.0;
+    const int Jown = own ? a.node_comm[row] : 0;
+    double yv = own ? a.y[row] : 0.0, kv = 0.0, Yv = yv;
     for (int q = tid; q < 2 * nc; q += SMALL_THREADS) S[q] = 0ull;
     __syncthreads();
     for (int64_t step = 0; step < n_steps; step++) {
         for (int st = 1; st <= 4; st++) {
-            // ---- table slice and fixed-point community sums of the own nodes
-            const double* th_in = st == 1 ? a.y : a.Y;
-            for (int i = tid; i < cnt; i += SMALL_THREADS) {
-                const double th = th_in[base + i];
+            // ---- table entry and fixed-point community sums of the own node
+            if (own) {
+                const double th = st == 1 ? yv : Yv;
                 if (!isfinite(th)) atomicOr(a.err, ERR_NONFINITE);
                 long long sf, cf;
                 if constexpr (MODE == MODE_FP64) {
@@ -110,20 +119,19 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_small_rk4(SmallArgs a, dou
                     sincos(th, &s, &c);
                     sf = __double2ll_rn(s * a.scale_q);
                     cf = __double2ll_rn(c * a.scale_q);
-                    reinterpret_cast<longlong2*>(tab)[i] = make_longlong2(sf, cf);
+                    reinterpret_cast<longlong2*>(tab)[tid] = make_longlong2(sf, cf);
                 } else {
                     const double k = rint(th * KURA_INV_TWO_PI);
                     double r = fma(-k, KURA_TWO_PI_HI, th);
                     r = fma(-k, KURA_TWO_PI_LO, r);
                     float s, c;
                     sincosf(static_cast<float>(r), &s, &c);
-                    reinterpret_cast<float2*>(tab)[i] = make_float2(s, c);
+                    reinterpret_cast<float2*>(tab)[tid] = make_float2(s, c);
                     sf = __float2ll_rn(s * static_cast<float>(a.scale_q));
                     cf = __float2ll_rn(c * static_cast<float>(a.scale_q));
                 }
-                const int J = a.node_comm[base + i];
-                atomicAdd(&S[2 * J], static_cast<unsigned long long>(sf));
-                atomicAdd(&S[2 * J + 1], static_cast<unsigned long long>(cf));
+                atomicAdd(&S[2 * Jown], static_cast<unsigned long long>(sf));
+                atomicAdd(&S[2 * Jown + 1], static_cast<unsigned long long>(cf));
             }
             cluster_barrier();
             // ---- T_I from the exact totals over the cluster (integer sums: order free)
@@ -139,54 +147,61 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_small_rk4(SmallArgs a, dou
                 Tq[2 * I] = ts;
                 Tq[2 * I + 1] = tc;
             }
-            __syncthreads();
-            // ---- rows: a warp per own row, listed entries gathered from the owning CTA's slice; the
-            // FP64 epilogue and the RK4 stage update by the row's lane 0
+            // ---- rows: a warp per own row with listed entries, gathered from the owning CTA's slice
             for (int i = warp; i < cnt; i += NW) {
-                const int row = base + i;
-                const int beg = a.row_off[row], end = a.row_off[row + 1], nm = a.row_nm[row];
+                const int rr = base + i;
+                const int beg = a.row_off[rr], end = a.row_off[rr + 1], nm = a.row_nm[rr];
                 A as = 0, ac = 0;
-                for (int k = beg + lane; k < end; k += 32) {
-                    const int c = a.ent[k];
-                    const E v = ld_cluster(&tab[c % a.P], uint32_t(c / a.P));
-                    if (k - beg < nm) { as -= v.x; ac -= v.y; }
-                    else              { as += v.x; ac += v.y; }
-                }
+                if (end > beg) {                                       // warp-uniform
+                    for (int k = beg + lane; k < end; k += 32) {
+                        const int c = a.ent[k];
+                        const E v = ld_cluster(&tab[c % a.P], uint32_t(c / a.P));
+                        if (k - beg < nm) { as -= v.x; ac -= v.y; }
+                        else              { as += v.x; ac += v.y; }
+                    }
 #pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    as += __shfl_xor_sync(0xffffffffu, as, o);
-                    ac += __shfl_xor_sync(0xffffffffu, ac, o);
+                    for (int o = 16; o; o >>= 1) {
+                        as += __shfl_xor_sync(0xffffffffu, as, o);
+                        ac += __shfl_xor_sync(0xffffffffu, ac, o);
+                    }
                 }
                 if (lane == 0) {
-                    const int J = a.node_comm[row];
-                    double acc_s, acc_c, s_i, c_i;
-                    const E own = tab[i];
-                    if constexpr (MODE == MODE_FP64) {
-                        // exact integer sums, rounded once
-                        acc_s = static_cast<double>(Tq[2 * J] + static_cast<long long>(as)) * a.inv_scale_q;
-                        acc_c = static_cast<double>(Tq[2 * J + 1] + static_cast<long long>(ac)) * a.inv_scale_q;
-                        s_i = static_cast<double>(own.x) * a.inv_scale_q;
-                        c_i = static_cast<double>(own.y) * a.inv_scale_q;
-                    } else {
-                        acc_s = static_cast<double>(Tq[2 * J]) * a.inv_scale_q + static_cast<double>(as);
-                        acc_c = static_cast<double>(Tq[2 * J + 1]) * a.inv_scale_q + static_cast<double>(ac);
-                        s_i = static_cast<double>(own.x);
-                        c_i = static_cast<double>(own.y);
-                    }
-                    const double sc = a.rscale ? a.rscale[row] : a.scale;
-                    const double f = a.omega[row] + sc * (c_i * acc_s - s_i * acc_c);
-                    if (st == 1) {
-                        a.krk[row] = f;
-                        a.Y[row] = a.y[row] + (0.5 * h) * f;
-                    } else if (st == 2) {
-                        a.krk[row] = a.krk[row] + 2.0 * f;
-                        a.Y[row] = a.y[row] + (0.5 * h) * f;
-                    } else if (st == 3) {
-                        a.krk[row] = a.krk[row] + 2.0 * f;
-                        a.Y[row] = a.y[row] + h * f;
-                    } else {
-                        a.y[row] = a.y[row] + (h / 6.0) * (a.krk[row] + f);
-                    }
+                    E v;
+                    v.x = as;
+                    v.y = ac;
+                    stash[i] = v;
+                }
+            }
+            __syncthreads();
+            // ---- FP64 epilogue and RK4 stage update of the own node
+            if (own) {
+                const E sum = stash[tid];
+                const E me = tab[tid];
+                double acc_s, acc_c, s_i, c_i;
+                if constexpr (MODE == MODE_FP64) {
+                    // exact integer sums, rounded once
+                    acc_s = static_cast<double>(Tq[2 * Jown] + static_cast<long long>(sum.x)) * a.inv_scale_q;
+                    acc_c = static_cast<double>(Tq[2 * Jown + 1] + static_cast<long long>(sum.y)) * a.inv_scale_q;
+                    s_i = static_cast<double>(me.x) * a.inv_scale_q;
+                    c_i = static_cast<double>(me.y) * a.inv_scale_q;
+                } else {
+                    acc_s = static_cast<double>(Tq[2 * Jown]) * a.inv_scale_q + static_cast<double>(sum.x);
+                    acc_c = static_cast<double>(Tq[2 * Jown + 1]) * a.inv_scale_q + static_cast<double>(sum.y);
+                    s_i = static_cast<double>(me.x);
+                    c_i = static_cast<double>(me.y);
+                }
+                const double f = om + sc * (c_i * acc_s - s_i * acc_c);
+                if (st == 1) {
+                    kv = f;
+                    Yv = yv + (0.5 * h) * f;
+                } else if (st == 2) {
+                    kv += 2.0 * f;
+                    Yv = yv + (0.5 * h) * f;
+                } else if (st == 3) {
+                    kv += 2.0 * f;
+                    Yv = yv + h * f;
+                } else {
+                    yv = yv + (h / 6.0) * (kv + f);
                 }
             }
             // every CTA is done reading the other slices and sums before they are overwritten
@@ -195,6 +210,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_small_rk4(SmallArgs a, dou
             __syncthreads();
         }
     }
+    if (own) a.y[row] = yv;
 }
 
 }  // namespace kura
