@@ -374,7 +374,7 @@ def bench_adjoint(dev):
     return out
 
 
-def bench_batch(dev, steps: int = 1000, tc_steps: int = 200):
+def bench_batch(dev, steps: int = 1000, tc_steps: int = 50):
     """2048 independent trajectories of uneven size in one persistent launch (half complete graphs, half SBMs),
     h = 0.01, mixed precision: the dense-block zeros as index lists (1000 steps), and as 0/1 masks multiplied
     on the tensor cores with split BF16 (sin, cos) (tc_steps steps)."""

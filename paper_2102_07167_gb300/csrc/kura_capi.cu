@@ -155,7 +155,8 @@ struct kura_ctx {
     DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
-        ad_tgt, ad_scratch, ad_absmax;
+        ad_tgt, ad_scratch, ad_absmax, ad_chunks, ad_chunk_ptr, ad_cpart;
+    int32_t ad_nchunks = 0;
     int64_t ad_M = 0, ad_nck = 0;
     int sym = -1;   // host CSR symmetric? (-1 unknown)
     DevMem y, Y, krk, fbuf, user, red, order_out;
@@ -1710,6 +1711,22 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         KCHECK(h, h->ad_part.alloc(8 * ((n + 255) / 256)), "alloc loss partials");
         KCHECK(h, h->ad_absmax.alloc(16), "alloc table maximum");        // [0] max |entry|, [2] ticket
         KCHECK(h, cudaMemsetAsync(h->ad_absmax.p, 0, 16, s), "zero the table maximum and the ticket");
+        // chunks of at most 256 nodes of one community each, communities in order (the stage kernel's CTAs)
+        {
+            std::vector<int4> chunks;
+            std::vector<int32_t> cptr(size_t(h->n_comm) + 1, 0);
+            for (int32_t J = 0; J < h->n_comm; J++) {
+                cptr[size_t(J)] = int32_t(chunks.size());
+                for (int64_t b = h->plan.comm_off[size_t(J)]; b < h->plan.comm_off[size_t(J) + 1]; b += 256)
+                    chunks.push_back(make_int4(J, int(b), int(std::min<int64_t>(b + 256, h->plan.comm_off[size_t(J) + 1])), 0));
+            }
+            cptr[size_t(h->n_comm)] = int32_t(chunks.size());
+            if (chunks.empty()) chunks.push_back(make_int4(0, 0, 0, 0));         // n = 0 cannot happen; keep a CTA
+            h->ad_nchunks = int32_t(chunks.size());
+            KCHECK(h, upload(h->ad_chunks, chunks, s), "upload adjoint chunks");
+            KCHECK(h, upload(h->ad_chunk_ptr, cptr, s), "upload adjoint chunk pointers");
+            KCHECK(h, h->ad_cpart.alloc(16 * chunks.size()), "alloc chunk sums");
+        }
         h->ad_M = M;
         h->ad_nck = nck;
         h->graphs.clear();                 // captured segments point at the old buffers
@@ -1792,10 +1809,10 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                 double* a_next = (st < 4) ? ((st % 2 == 1) ? h->ad_a0.as<double>() : h->ad_a1.as<double>()) : nullptr;
                 double* a_out = (st % 2 == 0) ? h->ad_a0.as<double>() : h->ad_a1.as<double>();
                 if (absmax) cudaMemsetAsync(absmax, 0, sizeof(unsigned int), q);
-                k_adj_prep_bsum<<<unsigned(std::max(h->n_comm, 1)), 256, 0, q>>>(
-                    ga, Ybuf + size_t(4 * t + st - 1) * n, lam, a_next, cl[st], ca[st], h->ad_w.as<double>(),
-                    h->ad_nu.as<double>(), h->ad_sc.as<float2>(), h->ad_gom.as<double>(), absmax,
-                    h->ad_bs.as<double2>(), ticket);
+                k_adj_prep_bsum<<<unsigned(h->ad_nchunks), 256, 0, q>>>(
+                    ga, h->ad_chunks.as<int4>(), h->ad_chunk_ptr.as<int32_t>(), Ybuf + size_t(4 * t + st - 1) * n, lam,
+                    a_next, cl[st], ca[st], h->ad_w.as<double>(), h->ad_nu.as<double>(), h->ad_sc.as<float2>(),
+                    h->ad_gom.as<double>(), absmax, h->ad_cpart.as<double2>(), h->ad_bs.as<double2>(), ticket);
                 if (absmax) k_adj_digits<<<nb, 256, 0, q>>>(ga, absmax);
                 AdjArgs adj{};
                 adj.fsums = Fbuf + size_t(4 * t + st - 1) * n;

@@ -855,6 +855,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     own.x = 0;
     own.y = 0;
     double om = 0.0, yv = 0.0, kv = 0.0, sc = 0.0;
+    // ST_ADJ: the stage's forward row sums, (sin, cos), nu, w, 1 / calM and the running adjoint sums
+    double2 a_fs = make_double2(0.0, 0.0);
+    float2 a_sc = make_float2(0.0f, 0.0f);
+    double a_nu = 0.0, a_w = 0.0, a_invm = 0.0, a_prev = 0.0;
     if (has_row) {
         rs0 = g.row_sub0[row];
         rs1 = g.row_sub0[row + 1];
@@ -864,6 +868,13 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             sc = g.rscale ? g.rscale[row] : g.scale;
             if (STAGE >= ST_1 && STAGE <= ST_4) yv = rk.y[row];
             if (STAGE >= ST_2 && STAGE <= ST_4) kv = rk.krk[row];
+        } else {
+            a_fs = adj.fsums[row];
+            a_sc = adj.sc[row];
+            a_nu = adj.nu[row];
+            a_w = adj.w[row];
+            a_invm = g.rinvdeg ? g.rinvdeg[row] : g.inv_n;
+            a_prev = adj.stage == 4 ? 0.0 : adj.asum[row];
         }
     }
     // TILE_TC: thread 32 w + l owns tile row 32 w + l = tensor-memory lane
@@ -909,19 +920,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         }
         if (STAGE == ST_ADJ) {
             // a = (J^T w)_m for symmetric A: c_m A(nu c)_m + s_m A(nu s)_m - nu_m (c_m (A c)_m + s_m (A s)_m)
-            const double2 fs = adj.fsums[row];
-            const float2 scv = adj.sc[row];
-            const double sj = static_cast<double>(scv.x), cj = static_cast<double>(scv.y);
-            const double nu = adj.nu[row];
+            const double2 fs = a_fs;
+            const double sj = static_cast<double>(a_sc.x), cj = static_cast<double>(a_sc.y);
+            const double nu = a_nu;
             const double a = cj * acc_c + sj * acc_s - nu * (cj * fs.y + sj * fs.x);
-            const double inv_m = g.rinvdeg ? g.rinvdeg[row] : g.inv_n;
-            gk_local += adj.w[row] * inv_m * (cj * fs.x - sj * fs.y);    // w . df/dK
+            gk_local += a_w * a_invm * (cj * fs.x - sj * fs.y);    // w . df/dK
             if (!isfinite(a)) atomicOr(g.err, ERR_NONFINITE);
             if (adj.stage > 1) {
                 adj.a_out[row] = a;
-                adj.asum[row] = (adj.stage == 4 ? 0.0 : adj.asum[row]) + a;
+                adj.asum[row] = a_prev + a;
             } else {
-                adj.lam[row] = adj.lam[row] + adj.asum[row] + a;
+                adj.lam[row] = adj.lam[row] + a_prev + a;
             }
         } else {
             const double f = om + sc * (ci * acc_s - si * acc_c);
@@ -1056,28 +1065,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_sum_partials(const double* __r
     if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// One CTA per community J (256 threads), fused per adjoint stage:
-//   - per node i of J: w_i = c_lam lambda_i + c_a a_next_i (the stage weight of the RK4 adjoint),
-//     nu_i = w_i K / calM_i, FP32 (sin, cos) of the FP64-reduced stage input, the table entry
-//     (nu sin, nu cos) that the row kernel's ST_ADJ pass gathers, and g_omega += w;
-//   - the FP64 block sums of that table over J in a fixed order (thread t takes nodes t, t + 256, ...,
-//     then a fixed tree), so the result does not depend on scheduling;
+// Fused per adjoint stage, one node per thread; CTA q takes chunk q = (community J, nodes [b, e)) of at
+// most 256 nodes (chunks follow the communities in order, chunk_ptr[J] .. chunk_ptr[J + 1] - 1 are J's):
+//   - node i: w_i = c_lam lambda_i + c_a a_next_i (the stage weight of the RK4 adjoint), nu_i = w_i K / calM_i,
+//     FP32 (sin, cos) of the FP64-reduced stage input, the table entry (nu sin, nu cos) that the row kernel's
+//     ST_ADJ pass gathers, and g_omega += w;
+//   - the chunk's FP64 sum of its table entries in a fixed tree order, into part[q];
 //   - the largest |table entry| (for the tensor-core digit scale), when absmax is given;
-//   - the last CTA to finish forms T_I = sum over the dense column blocks of I of the block sums and
-//     re-arms the ticket.
-__global__ void __launch_bounds__(256) k_adj_prep_bsum(DevGraph g, const double* __restrict__ Ys,
+//   - the last CTA to finish adds each community's chunk sums in chunk order (so the block sums do not
+//     depend on scheduling), forms T_I = sum over the dense column blocks of I, and re-arms the ticket.
+__global__ void __launch_bounds__(256) k_adj_prep_bsum(DevGraph g, const int4* __restrict__ chunks,
+                                                       const int32_t* __restrict__ chunk_ptr,
+                                                       const double* __restrict__ Ys,
                                                        const double* __restrict__ lam,
                                                        const double* __restrict__ a_next, double c_lam, double c_a,
                                                        double* __restrict__ w, double* __restrict__ nu,
                                                        float2* __restrict__ sc, double* __restrict__ g_omega,
-                                                       unsigned int* __restrict__ absmax, double2* __restrict__ bs,
-                                                       unsigned int* __restrict__ ticket)
+                                                       unsigned int* __restrict__ absmax, double2* __restrict__ part,
+                                                       double2* __restrict__ bs, unsigned int* __restrict__ ticket)
 {
-    const int J = blockIdx.x;
-    const int64_t b = g.comm_off[J], e = g.comm_off[J + 1];
+    const int4 ch = chunks[blockIdx.x];                     // (J, b, e, -)
+    const int64_t i = int64_t(ch.y) + threadIdx.x;
     double s_sum = 0.0, c_sum = 0.0;
     float amax = 0.0f;
-    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+    if (i < ch.z) {
         const double wi = c_lam * lam[i] + (a_next ? c_a * a_next[i] : 0.0);
         const double scale = g.rscale ? g.rscale[i] : g.scale;
         const double nui = wi * scale;
@@ -1094,9 +1105,9 @@ __global__ void __launch_bounds__(256) k_adj_prep_bsum(DevGraph g, const double*
                                        static_cast<float>(nui * static_cast<double>(c)));
         reinterpret_cast<float2*>(g.table)[i] = ent;
         g_omega[i] += wi;
-        s_sum += static_cast<double>(ent.x);
-        c_sum += static_cast<double>(ent.y);
-        amax = fmaxf(amax, fmaxf(fabsf(ent.x), fabsf(ent.y)));
+        s_sum = static_cast<double>(ent.x);
+        c_sum = static_cast<double>(ent.y);
+        amax = fmaxf(fabsf(ent.x), fabsf(ent.y));
     }
     if (absmax) {
         // non-negative floats order like their bit patterns
@@ -1116,17 +1127,27 @@ __global__ void __launch_bounds__(256) k_adj_prep_bsum(DevGraph g, const double*
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        bs[J] = make_double2(rs[0], rc[0]);
+        part[blockIdx.x] = make_double2(rs[0], rc[0]);
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
+    for (int J = threadIdx.x; J < g.n_comm; J += 256) {
+        double ts = 0.0, tc = 0.0;
+        for (int q = chunk_ptr[J]; q < chunk_ptr[J + 1]; q++) {
+            const double2 v = __ldcg(&part[q]);
+            ts += v.x;
+            tc += v.y;
+        }
+        bs[J] = make_double2(ts, tc);
+    }
+    __syncthreads();
     for (int I = threadIdx.x; I < g.n_comm; I += 256) {
         double ts = 0.0, tc = 0.0;
         for (int64_t q = g.dptr[I]; q < g.dptr[I + 1]; q++) {
-            const double2 v = __ldcg(&bs[g.dcol[q]]);
+            const double2 v = bs[g.dcol[q]];
             ts += v.x;
             tc += v.y;
         }
