@@ -64,10 +64,10 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA kernel sources: profile records made from other sources are stale."""
+    """Hash of the source of the row and trig kernels (kura_kernels.cuh): profile records made from other
+    sources are stale."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kura_kernels.cuh", "kura_capi.cu"):
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(CSRC, "kura_kernels.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
