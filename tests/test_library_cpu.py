@@ -336,6 +336,38 @@ def test_gather_rate_probe_rejects_bad_sizes():
     assert L.kura_measure_gather_rate(1 << 20, 1 << 20, 8, None, None) == kura.KURA_EINVAL
 
 
+def test_probes_and_batch_queries_reject_bad_arguments():
+    """Argument checks of the L2-bandwidth and launch-floor probes and of the batch queries run before any
+    CUDA call."""
+    import ctypes as C
+    L = kura.load()
+    r = C.c_double()
+    for nbytes in (0, (1 << 20) - 1, (1 << 30) + 1):
+        assert L.kura_measure_l2_bandwidth(nbytes, None, C.byref(r)) == kura.KURA_EINVAL
+    assert L.kura_measure_l2_bandwidth(1 << 24, None, None) == kura.KURA_EINVAL
+    for k, reps in ((0, 10), (4097, 10), (8, 0), (8, 100001)):
+        assert L.kura_measure_graph_launch_floor(k, reps, None, C.byref(r)) == kura.KURA_EINVAL
+    info = kura.KuraBatchInfo()
+    assert L.kura_batch_info(None, C.byref(info)) == kura.KURA_EINVAL
+    assert L.kura_batch_traj_params(None, 0, None, None, None) == kura.KURA_EINVAL
+
+
+def test_batch_create_rejects_bad_options_without_a_gpu():
+    """Option checks of kura_batch_create come before the device is touched."""
+    import ctypes as C
+    g = G.complete(8)
+    o = kura.kura_default_opts()
+    o.precision = kura.PREC_MIXED
+    o.row_lanes = 12
+    with pytest.raises(kura.KuraError) as e:
+        kura.kura_batch_create([(None, None, None, 1, np.zeros(8), 1.0)], o)
+    assert e.value.status == kura.KURA_EINVAL
+    o.row_lanes, o.tau = 0, 1.5
+    with pytest.raises(kura.KuraError) as e:
+        kura.kura_batch_create([(None, None, None, 1, np.zeros(8), 1.0)], o)
+    assert e.value.status == kura.KURA_EINVAL
+
+
 # ----------------------------------------------------------------------------- finite-valued matrices
 def _valued_case(seed, sizes=(40, 70, 25, 130), max_val=3, noise=0.25):
     rng = np.random.default_rng(seed)
