@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -292,6 +293,16 @@ void launch_row_stage(kura_ctx* h, const DevGraph& g, const RkArgs& rk, int stag
 template <int MODE>
 cudaError_t set_row_attrs(size_t smem)
 {
+    // The limit is a property of the kernel function on the device, shared by every handle: it only ever
+    // grows, so that a handle built later with a smaller plan cannot shrink it below what another live
+    // handle launches with.
+    static std::mutex mu;
+    static size_t granted[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = granted[MODE == MODE_MIXED ? 1 : 0][dev >= 0 && dev < 64 ? dev : 0];
+    if (smem <= cur) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     const void* fns[] = {(const void*)k_row_stage<MODE, ST_RHS>, (const void*)k_row_stage<MODE, ST_1>,
                          (const void*)k_row_stage<MODE, ST_2>, (const void*)k_row_stage<MODE, ST_3>,
@@ -300,6 +311,7 @@ cudaError_t set_row_attrs(size_t smem)
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
     }
+    cur = smem;
     return e;
 }
 

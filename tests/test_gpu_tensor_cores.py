@@ -201,3 +201,25 @@ def test_repeated_rhs_bitwise_identical_sbm_2p19(prec):
             k.sync()
             bad += int((out != first).sum())
     assert bad == 0
+
+
+def test_handles_with_different_plans_coexist(sbm_small):
+    """The row kernel's shared-memory limit is shared by every handle: after one handle is re-planned to a
+    smaller layout (the autotuner moving it to index lists), a second handle whose plan needs more shared
+    memory (tensor-core stages) still runs, and so does its own autotuning."""
+    w = sbm_small
+    g = w.graph
+    th = _dev(w.theta0)
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, w.theta0, w.K)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED,
+                       tensor_cores=2) as k1, \
+            kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED,
+                          tensor_cores=2) as k2:
+        k1.classify_blocks(0.5)
+        k1.autotune(th, budget_s=10.0)
+        f2 = _rhs(k2, w.theta0)
+        k2.autotune(th, budget_s=10.0)
+        f1 = _rhs(k1, w.theta0)
+    deg = np.diff(g.row_ptr)
+    check_rhs(f1, ref, deg, w.K, g.n, 1, "first handle")
+    check_rhs(f2, ref, deg, w.K, g.n, 1, "second handle")
