@@ -269,14 +269,16 @@ typedef struct {
  *   opts->precision  KURA_PREC_MIXED (1 <= n <= 16384 per trajectory) or
  *                    KURA_PREC_FP64 (1 <= n <= 8192: FP64 sin/cos, every sum
  *                    exact in 64-bit fixed point, FP64 epilogue and state)
- *   opts->tensor_cores (mixed only) the dense-block zeros of a community as a
- *                    0/1 mask multiplied on the tensor cores
+ *   opts->tensor_cores (mixed only) 2: the dense-block zeros of a community
+ *                    as a 0/1 mask multiplied on the tensor cores
  *                    (tcgen05.mma.kind::f16: BF16 mask, split BF16 hi + lo
- *                    (sin, cos), FP32 accumulation in tensor memory; the
- *                    dense columns must span <= 4096 columns): 0 never, 1
- *                    when the mask bits take fewer bytes than 4-byte index
- *                    lists would, 2 whenever possible.  With one graph per
- *                    trajectory the product has 4 useful columns (N = 16).
+ *                    (sin, cos), FP32 accumulation in tensor memory) wherever
+ *                    the dense columns span <= 4096 columns; 0 or 1: index
+ *                    lists.  With one graph per trajectory the product has 4
+ *                    useful columns (N = 16) and touches every entry of a
+ *                    dense block where the lists touch only its zeros, so the
+ *                    lists are the default; kura_autotune may choose either
+ *                    per size class.
  * On a batch handle kura_rk4_steps and kura_rhs take the phases (and the
  * right-hand side) of all trajectories concatenated in trajectory order
  * (user order within each); the other per-graph calls return KURA_ESTATE.

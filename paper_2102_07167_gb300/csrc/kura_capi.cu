@@ -2190,7 +2190,9 @@ kura_status kura_batch_create(int32_t n_traj, const kura_graph_desc* graphs, con
     std::vector<kura_graph_desc> gds(graphs, graphs + n_traj);
     BatchChoice c0;
     c0.tau = o.tau;
-    c0.tc = o.precision == KURA_PREC_FP64 ? 0 : o.tensor_cores;
+    // the mask product touches every entry of a dense block (the lists only its zeros): measured 15-17x
+    // slower on the batch workload, so only tensor_cores = 2 asks for it; the autotuner may still pick it
+    c0.tc = (o.precision == KURA_PREC_FP64 || o.tensor_cores != 2) ? 0 : 2;
     c0.lanes = o.row_lanes ? o.row_lanes : 32;
     std::vector<BatchChoice> ch(size_t(n_traj), c0);
     std::string err;
