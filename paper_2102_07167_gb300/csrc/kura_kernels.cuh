@@ -919,7 +919,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             ci = static_cast<double>(own.y);
         }
         if (STAGE == ST_ADJ) {
-            // a = (J^T w)_m for symmetric A: c_m A(nu c)_m + s_m A(nu s)_m - nu_m (c_m (A c)_m + s_m (A s)_m)
+            // a = (J^T w)_m = c_m B(nu c)_m + s_m B(nu s)_m - nu_m (c_m (A c)_m + s_m (A s)_m), where this pass
+            // runs over B = A^T (B = A for a symmetric A) and (A c, A s) are the forward row sums
             const double2 fs = a_fs;
             const double sj = static_cast<double>(a_sc.x), cj = static_cast<double>(a_sc.y);
             const double nu = a_nu;
