@@ -858,7 +858,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     // ST_ADJ: the stage's forward row sums, (sin, cos), nu, w, 1 / calM and the running adjoint sums
     double2 a_fs = make_double2(0.0, 0.0);
     float2 a_sc = make_float2(0.0f, 0.0f);
-    double a_nu = 0.0, a_w = 0.0, a_invm = 0.0, a_prev = 0.0;
+    double a_nu = 0.0, a_w = 0.0, a_invm = 0.0, a_prev = 0.0, a_lam = 0.0, a_gk = 0.0;
+    if (STAGE == ST_ADJ && tid == 0) a_gk = adj.gk_acc[blockIdx.x];      // this tile's dL/dK accumulator
     if (has_row) {
         rs0 = g.row_sub0[row];
         rs1 = g.row_sub0[row + 1];
@@ -875,6 +876,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             a_w = adj.w[row];
             a_invm = g.rinvdeg ? g.rinvdeg[row] : g.inv_n;
             a_prev = adj.stage == 4 ? 0.0 : adj.asum[row];
+            if (adj.stage == 1) a_lam = adj.lam[row];
         }
     }
     // TILE_TC: thread 32 w + l owns tile row 32 w + l = tensor-memory lane
@@ -931,7 +933,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 adj.a_out[row] = a;
                 adj.asum[row] = a_prev + a;
             } else {
-                adj.lam[row] = adj.lam[row] + a_prev + a;
+                adj.lam[row] = a_lam + a_prev + a;
             }
         } else {
             const double f = om + sc * (ci * acc_s - si * acc_c);
@@ -963,7 +965,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         if (tid == 0) {
             double v = 0.0;
             for (int q = 0; q < ROW_THREADS / 32; q++) v += gk_red[q];
-            adj.gk_acc[blockIdx.x] += v;
+            adj.gk_acc[blockIdx.x] = a_gk + v;
         }
     }
     if (tc) {
