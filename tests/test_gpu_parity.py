@@ -363,8 +363,8 @@ def test_long_horizon_mean_deviation_second_order():
     assert drift[1] < 1e-9 and drift[2] < 1e-9, drift
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_small_graph_cluster_step_loop_vs_oracle(prec):
+@pytest.mark.parametrize("prec,scaling", [(0, 0), (1, 0), (0, 1)])
+def test_small_graph_cluster_step_loop_vs_oracle(prec, scaling):
     """Small graphs run every RK4 step in one launch of one thread-block cluster (8 CTAs, the table spread over
     their shared memory): a 2000-node SBM with dense and sparse blocks (listed missing and present entries
     gathered across CTAs) and the complete graph, against the oracle and against the CUDA-graph step loop."""
@@ -372,17 +372,18 @@ def test_small_graph_cluster_step_loop_vs_oracle(prec):
     for w in cases:
         g = w.graph
         steps = 40
-        ref = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps)
+        ref = oracle.rk4_csr(g.row_ptr, g.col, w.omega, w.K, w.theta0, w.h, steps, scaling)
         out = {}
         for ps in (1, 0):
             with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec,
-                               persistent_small=ps) as k:
+                               persistent_small=ps, scaling=scaling) as k:
                 th = _dev(w.theta0)
                 k.rk4_steps(th, w.h, steps)
                 k.sync()
                 out[ps] = th.cpu().numpy()
         deg = np.diff(g.row_ptr)
-        bound = 1e-8 if prec == 0 else 2 * 1e-6 * w.K / g.n * (1 + deg.max()) * w.h * steps
+        calm = np.maximum(deg, 1) if scaling else g.n
+        bound = 1e-8 if prec == 0 else 2 * 1e-6 * np.max(w.K / calm * (1 + deg)) * w.h * steps
         for ps in (1, 0):
             assert np.abs(out[ps] - ref).max() <= bound, (w.name, ps, np.abs(out[ps] - ref).max(), bound)
         if prec == 0:
