@@ -124,6 +124,43 @@ def aggregate_replicas(el_ms_local: float, n: int, steps: int, dist=None, device
     return world * n * steps / (el / 1e3), el
 
 
+def aggregate_shards(el_ms_local: float, n_local: int, steps: int, dist=None, device=None):
+    """Shard runs: every rank integrates its own share of one batch.  Returns (value, max elapsed ms, total
+    oscillators): value = oscillator-steps of all ranks' shares / the slowest rank's time."""
+    import torch
+    el, n = float(el_ms_local), int(n_local)
+    if dist is not None and dist.is_initialized():
+        t = torch.tensor([el], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([n], dtype=torch.int64, device=device)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        el, n = float(t.item()), int(c.item())
+    return n * steps / (el / 1e3), el, n
+
+
+def timed_shards(run_steps, n_local: int, steps: int, warmup: int, barrier, timer, dist=None, device=None):
+    """The shard protocol: as timed_replicas, but each rank integrates a different share of the work."""
+    run_steps(max(warmup, 3))
+    barrier()
+    barrier()
+    t0 = timer.mark()
+    run_steps(steps)
+    t1 = timer.mark()
+    barrier()
+    return aggregate_shards(timer.ms(t0, t1), n_local, steps, dist, device)
+
+
+def shard_trajectories(graphs, world: int, rank: int, opts=None):
+    """This rank's trajectories of a batch split over `world` GPUs by the longest-processing-time rule on the
+    work-queue costs (kura_batch_costs, kura_partition_lpt).  Every rank computes the same partition from
+    the same graphs, so the split needs no communication.  Returns (indices of this rank's trajectories,
+    part of every trajectory, cost load of every part)."""
+    from paper_2102_07167_gb300 import kura
+    cost = kura.kura_batch_costs(graphs, opts)
+    part, load = kura.kura_partition_lpt(cost, world)
+    return np.flatnonzero(part == rank), part, load
+
+
 class EventTimer:
     """Marks on the current CUDA stream (CUDA events)."""
 
@@ -374,16 +411,43 @@ def bench_adjoint(dev):
     return out
 
 
-def bench_batch(dev, steps: int = 1000, tc_steps: int = 50):
+def bench_batch(dev, steps: int = 1000, tc_steps: int = 50, dist=None):
     """2048 independent trajectories of uneven size in one persistent launch (half complete graphs, half SBMs),
     h = 0.01, mixed precision: the dense-block zeros as index lists (1000 steps), and as 0/1 masks multiplied
-    on the tensor cores with split BF16 (sin, cos) (tc_steps steps)."""
+    on the tensor cores with split BF16 (sin, cos) (tc_steps steps).  With more than one rank, every rank
+    takes its LPT share of the trajectories and integrates it (index lists), with no collective in the
+    data path; the line is the whole batch's oscillator-steps over the slowest rank's time."""
     import torch
     from paper_2102_07167_gb300 import gen as G
     from paper_2102_07167_gb300 import kura
     t0 = time.perf_counter()
     ens = G.workload_batch()
     t_gen = time.perf_counter() - t0
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    if world > 1:
+        o = kura.kura_default_opts()
+        o.precision = kura.PREC_MIXED
+        rank = dist.get_rank()
+        mine, part, load = shard_trajectories(G.batch_graphs(ens), world, rank, o)
+        sub = [ens[int(t)] for t in mine]
+        theta0 = np.concatenate([th for (_, _, _, th, _) in sub])
+
+        def barrier():
+            dist.barrier()
+            torch.cuda.synchronize()
+
+        with kura.KuramotoBatch(G.batch_graphs(sub), tensor_cores=0) as b:
+            th = torch.tensor(theta0, device=dev)
+            value, el_ms, n_all = timed_shards(lambda k: b.rk4_steps(th, 0.01, k), theta0.size, steps, 3, barrier,
+                                               EventTimer(), dist, dev)
+        return {"workload": "2048 trajectories, n log-uniform in [256, 16384], half complete graphs, half SBMs "
+                            "(8-32 communities, p_in 0.9, p_out 0.005), K ~ U[0.5, 5], h = 0.01",
+                "n_total": n_all, "value": value, "unit": UNIT, "steps": steps, "ms_per_step": el_ms / steps,
+                "scaling": "strong", "sharding": {
+                    "ranks": world, "rule": "LPT on kura_batch_costs (kura_partition_lpt), no collective",
+                    "trajectories_per_rank": np.bincount(part, minlength=world).tolist(),
+                    "cost_per_rank": load.tolist(), "max_over_mean_cost": float(load.max() / load.mean())},
+                "precision": "mixed, index lists"}
     theta0 = np.concatenate([th for (_, _, _, th, _) in ens])
 
     def run(tcm, nsteps):
@@ -787,10 +851,14 @@ def run_ours(args):
         k2.close()
     if k is not None:
         k.close()
+    if not args.quick and not args.no_batch:
+        # every rank: with more than one, the batch is sharded across them (before the rank-0-only extras,
+        # so that no rank waits at a barrier while another runs them)
+        b = bench_batch(dev, dist=dist)
+        if rank == 0:
+            extra["batch"] = b
     if not args.quick and rank == 0 and not args.no_adjoint:
         extra["adjoint"] = bench_adjoint(dev)
-    if not args.quick and rank == 0 and not args.no_batch:
-        extra["batch"] = bench_batch(dev)
     if not args.quick and rank == 0 and not args.no_configs:
         extra["configs"] = {"complete_512": bench_complete_512(dev), "sbm_65536": bench_sbm_65536(dev)}
     if not args.quick and rank == 0 and not args.no_ensemble:

@@ -307,6 +307,28 @@ kura_status kura_batch_info(kura_t h, kura_batch_info_t* out);
  * 8); any output may be NULL. */
 kura_status kura_batch_traj_params(kura_t h, int32_t t, double* tau, int32_t* tensor_cores, int32_t* row_lanes);
 
+/* Host only (no device call): the cost the batch work queue would give each
+ * of n_traj trajectories under opts, the same per-node, listed-entry and
+ * tensor-core terms kura_batch_create sorts by.  Each trajectory is planned
+ * as kura_batch_create would plan it (opts->precision, opts->tau,
+ * opts->tensor_cores == 2); the planner's tile-size target uses the SM count
+ * of the current device, else 152.  cost: host array of n_traj doubles,
+ * caller-owned.  KURA_EINVAL for the trajectory errors of kura_batch_create
+ * (message in kura_last_error(NULL)). */
+kura_status kura_batch_costs(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, double* cost);
+
+/* Host only: longest-processing-time partition of n items over n_parts
+ * parts, the rule by which independent trajectories shard across GPUs with
+ * no collective.  Items are taken in decreasing cost (equal costs: lower
+ * index first) and each goes to the part with the least load so far (equal
+ * loads: lower part), so every process that calls it with the same costs
+ * gets the same partition; the largest load is at most the mean load plus
+ * the largest cost.  cost: n finite, non-negative doubles; part: n int32
+ * outputs in [0, n_parts); load: n_parts outputs (nullable).  Host arrays,
+ * caller-owned.  KURA_EINVAL for n < 0, n_parts < 1, NULL arrays or a
+ * negative or non-finite cost. */
+kura_status kura_partition_lpt(const double* cost, int32_t n, int32_t n_parts, int32_t* part, double* load);
+
 /* Replaces omega (nullable; n entries, user order, device or host) and/or
  * K (nullable). */
 kura_status kura_set_param(kura_t h, const double* omega, const double* K);

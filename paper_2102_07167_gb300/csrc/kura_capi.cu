@@ -8,9 +8,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -1981,6 +1983,61 @@ static kura_status batch_rk4_steps(kura_t h, double* theta, double step, int64_t
     return batch_launch(h, theta, theta, step, n_steps, false);
 }
 
+// Checks trajectory t of a batch and plans it with choice c: a complete graph
+// (NULL row_ptr) is one dense community with nothing stored, anything else
+// goes through the planner with tiles of one 128-row M-block.
+static kura_status plan_batch_traj(const kura_graph_desc& gd, int32_t t, const BatchChoice& c, bool fp64, Plan& p,
+                                   std::string& err)
+{
+    const int64_t max_n = fp64 ? BATCH_MAX_N_FP64 : BATCH_MAX_N;
+    if (gd.n < 1 || gd.n > max_n || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega || !std::isfinite(gd.K)) {
+        err = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(max_n) +
+              ", 1 <= n_comm <= " + std::to_string(BATCH_MAX_COMM) + ", omega and finite K";
+        return KURA_EINVAL;
+    }
+    if (gd.row_ptr == nullptr) {
+        if (gd.n_comm != 1) { err = "a complete-graph trajectory has n_comm = 1"; return KURA_EINVAL; }
+        p.n = gd.n;
+        p.n_comm = 1;
+        p.perm.resize(size_t(gd.n));
+        for (int64_t v = 0; v < gd.n; v++) p.perm[size_t(v)] = int32_t(v);
+        p.comm_off = {0, gd.n};
+        p.node_comm.assign(size_t(gd.n), 0);
+        p.dptr = {0, 1};
+        p.dcol = {0};
+        p.row_sub0.assign(size_t(gd.n) + 1, 0);      // no sub-rows: no stored corrections
+        return KURA_OK;
+    }
+    PlanInput in;
+    in.n_sms = current_sm_count();
+    in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
+    in.tau = c.tau;
+    in.tile_max_rows = TC_MBLOCK;     // a tensor-core tile is one 128-row M-block
+    in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
+    in.slot_ints = slot_ints_for(MODE_MIXED);
+    in.tensor_cores = fp64 ? 0 : c.tc;
+    std::string perr;
+    const int rc = build_plan(in, p, perr);
+    if (rc) { err = "trajectory " + std::to_string(t) + ": " + perr; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
+    return KURA_OK;
+}
+
+// The work-queue cost of a planned batch trajectory: per-node work, its listed
+// entries, and about 600 entries' worth per 64-column operand block of the
+// tensor-core tiles (expansion, barriers and MMA issue).
+static double batch_traj_cost(const Plan& p)
+{
+    int64_t listed = 0;
+    for (size_t sg = 0; sg < p.sub_hdr.size(); sg++) {
+        const int32_t* hdr = p.gstream.data() + p.sub_hdr[sg];
+        listed += hdr[1] + hdr[3];
+    }
+    double tc_cost = 0.0;
+    for (const Tile& tl : p.tiles)
+        if (tl.flags & TILE_TC) tc_cost += 1200.0 * double(tl.nsw);
+    return double(p.n) * 24.0 + double(listed) + tc_cost;
+}
+
 // (Re)builds the device data of batch handle h for the trajectories gds with
 // the per-trajectory plan choices ch (h->device, h->stream and h->opts set).
 static kura_status batch_build(kura_ctx* h, const std::vector<kura_graph_desc>& gds,
@@ -1988,7 +2045,6 @@ static kura_status batch_build(kura_ctx* h, const std::vector<kura_graph_desc>& 
 {
     const int32_t n_traj = int32_t(gds.size());
     const bool fp64 = h->opts.precision == KURA_PREC_FP64;
-    const int64_t max_n = fp64 ? BATCH_MAX_N_FP64 : BATCH_MAX_N;
     h->batch.reset(new BatchData());
     BatchData& B = *h->batch;
     B.n_traj = n_traj;
@@ -2004,38 +2060,8 @@ static kura_status batch_build(kura_ctx* h, const std::vector<kura_graph_desc>& 
     int64_t node_off = 0;
     for (int32_t t = 0; t < n_traj; t++) {
         const kura_graph_desc& gd = graphs[size_t(t)];
-        if (gd.n < 1 || gd.n > max_n || gd.n_comm < 1 || gd.n_comm > BATCH_MAX_COMM || !gd.omega ||
-            !std::isfinite(gd.K)) {
-            err = "trajectory " + std::to_string(t) + ": need 1 <= n <= " + std::to_string(max_n) +
-                             ", 1 <= n_comm <= " + std::to_string(BATCH_MAX_COMM) + ", omega and finite K";
-            return KURA_EINVAL;
-        }
         Plan p;
-        const bool complete = gd.row_ptr == nullptr;    // all-to-all: one dense community, nothing stored
-        if (complete) {
-            if (gd.n_comm != 1) { err = "a complete-graph trajectory has n_comm = 1"; return KURA_EINVAL; }
-            p.n = gd.n;
-            p.n_comm = 1;
-            p.perm.resize(size_t(gd.n));
-            for (int64_t v = 0; v < gd.n; v++) p.perm[size_t(v)] = int32_t(v);
-            p.comm_off = {0, gd.n};
-            p.node_comm.assign(size_t(gd.n), 0);
-            p.dptr = {0, 1};
-            p.dcol = {0};
-            p.row_sub0.assign(size_t(gd.n) + 1, 0);      // no sub-rows: no stored corrections
-        } else {
-            PlanInput in;
-            in.n_sms = current_sm_count();
-            in.n = gd.n; in.row_ptr = gd.row_ptr; in.col = gd.col; in.label = gd.label; in.n_comm = gd.n_comm;
-            in.tau = ch[size_t(t)].tau;
-            in.tile_max_rows = TC_MBLOCK;     // a tensor-core tile is one 128-row M-block
-            in.tile_max_sub = tile_max_sub_for(MODE_MIXED);
-            in.slot_ints = slot_ints_for(MODE_MIXED);
-            in.tensor_cores = fp64 ? 0 : ch[size_t(t)].tc;
-            std::string perr;
-            int rc = build_plan(in, p, perr);
-            if (rc) { err = "trajectory " + std::to_string(t) + ": " + perr; return rc == 2 ? KURA_ENOMEM : KURA_EINVAL; }
-        }
+        if (kura_status st = plan_batch_traj(gd, t, ch[size_t(t)], fp64, p, err)) return st;
         BatchTraj& tr = traj[size_t(t)];
         tr.tc0 = int32_t(tc_tiles.size());
         for (const Tile& tl : p.tiles) {
@@ -2091,11 +2117,7 @@ static kura_status batch_build(kura_ctx* h, const std::vector<kura_graph_desc>& 
             B.present += int64_t(pres.size());
         }
         row_off.push_back(pos);
-        // LPT cost: per-node work, listed entries, and about 600 entries' worth per 64-column operand
-        // block of the tensor-core tiles (expansion, barriers and MMA issue)
-        double tc_cost = 0.0;
-        for (int32_t q = tr.tc0; q < tr.tc1; q++) tc_cost += 1200.0 * double(tc_tiles[size_t(q)].nkb);
-        cost[size_t(t)] = double(gd.n) * 24.0 + double(pos) + tc_cost;
+        cost[size_t(t)] = batch_traj_cost(p);          // the LPT order of the work queue
         node_off += gd.n;
     }
     B.n_total = node_off;
@@ -2422,6 +2444,66 @@ kura_status kura_batch_info(kura_t h, kura_batch_info_t* out)
     out->tc_traj = B.tc_traj;
     out->tc_tiles = B.tc_tiles;
     out->tc_mask_bits = B.tc_mask_bits;
+    return KURA_OK;
+}
+
+kura_status kura_batch_costs(int32_t n_traj, const kura_graph_desc* graphs, const kura_opts* opts, double* cost)
+{
+    g_create_error.clear();
+    if (n_traj < 0 || (n_traj > 0 && (!graphs || !cost))) {
+        g_create_error = "n_traj must be non-negative, graphs and cost non-NULL";
+        return KURA_EINVAL;
+    }
+    kura_opts o;
+    kura_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != KURA_PREC_MIXED && o.precision != KURA_PREC_FP64) {
+        g_create_error = "unknown precision";
+        return KURA_EINVAL;
+    }
+    if (!(o.tau >= 0.0 && o.tau <= 1.0)) { g_create_error = "tau must be in [0, 1]"; return KURA_EINVAL; }
+    const bool fp64 = o.precision == KURA_PREC_FP64;
+    BatchChoice c;                               // the choice kura_batch_create starts from
+    c.tau = o.tau;
+    c.tc = (fp64 || o.tensor_cores != 2) ? 0 : 2;
+    for (int32_t t = 0; t < n_traj; t++) {
+        Plan p;
+        std::string err;
+        if (kura_status st = plan_batch_traj(graphs[t], t, c, fp64, p, err)) { g_create_error = err; return st; }
+        cost[t] = batch_traj_cost(p);
+    }
+    return KURA_OK;
+}
+
+kura_status kura_partition_lpt(const double* cost, int32_t n, int32_t n_parts, int32_t* part, double* load)
+{
+    g_create_error.clear();
+    if (n < 0 || n_parts < 1 || (n > 0 && (!cost || !part))) {
+        g_create_error = "need n >= 0, n_parts >= 1, cost and part non-NULL";
+        return KURA_EINVAL;
+    }
+    for (int32_t i = 0; i < n; i++)
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) {
+            g_create_error = "cost " + std::to_string(i) + " is negative or not finite";
+            return KURA_EINVAL;
+        }
+    std::vector<int32_t> order(static_cast<size_t>(n));
+    for (int32_t i = 0; i < n; i++) order[size_t(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    // least-loaded part first, lower part on equal loads
+    using Slot = std::pair<double, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int32_t q = 0; q < n_parts; q++) heap.push(Slot(0.0, q));
+    std::vector<double> acc(static_cast<size_t>(n_parts), 0.0);
+    for (int32_t i : order) {
+        const Slot s = heap.top();
+        heap.pop();
+        part[i] = s.second;
+        acc[size_t(s.second)] = s.first + cost[i];
+        heap.push(Slot(acc[size_t(s.second)], s.second));
+    }
+    if (load)
+        for (int32_t q = 0; q < n_parts; q++) load[q] = acc[size_t(q)];
     return KURA_OK;
 }
 

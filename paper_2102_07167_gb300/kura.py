@@ -132,6 +132,8 @@ def load() -> C.CDLL:
             "kura_batch_stats": (S, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
             "kura_batch_info": (S, [P, C.POINTER(KuraBatchInfo)]),
             "kura_batch_traj_params": (S, [P, I32, C.POINTER(D), C.POINTER(I32), C.POINTER(I32)]),
+            "kura_batch_costs": (S, [I32, C.POINTER(KuraGraphDesc), C.POINTER(KuraOpts), P]),
+            "kura_partition_lpt": (S, [P, I32, I32, P, P]),
             "kura_measure_l2_bandwidth": (S, [I64, P, C.POINTER(D)]),
             "kura_measure_graph_launch_floor": (S, [I32, I32, P, C.POINTER(D)]),
             "kura_plan_stats": (S, [P, C.POINTER(KuraBlockStats)]),
@@ -217,8 +219,9 @@ def kura_create(n, row_ptr, col, label, n_comm, omega, K, opts: Optional[KuraOpt
     return h
 
 
-def kura_batch_create(graphs, opts: Optional[KuraOpts] = None, stream=None):
-    """graphs: sequence of (row_ptr, col, label, n_comm, omega, K).  Returns (handle, node offsets)."""
+def _graph_descs(graphs):
+    """kura_graph_desc array of (row_ptr, col, label, n_comm, omega, K) tuples, the arrays it points into
+    (keep them alive) and the node offsets."""
     keep, descs, offs = [], [], [0]
     for (row_ptr, col, label, n_comm, omega, K) in graphs:
         om = np.ascontiguousarray(omega, dtype=np.float64)
@@ -234,14 +237,40 @@ def kura_batch_create(graphs, opts: Optional[KuraOpts] = None, stream=None):
             descs.append(KuraGraphDesc(n, rp.ctypes.data, cl.ctypes.data if cl.size else None, lb.ctypes.data,
                                        int(n_comm), om.ctypes.data, float(K)))
         offs.append(offs[-1] + n)
-    arr = (KuraGraphDesc * len(descs))(*descs)
+    return (KuraGraphDesc * len(descs))(*descs), keep, offs
+
+
+def kura_batch_create(graphs, opts: Optional[KuraOpts] = None, stream=None):
+    """graphs: sequence of (row_ptr, col, label, n_comm, omega, K).  Returns (handle, node offsets)."""
+    arr, keep, offs = _graph_descs(graphs)
     h = C.c_void_p()
     if opts is None:
         opts = kura_default_opts()
         opts.precision = PREC_MIXED
     s = _current_stream() if stream is None else int(stream)
-    _check(load().kura_batch_create(len(descs), arr, C.byref(opts), s or None, C.byref(h)), None)
+    _check(load().kura_batch_create(len(arr), arr, C.byref(opts), s or None, C.byref(h)), None)
     return h, np.array(offs, dtype=np.int64)
+
+
+def kura_batch_costs(graphs, opts: Optional[KuraOpts] = None) -> np.ndarray:
+    """Host only: the work-queue cost of each trajectory of a would-be batch (see kura_batch_create)."""
+    arr, keep, _ = _graph_descs(graphs)
+    cost = np.zeros(len(arr), dtype=np.float64)
+    _check(load().kura_batch_costs(len(arr), arr, C.byref(opts) if opts is not None else None,
+                                   cost.ctypes.data if cost.size else None), None)
+    return cost
+
+
+def kura_partition_lpt(cost, n_parts: int):
+    """Host only: longest-processing-time partition of items with these costs over n_parts parts.
+    Returns (part of each item, load of each part); the same costs give the same partition everywhere."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    part = np.zeros(c.size, dtype=np.int32)
+    load_ = np.zeros(max(int(n_parts), 0), dtype=np.float64)
+    _check(load().kura_partition_lpt(c.ctypes.data if c.size else None, int(c.size), int(n_parts),
+                                     part.ctypes.data if part.size else None,
+                                     load_.ctypes.data if load_.size else None), None)
+    return part, load_
 
 
 def kura_batch_stats(h):
