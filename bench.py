@@ -734,7 +734,8 @@ def run_ours(args):
                                       barrier, EventTimer(), dist, dev)
     launch_ms = k.kernel_times()
     ms_step = el_ms / args.steps
-    gpu_launches = 8 * args.steps + 2
+    # per 8-step graph: one trig/block-sum launch and 32 row kernels (the fused trig); two permutations
+    gpu_launches = 4 * args.steps + -(-args.steps // 8) + 2
 
     # ---- roofline of the dominant kernel (row kernel): algorithmic bytes / mean launch time
     peak, peak_kind = _peaks()

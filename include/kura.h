@@ -96,7 +96,13 @@ typedef struct {
      * shared memory and read through the cluster (not while kernel timing is
      * on); 0: always the CUDA-graph step loop */
     int32_t persistent_small;
-    int32_t reserved[2];
+    /* kura_rk4_steps on single handles: 1 (default) each RK4 stage's row
+     * kernel also makes the next stage's (sin, cos) table, digits and
+     * fixed-point block sums from the phases it writes, so a run of steps
+     * needs one trig/block-sum launch in all (bit-identical results); 0: a
+     * trig/block-sum launch before every stage */
+    int32_t fused_trig;
+    int32_t reserved;
 } kura_opts;
 
 typedef struct {
@@ -110,8 +116,11 @@ typedef struct {
     int64_t tiles, max_window;
     /* Algorithmic bytes of one right-hand-side evaluation, split by kernel:
      * stream_bytes = correction streams + per-row metadata read by the row
-     * kernel; node_bytes_row = per-node traffic of the row kernel in an RK4
-     * stage; node_bytes_trig = per-node traffic of the trig/block-sum kernel. */
+     * kernel (with opts.fused_trig and tensor-core tiles, plus the digit
+     * image it writes for the next stage); node_bytes_row = per-node traffic
+     * of the row kernel in an RK4 stage (with opts.fused_trig, plus the next
+     * stage's table entry); node_bytes_trig = per-node traffic of the
+     * trig/block-sum kernel. */
     int64_t stream_bytes, node_bytes_row, node_bytes_trig;
     int64_t direct_edges;            /* edges summed by the direct baseline */
     int64_t tc_tiles, tc_rows;       /* tiles (and their rows) whose zeros are a tensor-core mask */

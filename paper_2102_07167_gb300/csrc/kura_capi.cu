@@ -156,6 +156,7 @@ struct kura_ctx {
     DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig, dval, tcmask;
     bool valued = false;
     DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
+    DevMem table2, dig2, bsum4;               // fused trig: second table and digit image, 4 sum accumulators
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
         ad_tgt, ad_scratch, ad_absmax, ad_chunks, ad_chunk_ptr, ad_cpart;
@@ -271,6 +272,8 @@ void launch_trig(kura_ctx* h, const DevGraph& g, const double* theta_perm, int w
 {
     const unsigned nb = blocks_for(h->n, TRIG_THREADS);
     if (what == (TB_TABLE | TB_T)) k_trig_blocksum<MODE, TB_TABLE | TB_T><<<nb, TRIG_THREADS, 0, s>>>(g, theta_perm);
+    else if (what == (TB_TABLE | TB_KEEP))
+        k_trig_blocksum<MODE, TB_TABLE | TB_KEEP><<<nb, TRIG_THREADS, 0, s>>>(g, theta_perm);
     else k_trig_blocksum<MODE, 0><<<nb, TRIG_THREADS, 0, s>>>(g, theta_perm);
 }
 
@@ -342,6 +345,50 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
         if (h->opts.precision == KURA_PREC_MIXED) launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
         else launch_row_stage<MODE_FP64>(h, g, rk, st, s);
         if (ev) cudaEventRecordWithFlags(ev[2 * (st - 1) + 1], s, cudaEventRecordExternal);
+    }
+}
+
+// c RK4 steps enqueued on s; events (if any, 8 per step) bracket the row kernels.
+// With the fused trig (opts.fused_trig) one trig/block-sum launch makes the
+// first stage's table in buffer 0 and leaves its block sums in accumulator 0.
+// Stage st = 1..4 of every step then reads table buffer (st - 1) mod 2 and
+// accumulator st - 1; its row kernel writes the next stage's table into buffer
+// st mod 2 and its sums into accumulator st mod 4, and clears accumulator
+// (st + 1) mod 4, which no kernel of the stage touches.  Every step has four
+// stages, so the same buffers serve every step.
+void enqueue_rk4_steps(kura_ctx* h, double step, int64_t c, cudaStream_t s, cudaEvent_t* ev)
+{
+    if (!h->opts.fused_trig) {
+        for (int64_t k = 0; k < c; k++) enqueue_rk4_step(h, step, s, ev ? ev + 8 * k : nullptr);
+        return;
+    }
+    const bool mixed = h->opts.precision == KURA_PREC_MIXED;
+    const size_t nc2 = 2 * size_t(h->n_comm);
+    unsigned long long* acc = h->bsum4.as<unsigned long long>();
+    cudaMemsetAsync(acc, 0, 2 * nc2 * sizeof(unsigned long long), s);     // accumulators 0 and 1
+    DevGraph g = dev_graph(h);
+    DevGraph g0 = g;
+    g0.bsum = acc;
+    if (mixed) launch_trig<MODE_MIXED>(h, g0, h->y.as<double>(), TB_TABLE | TB_KEEP, s);
+    else launch_trig<MODE_FP64>(h, g0, h->y.as<double>(), TB_TABLE | TB_KEEP, s);
+    void* tables[2] = {h->table.p, h->table2.p};
+    uint8_t* digs[2] = {h->has_tc ? h->dig.as<uint8_t>() : nullptr, h->has_tc ? h->dig2.as<uint8_t>() : nullptr};
+    const RkArgs rk0 = rk_args(h, step);
+    for (int64_t k = 0; k < c; k++) {
+        for (int st = ST_1; st <= ST_4; st++) {
+            g.table = tables[(st - 1) % 2];
+            g.dig = digs[(st - 1) % 2];
+            RkArgs rk = rk0;
+            rk.next_table = tables[st % 2];
+            rk.next_dig = digs[st % 2];
+            rk.bsum_cur = acc + nc2 * size_t(st - 1);
+            rk.bsum_next = acc + nc2 * size_t(st % 4);
+            rk.bsum_zero = acc + nc2 * size_t((st + 1) % 4);
+            if (ev) cudaEventRecordWithFlags(ev[8 * k + 2 * (st - 1)], s, cudaEventRecordExternal);
+            if (mixed) launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
+            else launch_row_stage<MODE_FP64>(h, g, rk, st, s);
+            if (ev) cudaEventRecordWithFlags(ev[8 * k + 2 * (st - 1) + 1], s, cudaEventRecordExternal);
+        }
     }
 }
 
@@ -616,12 +663,19 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
         KCHECK(h, upload(h->rinvdeg, ri, s), "upload rinvdeg");
     }
     const size_t n = size_t(h->n), nc = size_t(h->n_comm);
-    KCHECK(h, h->table.alloc(esize * (n + 2)), "alloc table");
-    KCHECK(h, cudaMemsetAsync(h->table.p, 0, h->table.bytes, s), "memset table");
+    // two tables and digit images: with the fused trig a stage reads one and writes the other
+    for (DevMem* d : {&h->table, &h->table2}) {
+        KCHECK(h, d->alloc(esize * (n + 2)), "alloc table");
+        KCHECK(h, cudaMemsetAsync(d->p, 0, d->bytes, s), "memset table");
+    }
+    KCHECK(h, h->bsum4.alloc(4 * 16 * nc), "alloc the fused block-sum accumulators");
+    KCHECK(h, cudaMemsetAsync(h->bsum4.p, 0, h->bsum4.bytes, s), "memset the fused block-sum accumulators");
     if (h->has_tc) {
-        // digit image: one 4 KB block per 128 nodes; columns past n stay zero
-        KCHECK(h, h->dig.alloc(size_t((h->n + TC_KBLOCK - 1) / TC_KBLOCK) * TC_BBYTES), "alloc digit image");
-        KCHECK(h, cudaMemsetAsync(h->dig.p, 0, h->dig.bytes, s), "memset digit image");
+        // digit images: one 4 KB block per 128 nodes; columns past n stay zero
+        for (DevMem* d : {&h->dig, &h->dig2}) {
+            KCHECK(h, d->alloc(size_t((h->n + TC_KBLOCK - 1) / TC_KBLOCK) * TC_BBYTES), "alloc digit image");
+            KCHECK(h, cudaMemsetAsync(d->p, 0, d->bytes, s), "memset digit image");
+        }
         // mask images: every 128 x 128 block of mask bits (512 words) as 16 KB of FP8 operand
         const int64_t n_blocks = int64_t(p.bitmap.size()) / (TC_MBLOCK * 4);
         KCHECK(h, h->tcmask.alloc(size_t(n_blocks) * TC_ABYTES), "alloc mask images");
@@ -630,6 +684,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
         KCHECK(h, cudaGetLastError(), "expanding the masks");
     } else {
         h->dig.release();
+        h->dig2.release();
         h->tcmask.release();
     }
     KCHECK(h, h->bsum.alloc(16 * nc), "alloc bsum");
@@ -717,6 +772,7 @@ void kura_default_opts(kura_opts* o)
     o->tensor_cores = 1;
     o->bitmap_zmin = -1.0;
     o->persistent_small = 1;
+    o->fused_trig = 1;
 }
 
 int32_t kura_version(void) { return 100; }
@@ -850,10 +906,12 @@ kura_status kura_get_stats(kura_t h, kura_block_stats* s)
     s->tiles = h->n_tiles;
     s->max_window = h->max_wlen;
     const int64_t esize = h->opts.precision == KURA_PREC_MIXED ? 8 : 16;
-    // algorithmic bytes: 4 B per listed index, a 16 B header per sub-row, the row bitmaps
-    s->stream_bytes = h->stream_bytes;
-    // row kernel per node: omega, y, krk (read+write), Y (write) or y (write), own entry
-    s->node_bytes_row = (8 + 8 + 16 + 8 + esize) * h->n;
+    // algorithmic bytes: 4 B per listed index, a 16 B header per sub-row, the row bitmaps, the
+    // tensor-core operands; with the fused trig also the next stage's digit image (32 B per node)
+    s->stream_bytes = h->stream_bytes + (h->opts.fused_trig && h->has_tc ? 32 * h->n : 0);
+    // row kernel per node: omega, y, krk (read+write), Y (write) or y (write), own entry, and with
+    // the fused trig the next stage's table entry
+    s->node_bytes_row = (8 + 8 + 16 + 8 + esize + (h->opts.fused_trig ? esize : 0)) * h->n;
     // trig kernel per node: theta read, table write, community id
     s->node_bytes_trig = (8 + esize + 4) * h->n;
     s->direct_edges = h->nnz - p.self_loops;
@@ -1117,9 +1175,10 @@ kura_status kura_rk4_steps(kura_t h, double* theta, double step, int64_t n_steps
             }
             cudaGraph_t graph = nullptr;
             KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            for (int64_t k = 0; k < c; k++) {
-                if (h->ens) enqueue_ens_step(h, step, h->cap);
-                else enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            if (h->ens) {
+                for (int64_t k = 0; k < c; k++) enqueue_ens_step(h, step, h->cap);
+            } else {
+                enqueue_rk4_steps(h, step, c, h->cap, h->timing ? ge->events.data() : nullptr);
             }
             cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
             if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");
@@ -1402,9 +1461,10 @@ static kura_status run_steps_perm(kura_t h, double step, int64_t n_steps)
             }
             cudaGraph_t graph = nullptr;
             KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            for (int64_t k = 0; k < c; k++) {
-                if (h->ens) enqueue_ens_step(h, step, h->cap);
-                else enqueue_rk4_step(h, step, h->cap, h->timing ? ge->events.data() + 8 * k : nullptr);
+            if (h->ens) {
+                for (int64_t k = 0; k < c; k++) enqueue_ens_step(h, step, h->cap);
+            } else {
+                enqueue_rk4_steps(h, step, c, h->cap, h->timing ? ge->events.data() : nullptr);
             }
             cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
             if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture");

@@ -55,12 +55,20 @@ __host__ __device__ constexpr int tc_digit_offset(int d, int c) { return d * 128
 enum : int { MODE_FP64 = 0, MODE_MIXED = 1 };
 enum : int { ST_RHS = 0, ST_1 = 1, ST_2 = 2, ST_3 = 3, ST_4 = 4, ST_ADJ = 5 };
 enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
-enum : int { TB_TABLE = 1, TB_T = 2 };   // what k_trig_blocksum writes
+// what k_trig_blocksum does: write the table (and digits), form T_I; TB_KEEP leaves the
+// block sums in the accumulators for the first fused row kernel (no T, no re-zeroing)
+enum : int { TB_TABLE = 1, TB_T = 2, TB_KEEP = 4 };
 
 // 2 pi split in two doubles (Cody-Waite style): hi = nearest double, lo = remainder
 #define KURA_TWO_PI_HI 6.283185307179586232
 #define KURA_TWO_PI_LO 2.4492935982947064e-16
 #define KURA_INV_TWO_PI 0.15915494309189533577
+// 2^64 / (2 pi) = 2^63 / pi = 2935890503282001226.496..., rounded: one turn of phase is 2^64 units of a
+// 64-bit fixed-point fraction
+#define KURA_TURN_Q64 0x28BE60DB9391054Aull
+// 2 pi 2^-32 and 2 pi 2^-64 (FP32)
+#define KURA_TWO_PI_2M32 1.46291807926715968e-09f
+#define KURA_TWO_PI_2M64 3.40612158008655459e-19f
 
 template <int MODE> struct EntryT;
 template <> struct EntryT<MODE_FP64> { using T = longlong2; using A = long long; };   // fixed-point (sin, cos)
@@ -107,6 +115,15 @@ struct RkArgs {
     double* out;          // ST_RHS: f
     double2* sums_out;    // nullable: row sums sum_l A_ml (sin th_l, cos th_l) of the stage
     double h;
+    // Fused trig (forward stages ST_1..ST_4 of the step loop; next_table non-null): the CTA
+    // forms T_I of its community from the finished block sums bsum_cur, CTA 0 zeroes bsum_zero,
+    // and the epilogue writes the table entry (next_table), digits (next_dig, when non-null) and
+    // fixed-point block sums (bsum_next) of the phase it writes, for the next stage.
+    void* next_table;
+    uint8_t* next_dig;
+    const unsigned long long* bsum_cur;
+    unsigned long long* bsum_next;
+    unsigned long long* bsum_zero;
 };
 
 // Adjoint stage s of the discrete RK4 adjoint (ST_ADJ): the table holds
@@ -308,6 +325,64 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// The table entry of phase th and its fixed-point values (round(sin th 2^q),
+// round(cos th 2^q)): FP64 sincos (FP64), or FP32 sincosf of th reduced mod
+// 2 pi in FP64 (mixed; the fixed point then holds the FP32 values exactly).
+// The trig kernel and the fused row-kernel epilogue both use it, so the two
+// produce the same bits.
+// Phase th with 2^-10 <= |th| < 2^21 reduced mod 2 pi to r in [-pi, pi] in FP32, with no FP64
+// arithmetic (the FP64 pipe runs at about 1/70 of FP32 on this part).  th = m 2^e with a 53-bit
+// integer m, so th / (2 pi) mod 1 in 64-bit fixed point is bits [64 - s, 128 - s) of the 117-bit
+// product m KURA_TURN_Q64, s = e + 64 in [2, 32] (Payne and Hanek's reduction by a multiple-precision
+// 1 / (2 pi), here a single 64-bit word; its rounding moves the result by at most |th| 2^-65 turns,
+// below 2^-44 turns in this range).  The fraction's two's complement value in turns, times 2 pi, is r,
+// formed in FP32 from its two 32-bit halves (within about one FP32 ulp of r).
+__device__ __forceinline__ float reduce_turn_fx(double th)
+{
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(th));
+    const int s = int((bits >> 52) & 0x7FFu) - 1075 + 64;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long lo = m * KURA_TURN_Q64, hi = __umul64hi(m, KURA_TURN_Q64);
+    unsigned long long f = (hi << s) | (lo >> (64 - s));
+    if (bits >> 63) f = 0ull - f;
+    const long long fs = static_cast<long long>(f);
+    const float a = __int2float_rn(static_cast<int>(fs >> 32));
+    const float b = __uint2float_rn(static_cast<unsigned>(fs & 0xFFFFFFFFll));
+    return fmaf(a, KURA_TWO_PI_2M32, b * KURA_TWO_PI_2M64);
+}
+
+template <int MODE>
+__device__ __forceinline__ void node_entry(double th, double scale_q, long long& sf, long long& cf, float2& tab32)
+{
+    if (MODE == MODE_FP64) {
+        double s, c;
+        sincos(th, &s, &c);
+        sf = __double2ll_rn(s * scale_q);
+        cf = __double2ll_rn(c * scale_q);
+    } else {
+        // reduce mod 2 pi (in fixed point, or in FP64 outside 2^-10 <= |th| < 2^21), then FP32
+        // sin/cos of |r| <= pi
+        const int ex = int((static_cast<unsigned long long>(__double_as_longlong(th)) >> 52) & 0x7FFu);
+        float r;
+        if (ex >= 1023 - 10 && ex < 1023 + 21) {
+            r = reduce_turn_fx(th);
+        } else {
+            const double k = rint(th * KURA_INV_TWO_PI);
+            double rd = fma(-k, KURA_TWO_PI_HI, th);
+            rd = fma(-k, KURA_TWO_PI_LO, rd);
+            r = static_cast<float>(rd);
+        }
+        sincosf(r, &tab32.x, &tab32.y);
+        const float sq = static_cast<float>(scale_q);
+        sf = f32_to_ll_rn(tab32.x * sq);
+        cf = f32_to_ll_rn(tab32.y * sq);
+    }
+}
+__device__ __forceinline__ bool phase_nonfinite(double th)
+{
+    return (__double_as_longlong(th) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
 // ---------------------------------------------------------------- trig + block sums
 // One node per thread.  Writes the (sin, cos) table (TB_TABLE), accumulates
 // the fixed-point block sums with warp-aggregated 64-bit integer atomics
@@ -325,22 +400,8 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
     float2 tab32 = make_float2(0.0f, 0.0f);
     if (i < g.n) {
         const double th = theta[i];
-        if ((__double_as_longlong(th) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) atomicOr(g.err, ERR_NONFINITE);
-        if (MODE == MODE_FP64) {
-            double s, c;
-            sincos(th, &s, &c);
-            sf = __double2ll_rn(s * g.scale_q);
-            cf = __double2ll_rn(c * g.scale_q);
-        } else {
-            // reduce mod 2 pi in FP64, then FP32 sin/cos of |r| <= pi
-            const double k = rint(th * KURA_INV_TWO_PI);
-            double r = fma(-k, KURA_TWO_PI_HI, th);
-            r = fma(-k, KURA_TWO_PI_LO, r);
-            sincosf(static_cast<float>(r), &tab32.x, &tab32.y);
-            const float sq = static_cast<float>(g.scale_q);
-            sf = f32_to_ll_rn(tab32.x * sq);
-            cf = f32_to_ll_rn(tab32.y * sq);
-        }
+        if (phase_nonfinite(th)) atomicOr(g.err, ERR_NONFINITE);
+        node_entry<MODE>(th, g.scale_q, sf, cf, tab32);
         J = g.node_comm[i];
     }
     // block sums first: the fence that orders them before the CTA's ticket then
@@ -362,7 +423,7 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
         atomicAdd(&g.bsum[2 * J], static_cast<unsigned long long>(sf));
         atomicAdd(&g.bsum[2 * J + 1], static_cast<unsigned long long>(cf));
     }
-    __threadfence();
+    if (!(WHAT & TB_KEEP)) __threadfence();
     if ((WHAT & TB_TABLE) && i < g.n) {
         if (MODE == MODE_FP64) reinterpret_cast<longlong2*>(g.table)[i] = make_longlong2(sf, cf);
         else reinterpret_cast<float2*>(g.table)[i] = tab32;
@@ -380,6 +441,7 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
                 reinterpret_cast<uint4*>(g.dig + b * TC_BBYTES)[q & 255] = reinterpret_cast<const uint4*>(dstage)[q];
         }
     }
+    if (WHAT & TB_KEEP) return;          // the sums stay for the first fused row kernel
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(g.counter, 1u) == gridDim.x - 1);
@@ -529,6 +591,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     __shared__ int issued[ROW_SLOTS], b_issued[TC_NB], a_issued[TC_NA];
     __shared__ int2 slot_meta[ROW_SLOTS];        // (first sub-row relative to the tile, sub-rows) of the slot's group
     __shared__ uint32_t tmem_base;
+    __shared__ long long t_fx[2];                // fused trig: T_I of the tile's community, fixed point
+    constexpr bool FWD = STAGE >= ST_1 && STAGE <= ST_4;
+    const bool fused = FWD && rk.next_table != nullptr;
 
     int32_t* ring = reinterpret_cast<int32_t*>(smem_raw);
     // window at win[0, wlen), preceded by 16 bytes holding a zero entry at win[-1]
@@ -603,6 +668,23 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 bulk_g2s(ring + size_t(sl) * SLOT, g.gstream + G.off, bytes, &full_bar[sl]);
                 issued[sl] = fill + 1;
             }
+        } else if (fused) {
+            // fused trig: T_I of this tile's community from the finished fixed-point block sums
+            // (integer sums, so the order does not matter), and CTA 0 clears the accumulators
+            // that the stage after next adds into
+            if (lane == 1) {
+                long long ts = 0, tcs = 0;
+                for (int64_t k = g.dptr[t.comm]; k < g.dptr[t.comm + 1]; k++) {
+                    const int Jd = g.dcol[k];
+                    const long long bv = g.dval ? g.dval[k] : 1;      // the block's prevalent value
+                    ts += bv * static_cast<long long>(__ldcg(rk.bsum_cur + 2 * Jd));
+                    tcs += bv * static_cast<long long>(__ldcg(rk.bsum_cur + 2 * Jd + 1));
+                }
+                t_fx[0] = ts;
+                t_fx[1] = tcs;
+            }
+            if (blockIdx.x == 0)
+                for (int q = lane - 1; q < 2 * g.n_comm; q += 31) rk.bsum_zero[q] = 0ull;
         }
     } else if (warp == TC_WARP) {
         // ---------------- tensor cores: lane 0 streams the mask blocks (FP8 operand images
@@ -854,7 +936,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
     E own;
     own.x = 0;
     own.y = 0;
-    double om = 0.0, yv = 0.0, kv = 0.0, sc = 0.0;
+    double om = 0.0, yv = 0.0, kv = 0.0, sc = 0.0, ynew = 0.0;
     // ST_ADJ: the stage's forward row sums, (sin, cos), nu, w, 1 / calM and the running adjoint sums
     double2 a_fs = make_double2(0.0, 0.0);
     float2 a_sc = make_float2(0.0f, 0.0f);
@@ -908,13 +990,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
         }
         double acc_s, acc_c, si, ci;
         if (MODE == MODE_FP64) {
-            const longlong2 T = reinterpret_cast<const longlong2*>(g.T)[t.comm];
+            const longlong2 T = fused ? make_longlong2(t_fx[0], t_fx[1]) : reinterpret_cast<const longlong2*>(g.T)[t.comm];
             acc_s = static_cast<double>(T.x + static_cast<long long>(sa) - ms_s) * g.inv_scale_q;
             acc_c = static_cast<double>(T.y + static_cast<long long>(sc_) - ms_c) * g.inv_scale_q;
             si = static_cast<double>(own.x) * g.inv_scale_q;
             ci = static_cast<double>(own.y) * g.inv_scale_q;
         } else {
-            const double2 T = reinterpret_cast<const double2*>(g.T)[t.comm];
+            const double2 T = fused ? make_double2(static_cast<double>(t_fx[0]) * g.inv_scale_q,
+                                                   static_cast<double>(t_fx[1]) * g.inv_scale_q)
+                                    : reinterpret_cast<const double2*>(g.T)[t.comm];
             acc_s = T.x + static_cast<double>(sa) - static_cast<double>(ms_s) * dig_inv;
             acc_c = T.y + static_cast<double>(sc_) - static_cast<double>(ms_c) * dig_inv;
             si = static_cast<double>(own.x);
@@ -943,16 +1027,52 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
                 rk.out[row] = f;
             } else if (STAGE == ST_1) {
                 rk.krk[row] = f;
-                rk.Y[row] = yv + (0.5 * rk.h) * f;
+                ynew = yv + (0.5 * rk.h) * f;
+                rk.Y[row] = ynew;
             } else if (STAGE == ST_2) {
                 rk.krk[row] = kv + 2.0 * f;
-                rk.Y[row] = yv + (0.5 * rk.h) * f;
+                ynew = yv + (0.5 * rk.h) * f;
+                rk.Y[row] = ynew;
             } else if (STAGE == ST_3) {
                 rk.krk[row] = kv + 2.0 * f;
-                rk.Y[row] = yv + rk.h * f;
+                ynew = yv + rk.h * f;
+                rk.Y[row] = ynew;
             } else {
-                rk.y_out[row] = yv + (rk.h / 6.0) * (kv + f);
+                ynew = yv + (rk.h / 6.0) * (kv + f);
+                rk.y_out[row] = ynew;
             }
+        }
+    }
+    if (fused) {
+        // fused trig: the next stage's table entry, digits and block sums of the phase just written
+        // (the digit bytes go straight to the image: staging them in shared memory for 16-byte stores
+        // measured slower, since it lengthens every CTA's epilogue)
+        long long sf = 0, cf = 0;
+        if (has_row) {
+            float2 tab32 = make_float2(0.0f, 0.0f);
+            if (phase_nonfinite(ynew)) atomicOr(g.err, ERR_NONFINITE);
+            node_entry<MODE>(ynew, g.scale_q, sf, cf, tab32);
+            if (MODE == MODE_FP64) reinterpret_cast<longlong2*>(rk.next_table)[row] = make_longlong2(sf, cf);
+            else reinterpret_cast<float2*>(rk.next_table)[row] = tab32;
+            if (rk.next_dig) tc_write_digits(rk.next_dig, row, sf, cf);
+        }
+        // every row of a tile lies in community t.comm: one pair of atomics per CTA
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sf += __shfl_xor_sync(0xffffffffu, sf, o);
+            cf += __shfl_xor_sync(0xffffffffu, cf, o);
+        }
+        __shared__ long long nb_red[2][ROW_THREADS / 32];
+        if (lane == 0) {
+            nb_red[0][warp] = sf;
+            nb_red[1][warp] = cf;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long a = 0, b = 0;
+            for (int q = 0; q < ROW_THREADS / 32; q++) { a += nb_red[0][q]; b += nb_red[1][q]; }
+            atomicAdd(&rk.bsum_next[2 * t.comm], static_cast<unsigned long long>(a));
+            atomicAdd(&rk.bsum_next[2 * t.comm + 1], static_cast<unsigned long long>(b));
         }
     }
     if (STAGE == ST_ADJ) {

@@ -43,7 +43,8 @@ class KuraError(RuntimeError):
 class KuraOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scaling", C.c_int32), ("tau", C.c_double),
                 ("keep_host_csr", C.c_int32), ("tensor_cores", C.c_int32), ("bitmap_zmin", C.c_double),
-                ("row_lanes", C.c_int32), ("persistent_small", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("row_lanes", C.c_int32), ("persistent_small", C.c_int32), ("fused_trig", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class KuraBlockStats(C.Structure):
@@ -548,7 +549,7 @@ class Kuramoto:
 
     def __init__(self, row_ptr, col, label, n_comm, omega, K, precision=PREC_FP64,
                  scaling=SCALING_UNIFORM, tau=0.5, keep_host_csr=True, stream=None, bitmap_zmin=None,
-                 tensor_cores=None, val=None, persistent_small=None):
+                 tensor_cores=None, val=None, persistent_small=None, fused_trig=None):
         self.n = int(np.asarray(row_ptr).shape[0] - 1)
         self.n_comm = int(n_comm)
         o = kura_default_opts()
@@ -559,6 +560,8 @@ class Kuramoto:
             o.tensor_cores = int(tensor_cores)
         if persistent_small is not None:
             o.persistent_small = int(persistent_small)
+        if fused_trig is not None:
+            o.fused_trig = int(fused_trig)
         if val is not None:
             self.h = kura_create_valued(self.n, row_ptr, col, val, label, n_comm, omega, K, o, stream)
         else:

@@ -34,6 +34,25 @@ def _rhs_gpu(sysk, theta):
     return out.cpu().numpy()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_phases_across_the_reduction_ranges(prec):
+    """Mixed mode reduces a phase mod 2 pi in 64-bit fixed point for 2^-10 <= |theta| < 2^21 and in FP64
+    outside: phases of both signs from 1e-5 to 1e7 rad, the boundaries 2^-10 and 2^21 included, give the
+    oracle's right-hand side within the stated bounds (FP64 mode as a control)."""
+    w = G.workload_sbm_small(n=12000, n_comm=12, min_size=128, seed=3)
+    g = w.graph
+    rng = np.random.default_rng(21)
+    theta = rng.choice([-1.0, 1.0], g.n) * 10.0 ** rng.uniform(-5, 7, g.n)
+    edges = np.array([2.0**-10, np.nextafter(2.0**-10, 0), 2.0**21, np.nextafter(2.0**21, 0), 0.0, np.pi,
+                      2 * np.pi, 1e6 * np.pi])
+    theta[:edges.size] = edges
+    theta[edges.size:2 * edges.size] = -edges
+    ref = oracle.rhs_csr(g.row_ptr, g.col, w.omega, theta, w.K)
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=prec) as k:
+        f = _rhs_gpu(k, theta)
+    check_rhs(f, ref, np.diff(g.row_ptr), w.K, g.n, prec, "phases across the reduction ranges")
+
+
 @pytest.fixture(scope="module")
 def sbm_small():
     return G.workload_sbm_small(n=12000, n_comm=12, min_size=128, seed=3)

@@ -223,3 +223,32 @@ def test_handles_with_different_plans_coexist(sbm_small):
     deg = np.diff(g.row_ptr)
     check_rhs(f1, ref, deg, w.K, g.n, 1, "first handle")
     check_rhs(f2, ref, deg, w.K, g.n, 1, "second handle")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("tcm", [0, 2])
+@pytest.mark.parametrize("which", ["ragged", "sbm_small"])
+def test_fused_trig_bit_identical_to_a_trig_launch_per_stage(which, tcm, prec, ragged, sbm_small):
+    """kura_rk4_steps with the fused trig (each stage's row kernel makes the next stage's table, digits and
+    block sums; one trig launch per run) gives the same bits as a trig/block-sum launch before every stage:
+    index lists and tensor-core digits, partial 128-node digit blocks (ragged sizes), 11 steps (an 8-step
+    graph and a 3-step one), and the FP64 result stays within 1e-8 of the oracle's trajectory."""
+    if which == "ragged":
+        g = ragged
+        rng = np.random.default_rng(4)
+        omega, theta, K = rng.normal(size=g.n), rng.uniform(0, 2 * np.pi, g.n), 2.5
+    else:
+        w = sbm_small
+        g, omega, theta, K = w.graph, w.omega, w.theta0, w.K
+    out = {}
+    for fused in (1, 0):
+        with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, omega, K, precision=prec, tensor_cores=tcm,
+                           persistent_small=0, fused_trig=fused) as k:
+            assert (k.stats()["tc_tiles"] > 0) == (tcm == 2)
+            out[fused] = _traj(k, theta, 0.01, 11)
+            # a later call starts from the state the last one left
+            out[fused] = np.concatenate([out[fused], _traj(k, out[fused], 0.01, 2)])
+    assert np.array_equal(out[1], out[0])
+    if prec == 0:
+        ref = oracle.rk4_csr(g.row_ptr, g.col, omega, K, theta, 0.01, 11)
+        assert np.max(np.abs(out[1][:g.n] - ref)) < 1e-8

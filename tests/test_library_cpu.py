@@ -503,3 +503,17 @@ def test_fp32_split_rounding_equals_round_half_even():
         x = np.float32(v * np.float32(2.0**q))        # the kernel's FP32 product
         want = int(np.rint(np.float64(x)))           # round half to even of the same float32 value
         assert _f32_to_ll_rn_split(x) == want, v
+
+
+def test_fixed_point_turn_constants_match_pi():
+    """The mixed-mode phase reduction multiplies by round(2^64 / (2 pi)) and scales by 2 pi 2^-32 and
+    2 pi 2^-64 in FP32: the constants in the kernel source against a 60-digit pi."""
+    import os
+    import re
+    sp = pytest.importorskip("sympy")
+    src = open(os.path.join(os.path.dirname(kura.__file__), "csrc", "kura_kernels.cuh")).read()
+    q64 = int(re.search(r"#define KURA_TURN_Q64 (0x[0-9A-Fa-f]+)ull", src).group(1), 16)
+    assert q64 == int(sp.floor(sp.Integer(2) ** 63 / sp.pi + sp.Rational(1, 2)))
+    for name, e in (("KURA_TWO_PI_2M32", -32), ("KURA_TWO_PI_2M64", -64)):
+        v = float(re.search(rf"#define {name} ([0-9.e+-]+)f", src).group(1))
+        assert np.float32(v) == np.float32(float(sp.N(2 * sp.pi * sp.Integer(2) ** e, 40)))
