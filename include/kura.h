@@ -61,9 +61,10 @@ enum { KURA_SCALING_UNIFORM = 0, KURA_SCALING_DEGREE = 1 };
 typedef struct {
     /* KURA_PREC_FP64: FP64 sin/cos, per-edge sums exact in 64-bit fixed
      *   point, FP64 epilogue and state.
-     * KURA_PREC_MIXED: FP32 sin/cos of the phase reduced mod 2 pi in FP64,
-     *   FP32 per-edge corrections, block sums exact in fixed point and
-     *   rounded once to FP64, FP64 epilogue and state. */
+     * KURA_PREC_MIXED: FP32 sin/cos of the phase reduced mod 2 pi (in 64-bit
+     *   fixed point for 2^-10 <= |theta| < 2^21, else in FP64), FP32
+     *   per-edge corrections, block sums exact in fixed point and rounded
+     *   once to FP64, FP64 epilogue and state. */
     int32_t precision;
     /* calM_m of eq:KuramotoGraph: KURA_SCALING_UNIFORM (calM_m = N) or
      * KURA_SCALING_DEGREE (calM_m = sum_l A_{m l}; zero rows get theta' = omega). */
