@@ -348,14 +348,41 @@ void enqueue_rk4_step(kura_ctx* h, double step, cudaStream_t s, cudaEvent_t* ev)
     }
 }
 
+// The fused trig (opts.fused_trig).  A run of RK4 stages starts with one
+// trig/block-sum launch on the first stage's input: it makes the table in
+// buffer 0 and leaves its block sums in accumulator 0.  Stage st = 1..4 of
+// every step then reads table buffer (st - 1) mod 2 and accumulator st - 1;
+// its row kernel writes the next stage's table into buffer st mod 2 and its
+// sums into accumulator st mod 4, and clears accumulator (st + 1) mod 4, which
+// no kernel of the stage touches.  Every step has four stages, so the same
+// buffers serve every step.
+void enqueue_fused_start(kura_ctx* h, const double* y_first, cudaStream_t s)
+{
+    unsigned long long* acc = h->bsum4.as<unsigned long long>();
+    cudaMemsetAsync(acc, 0, 2 * 2 * size_t(h->n_comm) * sizeof(unsigned long long), s);   // accumulators 0, 1
+    DevGraph g0 = dev_graph(h);
+    g0.bsum = acc;
+    if (h->opts.precision == KURA_PREC_MIXED) launch_trig<MODE_MIXED>(h, g0, y_first, TB_TABLE | TB_KEEP, s);
+    else launch_trig<MODE_FP64>(h, g0, y_first, TB_TABLE | TB_KEEP, s);
+}
+
+// The tables, digit images and accumulators of fused stage st (see enqueue_fused_start).
+void fused_stage_args(kura_ctx* h, int st, DevGraph& g, RkArgs& rk)
+{
+    void* tables[2] = {h->table.p, h->table2.p};
+    uint8_t* digs[2] = {h->has_tc ? h->dig.as<uint8_t>() : nullptr, h->has_tc ? h->dig2.as<uint8_t>() : nullptr};
+    unsigned long long* acc = h->bsum4.as<unsigned long long>();
+    const size_t nc2 = 2 * size_t(h->n_comm);
+    g.table = tables[(st - 1) % 2];
+    g.dig = digs[(st - 1) % 2];
+    rk.next_table = tables[st % 2];
+    rk.next_dig = digs[st % 2];
+    rk.bsum_cur = acc + nc2 * size_t(st - 1);
+    rk.bsum_next = acc + nc2 * size_t(st % 4);
+    rk.bsum_zero = acc + nc2 * size_t((st + 1) % 4);
+}
+
 // c RK4 steps enqueued on s; events (if any, 8 per step) bracket the row kernels.
-// With the fused trig (opts.fused_trig) one trig/block-sum launch makes the
-// first stage's table in buffer 0 and leaves its block sums in accumulator 0.
-// Stage st = 1..4 of every step then reads table buffer (st - 1) mod 2 and
-// accumulator st - 1; its row kernel writes the next stage's table into buffer
-// st mod 2 and its sums into accumulator st mod 4, and clears accumulator
-// (st + 1) mod 4, which no kernel of the stage touches.  Every step has four
-// stages, so the same buffers serve every step.
 void enqueue_rk4_steps(kura_ctx* h, double step, int64_t c, cudaStream_t s, cudaEvent_t* ev)
 {
     if (!h->opts.fused_trig) {
@@ -363,27 +390,13 @@ void enqueue_rk4_steps(kura_ctx* h, double step, int64_t c, cudaStream_t s, cuda
         return;
     }
     const bool mixed = h->opts.precision == KURA_PREC_MIXED;
-    const size_t nc2 = 2 * size_t(h->n_comm);
-    unsigned long long* acc = h->bsum4.as<unsigned long long>();
-    cudaMemsetAsync(acc, 0, 2 * nc2 * sizeof(unsigned long long), s);     // accumulators 0 and 1
-    DevGraph g = dev_graph(h);
-    DevGraph g0 = g;
-    g0.bsum = acc;
-    if (mixed) launch_trig<MODE_MIXED>(h, g0, h->y.as<double>(), TB_TABLE | TB_KEEP, s);
-    else launch_trig<MODE_FP64>(h, g0, h->y.as<double>(), TB_TABLE | TB_KEEP, s);
-    void* tables[2] = {h->table.p, h->table2.p};
-    uint8_t* digs[2] = {h->has_tc ? h->dig.as<uint8_t>() : nullptr, h->has_tc ? h->dig2.as<uint8_t>() : nullptr};
+    enqueue_fused_start(h, h->y.as<double>(), s);
     const RkArgs rk0 = rk_args(h, step);
     for (int64_t k = 0; k < c; k++) {
         for (int st = ST_1; st <= ST_4; st++) {
-            g.table = tables[(st - 1) % 2];
-            g.dig = digs[(st - 1) % 2];
+            DevGraph g = dev_graph(h);
             RkArgs rk = rk0;
-            rk.next_table = tables[st % 2];
-            rk.next_dig = digs[st % 2];
-            rk.bsum_cur = acc + nc2 * size_t(st - 1);
-            rk.bsum_next = acc + nc2 * size_t(st % 4);
-            rk.bsum_zero = acc + nc2 * size_t((st + 1) % 4);
+            fused_stage_args(h, st, g, rk);
             if (ev) cudaEventRecordWithFlags(ev[8 * k + 2 * (st - 1)], s, cudaEventRecordExternal);
             if (mixed) launch_row_stage<MODE_MIXED>(h, g, rk, st, s);
             else launch_row_stage<MODE_FP64>(h, g, rk, st, s);
@@ -1865,6 +1878,8 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     // forward row sums, then the adjoint steps, last to first (every pointer is fixed for a given L, so
     // full segments are captured once as a CUDA graph)
     auto enqueue_segment = [&](int64_t L, cudaStream_t q) {
+        const bool fused = h->opts.fused_trig != 0;
+        if (fused) enqueue_fused_start(h, Ybuf, q);
         for (int64_t t = 0; t < L; t++) {
             for (int st = ST_1; st <= ST_4; st++) {
                 RkArgs rk{};
@@ -1874,8 +1889,10 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
                 rk.krk = h->krk.as<double>();
                 rk.sums_out = Fbuf + size_t(4 * t + st - 1) * n;
                 rk.h = step;
-                launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, q);
-                launch_row_stage<MODE_MIXED>(h, g, rk, st, q);
+                DevGraph gs = g;
+                if (fused) fused_stage_args(h, st, gs, rk);
+                else launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, q);
+                launch_row_stage<MODE_MIXED>(h, gs, rk, st, q);
             }
         }
         for (int64_t t = L - 1; t >= 0; t--) {
