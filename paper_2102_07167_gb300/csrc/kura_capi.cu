@@ -1794,7 +1794,6 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
             KCHECK(h, d->alloc(N8), "alloc adjoint vectors");
         KCHECK(h, h->ad_sc.alloc(8 * n), "alloc sc");
         KCHECK(h, h->ad_bs.alloc(16 * size_t(h->n_comm)), "alloc block sums");
-        KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(ah->n_tiles, 1))), "alloc dK accumulators");
         KCHECK(h, h->ad_part.alloc(8 * ((n + 255) / 256)), "alloc loss partials");
         KCHECK(h, h->ad_absmax.alloc(16), "alloc table maximum");        // [0] max |entry|, [2] ticket
         KCHECK(h, cudaMemsetAsync(h->ad_absmax.p, 0, 16, s), "zero the table maximum and the ticket");
@@ -1817,6 +1816,13 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         h->ad_M = M;
         h->ad_nck = nck;
         h->graphs.clear();                 // captured segments point at the old buffers
+        h->last_graph = nullptr;
+    }
+    // the dK accumulators follow the tiles of the nu-weighted pass's plan, which kura_autotune or
+    // kura_classify_blocks may have rebuilt since the last call
+    if (h->ad_gk.bytes < 8 * size_t(std::max(ah->n_tiles, 1))) {
+        KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(ah->n_tiles, 1))), "alloc dK accumulators");
+        h->graphs.clear();
         h->last_graph = nullptr;
     }
     double* ck = h->ad_ck.as<double>();

@@ -221,3 +221,26 @@ def test_adjoint_config5_finite_differences_32_directions():
             ad.append(gth @ dth + gom @ dom + gK * dK)
     fd, ad = np.array(fd), np.array(ad)
     assert np.linalg.norm(ad - fd) <= 2e-3 * np.linalg.norm(fd), (np.linalg.norm(ad - fd), np.linalg.norm(fd))
+
+
+def test_adjoint_after_a_replan_with_more_tiles(small):
+    """The per-tile dK accumulators follow the plan: after kura_classify_blocks re-plans the handle into more
+    tiles, the next adjoint sizes them anew and gives the result of a handle planned that way from the
+    start."""
+    w = small
+    g = w.graph
+    h, steps, M = 0.01, 12, 4
+    th0 = torch.tensor(w.theta0, device="cuda:0")
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED,
+                       tensor_cores=0) as k:
+        k.adjoint(th0, h, steps, M, 0)
+        tiles0 = k.stats()["tiles"]
+        k.classify_blocks(0.01)                 # the dense blocks become sparse: many more listed entries
+        assert k.stats()["tiles"] > tiles0
+        L, gom, gK, gth = k.adjoint(th0, h, steps, M, 0)
+        got = (L, gom.cpu().numpy(), gK, gth.cpu().numpy())
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED,
+                       tensor_cores=0, tau=0.01) as k2:
+        L2, gom2, gK2, gth2 = k2.adjoint(th0, h, steps, M, 0)
+    assert abs(got[0] - L2) <= 1e-12 and abs(got[2] - gK2) <= 1e-10 * abs(gK2)
+    assert _rel(got[1], gom2.cpu().numpy()) < 1e-10 and _rel(got[3], gth2.cpu().numpy()) < 1e-10
