@@ -237,7 +237,7 @@ kura_status kura_mean_deviation(kura_t h, const double* theta_t, const double* t
 /* Gradient of a terminal loss of an RK4 trajectory by the discrete adjoint
  * of the classical RK4 step (backward sweep over the stage Jacobians of
  * eq:KuramotoGraph; the paper's integrator section, Sec. 2, extended to a
- * loss as the spec training use):
+ * terminal loss, as in training):
  *   loss_kind 0: L = 1 - r(theta(T)) (eq:OrderParameter);
  *   loss_kind 1: L = 1/2 sum_m (theta_m(T) - target_m)^2 (target[n], user order).
  * theta0[n] (user order, device or host) is not modified.  The forward pass
@@ -419,7 +419,7 @@ typedef struct {
  * threshold tau (0.35, 0.65), within about budget_s seconds of wall time
  * (plan builds included).  The fastest plan is kept on the handle (cached
  * step graphs are dropped).  Needs the host CSR (keep_host_csr = 1), else
- * KURA_ESTATE.  Synchronous.  Not available on batch handles. */
+ * KURA_ESTATE.  Synchronous. */
 kura_status kura_autotune(kura_t h, const double* theta, double budget_s, kura_tune_result* out);
 
 /* Measurement for rooflines (not part of the method): the median rate, in

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
 element by element on the same seeded inputs.
 
-Tolerances (spec readings):
+Tolerances (the stated ones, and the scale-free bound):
   FP64 right-hand side:   |df_i| <= 1e-11 (1 + deg_i)
   mixed right-hand side:  |df_i| <= 2e-4 (1 + deg_i) max(1, |f_i|)
   and, for both, the scale-free error e_i = |df_i| / ((K/calM_i)(1 + deg_i))
