@@ -142,6 +142,8 @@ struct kura_ctx {
     double K = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;        // capture stream (graphs are replayed on `stream`)
+    cudaStream_t ad_stream = nullptr;  // adjoint: the recompute of the next segment runs here
+    cudaEvent_t ad_ev[5] = {};         // adjoint: start, recompute done (per set), adjoint done (per set)
     // host copies
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_col, h_label, h_val;   // h_val: values of a finite-valued matrix (else empty)
@@ -159,7 +161,9 @@ struct kura_ctx {
     DevMem table2, dig2, bsum4;               // fused trig: second table and digit image, 4 sum accumulators
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
-        ad_tgt, ad_scratch, ad_absmax, ad_chunks, ad_chunk_ptr, ad_cpart;
+        ad_tgt, ad_scratch, ad_absmax, ad_chunks, ad_chunk_ptr, ad_cpart,
+        ad_Y2, ad_F2,                          // the second set of stage inputs and row sums
+        ad_table, ad_dig;                      // the nu-weighted table and its digits (the adjoint's own)
     int32_t ad_nchunks = 0;
     int64_t ad_M = 0, ad_nck = 0;
     int sym = -1;   // host CSR symmetric? (-1 unknown)
@@ -198,6 +202,9 @@ struct kura_ctx {
         if (device >= 0) cudaSetDevice(device);
         graphs.clear();
         if (cap) cudaStreamDestroy(cap);
+        if (ad_stream) cudaStreamDestroy(ad_stream);
+        for (cudaEvent_t e : ad_ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -1787,8 +1794,10 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     // buffers
     if (h->ad_M != M || h->ad_nck < nck || !h->ad_lam.p) {
         KCHECK(h, h->ad_ck.alloc(N8 * size_t(nck)), "alloc checkpoints");
-        KCHECK(h, h->ad_Y.alloc(N8 * size_t(4 * M + 1)), "alloc stage inputs");
-        KCHECK(h, h->ad_F.alloc(16 * n * size_t(4 * M)), "alloc stage sums");
+        for (DevMem* d : {&h->ad_Y, &h->ad_Y2}) KCHECK(h, d->alloc(N8 * size_t(4 * M + 1)), "alloc stage inputs");
+        for (DevMem* d : {&h->ad_F, &h->ad_F2}) KCHECK(h, d->alloc(16 * n * size_t(4 * M)), "alloc stage sums");
+        KCHECK(h, h->ad_table.alloc(8 * (n + 2)), "alloc the nu-weighted table");
+        KCHECK(h, cudaMemsetAsync(h->ad_table.p, 0, h->ad_table.bytes, s), "zero the nu-weighted table");
         for (DevMem* d : {&h->ad_lam, &h->ad_asum, &h->ad_a0, &h->ad_a1, &h->ad_w, &h->ad_nu, &h->ad_gom, &h->ad_tgt,
                           &h->ad_scratch})
             KCHECK(h, d->alloc(N8), "alloc adjoint vectors");
@@ -1819,15 +1828,23 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         h->last_graph = nullptr;
     }
     // the dK accumulators follow the tiles of the nu-weighted pass's plan, which kura_autotune or
-    // kura_classify_blocks may have rebuilt since the last call
+    // kura_classify_blocks may have rebuilt since the last call; so does the need for digits of the
+    // nu-weighted table (tensor-core tiles of A's own plan; A^T's plan has a digit image of its own)
     if (h->ad_gk.bytes < 8 * size_t(std::max(ah->n_tiles, 1))) {
         KCHECK(h, h->ad_gk.alloc(8 * size_t(std::max(ah->n_tiles, 1))), "alloc dK accumulators");
         h->graphs.clear();
         h->last_graph = nullptr;
     }
+    if (!h->tr && h->has_tc && h->ad_dig.bytes < h->dig.bytes) {
+        KCHECK(h, h->ad_dig.alloc(h->dig.bytes), "alloc the nu-weighted digit image");
+        KCHECK(h, cudaMemsetAsync(h->ad_dig.p, 0, h->ad_dig.bytes, s), "zero the nu-weighted digit image");
+        h->graphs.clear();
+        h->last_graph = nullptr;
+    }
     double* ck = h->ad_ck.as<double>();
-    double* Ybuf = h->ad_Y.as<double>();                // stage inputs: slot 4 t + (s - 1), plus one spare
-    double2* Fbuf = h->ad_F.as<double2>();              // forward row sums per (t, s)
+    // two sets of stage inputs (slot 4 t + (s - 1), plus one spare) and forward row sums per (t, s)
+    double* Ysets[2] = {h->ad_Y.as<double>(), h->ad_Y2.as<double>()};
+    double2* Fsets[2] = {h->ad_F.as<double2>(), h->ad_F2.as<double2>()};
     const unsigned nb = blocks_for(h->n, 256);
     const DevGraph g = dev_graph(h);
 
@@ -1843,9 +1860,73 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
         k_gather_perm<<<nb, 256, 0, s>>>(h->n, h->perm.as<int32_t>(), tg_dev, h->ad_tgt.as<double>());
     }
     KCHECK(h, cudaGetLastError(), "launching the permutation");
+    auto seg_len = [&](int64_t c) { return std::min(M, n_steps - c * M); };
+    // with the fused trig the backward runs two streams (below), and the forward keeps the stage inputs
+    // and row sums of its last segment, which then needs no recompute
+    const bool pipe = h->opts.fused_trig != 0;
+    // one segment of L steps from the state in Ysets[set] slot 0: integrate it, keeping every stage input
+    // and the forward row sums; the last step's new state goes to y_last
+    auto enqueue_recompute = [&](int64_t L, int set, double* y_last, cudaStream_t q) {
+        double* Ybuf = Ysets[set];
+        double2* Fbuf = Fsets[set];
+        const bool fused = h->opts.fused_trig != 0;
+        if (fused) enqueue_fused_start(h, Ybuf, q);
+        for (int64_t t = 0; t < L; t++) {
+            for (int st = ST_1; st <= ST_4; st++) {
+                RkArgs rk{};
+                rk.y = Ybuf + size_t(4 * t) * n;
+                rk.Y = Ybuf + size_t(4 * t + st) * n;                         // next stage input
+                rk.y_out = (t + 1 < L) ? Ybuf + size_t(4 * (t + 1)) * n : y_last;
+                rk.krk = h->krk.as<double>();
+                rk.sums_out = Fbuf + size_t(4 * t + st - 1) * n;
+                rk.h = step;
+                DevGraph gs = g;
+                if (fused) fused_stage_args(h, st, gs, rk);
+                else launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, q);
+                launch_row_stage<MODE_MIXED>(h, gs, rk, st, q);
+            }
+        }
+    };
+    // half 0: recompute a segment (its new state is not needed); 1: its adjoint steps; 2: the forward's
+    // last segment, kept for the backward (its new state is theta(T)).  Full segments are captured once
+    // per (half, set) as CUDA graphs, keyed apart from the forward step graphs.
+    std::function<void(int64_t, int, cudaStream_t)> enqueue_adjoint;
+    auto enqueue_half = [&](int half, int64_t L, int set, cudaStream_t q) {
+        if (half == 1) enqueue_adjoint(L, set, q);
+        else enqueue_recompute(L, set, half == 2 ? h->y.as<double>() : h->ad_scratch.as<double>(), q);
+    };
+    auto run_half = [&](int half, int64_t L, int set, cudaStream_t q) -> kura_status {
+        if (!(L == M && nck > 2)) {
+            enqueue_half(half, L, set, q);
+            return KURA_OK;
+        }
+        const std::pair<double, int64_t> key{step, -(int64_t(1) << 41) - 8 * M - 3 * set - half};
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            std::unique_ptr<GraphEntry> ge(new GraphEntry());
+            cudaGraph_t graph = nullptr;
+            KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            enqueue_half(half, L, set, h->cap);
+            cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture of an adjoint segment");
+            ec = cudaGraphInstantiate(&ge->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate an adjoint segment");
+            it = h->graphs.emplace(key, std::move(ge)).first;
+        }
+        KCHECK(h, cudaGraphLaunch(it->second->exec, q), "adjoint segment launch");
+        return KURA_OK;
+    };
     for (int64_t c = 0; c < nck; c++) {
+        if (pipe && c == nck - 1) {
+            const int set = int(c % 2);
+            KCHECK(h, cudaMemcpyAsync(Ysets[set], h->y.p, N8, cudaMemcpyDeviceToDevice, s), "last segment's start");
+            if (kura_status st = run_half(2, seg_len(c), set, s)) return st;
+            KCHECK(h, cudaGetLastError(), "launching the last forward segment");
+            break;
+        }
         KCHECK(h, cudaMemcpyAsync(ck + size_t(c) * n, h->y.p, N8, cudaMemcpyDeviceToDevice, s), "checkpoint");
-        if (kura_status st = run_steps_perm(h, step, std::min(M, n_steps - c * M))) return st;
+        if (kura_status st = run_steps_perm(h, step, seg_len(c))) return st;
     }
     // ---- terminal loss and lambda
     double* lam = h->ad_lam.as<double>();
@@ -1868,39 +1949,26 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     const double ca[5] = {0, 0.5 * step, 0.5 * step, step, 0.0};
     unsigned int* absmax = ah->has_tc ? h->ad_absmax.as<unsigned int>() : nullptr;
     unsigned int* ticket = h->ad_absmax.as<unsigned int>() + 2;
-    // graph of the nu-weighted pass: A's own, or A^T's plan reading A's table, T, scalings and error word
+    // graph of the nu-weighted pass: A's own, or A^T's plan reading A's T, scalings and error word; the
+    // nu-weighted table (and A's digits of it) are the adjoint's own buffers, so that the recompute of
+    // another segment, which uses the handle's tables, may run at the same time
     DevGraph ga = g;
     if (h->tr) {
         ga = dev_graph(h->tr.get());
-        ga.table = g.table;
         ga.T = g.T;
         ga.scale = g.scale;
         ga.rscale = g.rscale;
         ga.rinvdeg = g.rinvdeg;
         ga.inv_n = g.inv_n;
         ga.err = g.err;
+    } else if (absmax) {
+        ga.dig = h->ad_dig.as<uint8_t>();
     }
-    // one segment of L steps from the checkpoint in Ybuf: recompute it, keeping every stage input and the
-    // forward row sums, then the adjoint steps, last to first (every pointer is fixed for a given L, so
-    // full segments are captured once as a CUDA graph)
-    auto enqueue_segment = [&](int64_t L, cudaStream_t q) {
-        const bool fused = h->opts.fused_trig != 0;
-        if (fused) enqueue_fused_start(h, Ybuf, q);
-        for (int64_t t = 0; t < L; t++) {
-            for (int st = ST_1; st <= ST_4; st++) {
-                RkArgs rk{};
-                rk.y = Ybuf + size_t(4 * t) * n;
-                rk.Y = Ybuf + size_t(4 * t + st) * n;                         // next stage input
-                rk.y_out = (t + 1 < L) ? Ybuf + size_t(4 * (t + 1)) * n : h->ad_scratch.as<double>();
-                rk.krk = h->krk.as<double>();
-                rk.sums_out = Fbuf + size_t(4 * t + st - 1) * n;
-                rk.h = step;
-                DevGraph gs = g;
-                if (fused) fused_stage_args(h, st, gs, rk);
-                else launch_trig<MODE_MIXED>(h, g, Ybuf + size_t(4 * t + st - 1) * n, TB_TABLE | TB_T, q);
-                launch_row_stage<MODE_MIXED>(h, gs, rk, st, q);
-            }
-        }
+    ga.table = h->ad_table.p;
+    // a segment's adjoint steps, last to first
+    enqueue_adjoint = [&](int64_t L, int set, cudaStream_t q) {
+        double* Ybuf = Ysets[set];
+        double2* Fbuf = Fsets[set];
         for (int64_t t = L - 1; t >= 0; t--) {
             for (int st = 4; st >= 1; st--) {
                 double* a_next = (st < 4) ? ((st % 2 == 1) ? h->ad_a0.as<double>() : h->ad_a1.as<double>()) : nullptr;
@@ -1927,30 +1995,48 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
             }
         }
     };
-    for (int64_t c = nck - 1; c >= 0; c--) {
-        const int64_t L = std::min(M, n_steps - c * M);
-        KCHECK(h, cudaMemcpyAsync(Ybuf, ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, s), "restore checkpoint");
-        if (L == M && nck > 2) {
-            // full segments: replay one captured graph (keyed apart from the forward step graphs)
-            const std::pair<double, int64_t> key{step, -(int64_t(1) << 40) - M};
-            auto it = h->graphs.find(key);
-            if (it == h->graphs.end()) {
-                std::unique_ptr<GraphEntry> ge(new GraphEntry());
-                cudaGraph_t graph = nullptr;
-                KCHECK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-                enqueue_segment(L, h->cap);
-                cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
-                if (ec != cudaSuccess) return h->cuda_fail(ec, "end capture of an adjoint segment");
-                ec = cudaGraphInstantiate(&ge->exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ec != cudaSuccess) return h->cuda_fail(ec, "instantiate an adjoint segment");
-                it = h->graphs.emplace(key, std::move(ge)).first;
-            }
-            KCHECK(h, cudaGraphLaunch(it->second->exec, s), "adjoint segment launch");
-        } else {
-            enqueue_segment(L, s);
+    if (!pipe) {
+        // a trig launch per recompute stage writes the handle's T and block-sum counter, which the adjoint
+        // stages use too: one segment after the other on the handle's stream
+        for (int64_t c = nck - 1; c >= 0; c--) {
+            KCHECK(h, cudaMemcpyAsync(Ysets[0], ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, s), "restore checkpoint");
+            if (kura_status st = run_half(0, seg_len(c), 0, s)) return st;
+            if (kura_status st = run_half(1, seg_len(c), 0, s)) return st;
+            KCHECK(h, cudaGetLastError(), "launching the adjoint");
         }
-        KCHECK(h, cudaGetLastError(), "launching the adjoint");
+    } else {
+        // segment c's adjoint stages run on the handle's stream while segment c - 1 is recomputed on a
+        // second stream into the other set of stage buffers: the two share no buffer but read-only ones.
+        // Events: recomputing into a set waits for the end of the adjoint that last read it; an adjoint
+        // waits for its segment's recompute.
+        if (!h->ad_stream) KCHECK(h, cudaStreamCreateWithFlags(&h->ad_stream, cudaStreamNonBlocking), "adjoint stream");
+        for (cudaEvent_t& e : h->ad_ev)
+            if (!e) KCHECK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "adjoint events");
+        cudaStream_t r = h->ad_stream;
+        cudaEvent_t ev_start = h->ad_ev[0], *rec_done = h->ad_ev + 1, *adj_done = h->ad_ev + 3;
+        KCHECK(h, cudaEventRecord(ev_start, s), "record the backward start");
+        KCHECK(h, cudaStreamWaitEvent(r, ev_start, 0), "order the recompute stream");
+        auto recompute = [&](int64_t c) -> kura_status {
+            const int set = int(c % 2);
+            KCHECK(h, cudaMemcpyAsync(Ysets[set], ck + size_t(c) * n, N8, cudaMemcpyDeviceToDevice, r),
+                   "restore checkpoint");
+            if (kura_status st = run_half(0, seg_len(c), set, r)) return st;
+            KCHECK(h, cudaEventRecord(rec_done[set], r), "record a recompute");
+            return KURA_OK;
+        };
+        // the last segment's stage buffers come from the forward pass, on this stream
+        for (int64_t c = nck - 1; c >= 0; c--) {
+            const int set = int(c % 2);
+            if (c >= 1) {
+                // set (c - 1) mod 2 was last read by the adjoint of segment c + 1
+                if (c + 1 <= nck - 1) KCHECK(h, cudaStreamWaitEvent(r, adj_done[(c - 1) % 2], 0), "order a recompute");
+                if (kura_status st = recompute(c - 1)) return st;
+            }
+            if (c < nck - 1) KCHECK(h, cudaStreamWaitEvent(s, rec_done[set], 0), "order an adjoint segment");
+            if (kura_status st = run_half(1, seg_len(c), set, s)) return st;
+            KCHECK(h, cudaEventRecord(adj_done[set], s), "record an adjoint segment");
+            KCHECK(h, cudaGetLastError(), "launching the adjoint");
+        }
     }
     // ---- outputs
     double* gth_dev = host ? h->user.as<double>() : g_theta0;
