@@ -416,6 +416,28 @@ def bench_adjoint(dev):
     return out
 
 
+def adjoint_launches(dev):
+    """A short adjoint for a launch list: the adjoint workload's graph with the autotuner's plan for it (index
+    lists, tau 0.35), 192 steps with a checkpoint every 64; a warm-up call, then one call inside the NVTX
+    range "profiled" (for ncu --nvtx --nvtx-include "profiled/")."""
+    import torch
+    from paper_2102_07167_gb300 import gen as G
+    from paper_2102_07167_gb300 import kura
+    w = G.workload_sbm_small()
+    g = w.graph
+    with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED, tau=0.35,
+                       tensor_cores=0) as k:
+        th0 = torch.tensor(w.theta0, device=dev)
+        k.adjoint(th0, 0.01, 192, 64, 0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        L, gom, gK, gth = k.adjoint(th0, 0.01, 192, 64, 0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    return {"workload": "SBM N=65536, loss 1 - r(T), h = 0.01, 192 steps, checkpoint every 64, index lists, "
+                        "tau 0.35", "loss": L, "g_K": gK}
+
+
 def bench_batch(dev, steps: int = 1000, tc_steps: int = 50, dist=None):
     """2048 independent trajectories of uneven size in one persistent launch (half complete graphs, half SBMs),
     h = 0.01, mixed precision: the dense-block zeros as index lists (1000 steps), and as 0/1 masks multiplied
@@ -911,7 +933,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
-    ap.add_argument("--only", choices=["ensemble", "batch", "complete-512", "sbm-65536", "adjoint"], default=None,
+    ap.add_argument("--only", choices=["ensemble", "batch", "complete-512", "sbm-65536", "adjoint", "adjoint-launches"],
+                    default=None,
                     help="run one of the extra measurements alone (for profiling) and print its JSON")
     args = ap.parse_args()
     if args.only is not None:
@@ -925,6 +948,8 @@ def main():
             out = bench_complete_512(dev)
         elif args.only == "adjoint":
             out = bench_adjoint(dev)
+        elif args.only == "adjoint-launches":
+            out = adjoint_launches(dev)
         else:
             out = bench_sbm_65536(dev)
         print(json.dumps(out))
