@@ -1788,6 +1788,12 @@ kura_status kura_adjoint(kura_t h, const double* theta0, double step, int64_t n_
     }
     kura_ctx* ah = h->tr ? h->tr.get() : h;           // the plan the nu-weighted pass runs on
     cudaStream_t s = h->stream;
+    if (h->ad_stream && h->ad_ev[0]) {
+        // a previous call that failed midway may have left recompute work on the second stream: this
+        // call's work on the handle's stream comes after it
+        KCHECK(h, cudaEventRecord(h->ad_ev[0], h->ad_stream), "order after the recompute stream");
+        KCHECK(h, cudaStreamWaitEvent(s, h->ad_ev[0], 0), "order after the recompute stream");
+    }
     const size_t n = size_t(h->n), N8 = 8 * n;
     const int64_t M = ckpt_every;
     const int64_t nck = (n_steps + M - 1) / M;

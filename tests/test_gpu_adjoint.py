@@ -244,3 +244,29 @@ def test_adjoint_after_a_replan_with_more_tiles(small):
         L2, gom2, gK2, gth2 = k2.adjoint(th0, h, steps, M, 0)
     assert abs(got[0] - L2) <= 1e-12 and abs(got[2] - gK2) <= 1e-10 * abs(gK2)
     assert _rel(got[1], gom2.cpu().numpy()) < 1e-10 and _rel(got[3], gth2.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("tcm", [0, 2])
+def test_two_stream_backward_matches_one_stream(small, tcm):
+    """With the fused trig the backward recomputes segment c - 1 on a second stream while segment c's adjoint
+    stages run, alternating two sets of stage buffers, and the forward keeps its last segment; without it,
+    every segment is recomputed and then adjoined on one stream.  The kernels and their data are the same,
+    so the gradients agree bit for bit: 4 full segments (captured graphs, both buffer sets), index lists and
+    tensor-core tiles, two calls in a row."""
+    w = small
+    g = w.graph
+    h, steps, M = 0.01, 32, 8
+    res = {}
+    for fused in (1, 0):
+        with kura.Kuramoto(g.row_ptr, g.col, g.label, g.n_comm, w.omega, w.K, precision=kura.PREC_MIXED,
+                           tensor_cores=tcm, fused_trig=fused) as k:
+            th0 = torch.tensor(w.theta0, device="cuda:0")
+            out = []
+            for _ in range(2):
+                L, gom, gK, gth = k.adjoint(th0, h, steps, M, 0)
+                out.append((L, gom.cpu().numpy(), gK, gth.cpu().numpy()))
+            res[fused] = out
+    for call in range(2):
+        (L1, gom1, gK1, gth1), (L0, gom0, gK0, gth0) = res[1][call], res[0][call]
+        assert L1 == L0 and gK1 == gK0
+        assert np.array_equal(gom1, gom0) and np.array_equal(gth1, gth0)
