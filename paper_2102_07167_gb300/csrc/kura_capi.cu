@@ -157,7 +157,7 @@ struct kura_ctx {
     // device buffers
     DevMem perm, node_comm, gstream, groups, tiles, row_sub0, bitmap, dptr, dcol, comm_off, dig, dval, tcmask;
     bool valued = false;
-    DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, counter, err_flags;
+    DevMem omega, rscale, rinvdeg, table, bsum, bsum_out, tot, T, Tq, counter, err_flags;
     DevMem table2, dig2, bsum4;               // fused trig: second table and digit image, 4 sum accumulators
     // adjoint (allocated on first use)
     DevMem ad_ck, ad_Y, ad_F, ad_lam, ad_asum, ad_a0, ad_a1, ad_w, ad_nu, ad_sc, ad_gom, ad_bs, ad_gk, ad_part,
@@ -266,6 +266,7 @@ DevGraph dev_graph(kura_ctx* h)
     g.bsum_out = h->bsum_out.as<long long>();
     g.tot = h->tot.as<long long>();
     g.T = h->T.p;
+    g.Tq = h->Tq.as<long long>();
     g.counter = h->counter.as<unsigned int>();
     g.err = h->err_flags.as<int>();
     return g;
@@ -712,6 +713,7 @@ kura_status build_device(kura_ctx* h, Plan&& plan)
     KCHECK(h, h->bsum_out.alloc(16 * nc), "alloc bsum_out");
     KCHECK(h, h->tot.alloc(16), "alloc tot");
     KCHECK(h, h->T.alloc(16 * nc), "alloc T");
+    KCHECK(h, h->Tq.alloc(16 * nc), "alloc fixed-point T");
     KCHECK(h, h->counter.alloc(16), "alloc counter");
     KCHECK(h, cudaMemsetAsync(h->counter.p, 0, 16, s), "memset counter");
     if (!h->err_flags.p) {

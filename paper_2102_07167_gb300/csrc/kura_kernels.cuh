@@ -103,6 +103,7 @@ struct DevGraph {
     long long* bsum_out;                    // [2 n_comm] last block sums (S_J, C_J)
     long long* tot;                         // [2] last totals
     void* T;                                // FP64: longlong2[n_comm]; MIXED: double2[n_comm]
+    long long* Tq;                          // MIXED: the same T_I in fixed point, [2 n_comm] (forward stages)
     unsigned int* counter;                  // last-CTA ticket, zero between launches
     int* err;                               // latched error bits
 };
@@ -463,6 +464,10 @@ __global__ void __launch_bounds__(TRIG_THREADS) k_trig_blocksum(DevGraph g, cons
             else
                 reinterpret_cast<double2*>(g.T)[I] =
                     make_double2(static_cast<double>(ts) * g.inv_scale_q, static_cast<double>(tc) * g.inv_scale_q);
+            if (MODE == MODE_MIXED) {
+                g.Tq[2 * I] = ts;
+                g.Tq[2 * I + 1] = tc;
+            }
         }
     }
     __syncthreads();
@@ -996,11 +1001,18 @@ __global__ void __launch_bounds__(ROW_THREADS, 2) k_row_stage(DevGraph g, RkArgs
             si = static_cast<double>(own.x) * g.inv_scale_q;
             ci = static_cast<double>(own.y) * g.inv_scale_q;
         } else {
-            const double2 T = fused ? make_double2(static_cast<double>(t_fx[0]) * g.inv_scale_q,
-                                                   static_cast<double>(t_fx[1]) * g.inv_scale_q)
-                                    : reinterpret_cast<const double2*>(g.T)[t.comm];
-            acc_s = T.x + static_cast<double>(sa) - static_cast<double>(ms_s) * dig_inv;
-            acc_c = T.y + static_cast<double>(sc_) - static_cast<double>(ms_c) * dig_inv;
+            if (STAGE == ST_ADJ) {
+                const double2 T = reinterpret_cast<const double2*>(g.T)[t.comm];
+                acc_s = T.x + static_cast<double>(sa) - static_cast<double>(ms_s) * dig_inv;
+                acc_c = T.y + static_cast<double>(sc_) - static_cast<double>(ms_c) * dig_inv;
+            } else {
+                // T_I and the tensor-core sums are both exact fixed point: combined as integers, they
+                // cost one conversion and one FMA (FP64 is about 1/70 of the FP32 rate on this part)
+                const long long tqs = fused ? t_fx[0] : g.Tq[2 * t.comm];
+                const long long tqc = fused ? t_fx[1] : g.Tq[2 * t.comm + 1];
+                acc_s = fma(static_cast<double>(tqs - ms_s), g.inv_scale_q, static_cast<double>(sa));
+                acc_c = fma(static_cast<double>(tqc - ms_c), g.inv_scale_q, static_cast<double>(sc_));
+            }
             si = static_cast<double>(own.x);
             ci = static_cast<double>(own.y);
         }
