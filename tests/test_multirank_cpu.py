@@ -141,3 +141,10 @@ def test_batch_shards_two_gloo_ranks():
     n_total = sum(n for (_, n, _, _, _) in ens)
     assert r0[3] + r1[3] == n_total and r0[6] == r1[6] == n_total
     assert r0[5] == r1[5] and abs(r0[4] - n_total * 10 / (r0[5] / 1e3)) < 1e-6 * r0[4]
+
+
+def test_single_rank_shard_aggregate():
+    """One rank, no process group: the whole batch's oscillator-steps over that rank's time."""
+    import bench
+    value, el, n_all = bench.aggregate_shards(10.0, 1000, 5)
+    assert n_all == 1000 and el == 10.0 and abs(value - 1000 * 5 / 0.010) < 1e-9
